@@ -1,0 +1,131 @@
+/*
+ * tcm_oracle.c -- CPU oracle for the Triggered Cells Method (Naeh, arXiv:1702.00216).
+ *
+ * TEST INFRASTRUCTURE ONLY (see tcm_oracle.h).  Plain, slow, obviously correct
+ * C.  Built with -O2 -ffp-contract=off and without -ffast-math, so every + - *
+ * is one IEEE round-to-nearest operation and subnormals are kept.
+ *
+ * The type-generic parts (dense FDTD and TCM) live in tcm_oracle_impl.inc,
+ * included once with REAL = float and once with REAL = double.
+ */
+#include "tcm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n < 1) n = 1;
+    omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* Media rules at one node (Media: "describe the media by rules").  Later rules
+ * override earlier ones: background, then layers, then spheres. */
+static float media_rule_c(int64_t i, int64_t j, int64_t l, float c_background,
+                          int n_layers, const double *layer_z, const float *layer_c,
+                          int n_spheres, const double *sph, const float *sphere_c)
+{
+    float c = c_background;
+    for (int m = 0; m < n_layers; ++m)
+        if ((double)l >= layer_z[m]) c = layer_c[m];
+    for (int s = 0; s < n_spheres; ++s) {
+        double dx = (double)i - sph[4 * s + 0];
+        double dy = (double)j - sph[4 * s + 1];
+        double dz = (double)l - sph[4 * s + 2];
+        double r = sph[4 * s + 3];
+        if (dx * dx + dy * dy + dz * dz <= r * r) c = sphere_c[s];
+    }
+    return c;
+}
+
+void orc_rules_c(int64_t nx, int64_t ny, int64_t nz, float c_background,
+                 int n_layers, const double *layer_z, const float *layer_c,
+                 int n_spheres, const double *sphere_xyzr, const float *sphere_c,
+                 float *c_out)
+{
+    for (int64_t l = 0; l < nz; ++l)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i)
+                c_out[(l * ny + j) * nx + i] =
+                    media_rule_c(i, j, l, c_background, n_layers, layer_z, layer_c,
+                                 n_spheres, sphere_xyzr, sphere_c);
+}
+
+/* Eq. 3 coefficient (c*dt/dx)^2, formed in FP64. */
+static double k_of_c(float c, double dt, double dx)
+{
+    double r = (double)c * dt / dx;
+    return r * r;
+}
+
+void orc_k_from_c_f32(const float *c, int64_t n, double dt, double dx, float *k_out)
+{
+    for (int64_t i = 0; i < n; ++i) k_out[i] = (float)k_of_c(c[i], dt, dx);
+}
+
+void orc_k_from_c_f64(const float *c, int64_t n, double dt, double dx, double *k_out)
+{
+    for (int64_t i = 0; i < n; ++i) k_out[i] = k_of_c(c[i], dt, dx);
+}
+
+/* ---- energy ------------------------------------------------------------- */
+/* Leapfrog energy (see header).  Plain double loops; the FP32 entry widens
+ * each value first. */
+#define ENERGY_BODY(KT, FT)                                                              \
+    double e = 0.0;                                                                      \
+    for (int64_t l = 0; l < nz; ++l)                                                     \
+        for (int64_t j = 0; j < ny; ++j)                                                 \
+            for (int64_t i = 0; i < nx; ++i) {                                           \
+                int64_t id = (l * ny + j) * nx + i;                                      \
+                double bi = (double)b[id];                                               \
+                double nb = 0.0;                                                         \
+                if (i > 0) nb += (double)b[id - 1];                                      \
+                if (i < nx - 1) nb += (double)b[id + 1];                                 \
+                if (j > 0) nb += (double)b[id - nx];                                     \
+                if (j < ny - 1) nb += (double)b[id + nx];                                \
+                if (l > 0) nb += (double)b[id - nx * ny];                                \
+                if (l < nz - 1) nb += (double)b[id + nx * ny];                           \
+                double kb = 6.0 * bi - nb;                                               \
+                double d = (double)a[id] - bi;                                           \
+                e += d * d / (double)k[id] + (double)a[id] * kb;                         \
+            }                                                                            \
+    return e;
+
+double orc_energy_f64(int64_t nx, int64_t ny, int64_t nz, const double *k,
+                      const double *a, const double *b)
+{
+    ENERGY_BODY(double, double)
+}
+
+double orc_energy_f32(int64_t nx, int64_t ny, int64_t nz, const float *k,
+                      const float *a, const float *b)
+{
+    ENERGY_BODY(float, float)
+}
+
+/* ---- type-generic programs ---------------------------------------------- */
+#define REAL float
+#define SFX(name) name##_f32
+#define ORC_TCM_STRUCT orc_tcm_f32_s
+#include "tcm_oracle_impl.inc"
+#undef REAL
+#undef SFX
+#undef ORC_TCM_STRUCT
+
+#define REAL double
+#define SFX(name) name##_f64
+#define ORC_TCM_STRUCT orc_tcm_f64_s
+#include "tcm_oracle_impl.inc"
+#undef REAL
+#undef SFX
+#undef ORC_TCM_STRUCT
