@@ -1,0 +1,390 @@
+"""Benchmark of the Triggered Cells Method hot path on one GB300.
+
+A step is one time step of the whole hot path (Eq. 3 on the active bricks,
+source insertion, Eq. 6 decay, maxima, trigger/retire/box, active-list
+compaction) = one launch of the persistent step kernel, on the 512^3 layered,
+perturbed medium (relative threshold 1e-6, 20-step decay, 1500 steps).
+The simulation is first advanced untimed so that the K timed steps end at
+step 1500, where the wave fills most of the domain; W warm-up steps precede
+them.  Inputs stay resident in HBM (they are far larger than L2).
+
+Metric: active-cell updates per second (plus HBM GB/s against the measured
+copy roofline, TCM vs dense time to solution, per-step p50/p99).
+`--impl reference` times the CPU oracle on the host cores instead.
+
+Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOTAL_STEPS = 1500
+BYTES_PER_UPDATE = 16          # read phi^n, phi^{n-1}, k; write phi^{n+1} (FP32, per-node k)
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("tcm_kernels.cu", "tcm_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1702_00216_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(updates_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled by units, or None
+    when the kernel changed since the counters were taken."""
+    try:
+        d = json.load(open(PROFILE_TRAFFIC))
+    except Exception:
+        return None
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_update"]) * updates_per_launch
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__ as ge
+    from paper_1702_00216_gb300 import tcm, workloads as W
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1702_00216_gb300", "libtcm.so")):
+        ge.build()
+    if world > 1:
+        torch.distributed.barrier()
+        ge.build()
+    dev = torch.device("cuda", local_rank)
+    K, Wm = args.steps, args.warmup
+    wl = W.layered(steps=TOTAL_STEPS)
+    pool_bytes = 3 * 1024 ** 3
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device=dev)
+    sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
+    t0 = max(0, TOTAL_STEPS - K - Wm)
+    sim.step(t0)
+    sim.step(Wm)
+    torch.cuda.synchronize()
+    u0 = sim.updates
+    l0 = sim.launches
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        ev[0].record()
+        for i in range(K):
+            sim.step_async(1)
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sim.sync()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    updates = sim.updates - u0
+    launches = sim.launches - l0
+    active_end = sim.active_count()
+
+    t_max = total_ms
+    upd_all = updates
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+        uu = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(uu)
+        upd_all = float(uu.item())
+    value = upd_all / (t_max / 1e3)
+
+    peaks, peak_kind = measured_peaks()
+    achieved = updates * BYTES_PER_UPDATE / (total_ms / 1e3) / 1e9
+    traffic = profiled_traffic(updates / max(launches, 1))
+    sim.close()
+    del pool
+    torch.cuda.empty_cache()
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = time_to_solution(torch, tcm, W, wl, dev, local_rank)
+    e2e = end_to_end(torch, tcm, W, wl, local_rank) if not args.quick else None
+    cpu = cpu_baseline(W, args) if (rank == 0 and world == 1 and not args.quick) else None
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "active-cell updates/s",
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": t_max / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "grid": list(wl.shape[::-1]), "brick": list(wl.brick),
+                   "threshold": "relative 1e-6", "decay": "alpha 0.8, 20 steps",
+                   "timed_steps": [TOTAL_STEPS - K, TOTAL_STEPS],
+                   "l2": "inputs larger than L2 (fields + per-node k > 1.5 GB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "algorithmic_bytes_per_update": BYTES_PER_UPDATE,
+                     "kernel": "k_step (persistent, one launch per step)"},
+        "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                    "min": float(min(step_ms)), "max": float(max(step_ms))},
+        "active_bricks_end": active_end[0],
+        "active_cells_end": active_end[1],
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def time_to_solution(torch, tcm, W, wl, dev, local_rank):
+    """Full 1500-step runs from create to the final field on the device: TCM vs
+    the same kernel over every brick (dense)."""
+    out = {}
+    for dense in (False, True):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s = tcm.Sim.from_workload(wl, dense=dense, device=local_rank,
+                                  pool_bytes=None if dense else 3 * 1024 ** 3)
+        s.step(TOTAL_STEPS)
+        buf = torch.empty(wl.shape, dtype=torch.float32, device=dev)
+        tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out["dense" if dense else "tcm"] = {"seconds": dt, "cell_updates": s.updates}
+        if not dense:
+            ref = buf
+        else:
+            diff = float((buf - ref).abs().max().item())
+            out["max_abs_diff_tcm_vs_dense"] = diff
+            out["max_abs_field"] = float(buf.abs().max().item())
+        s.close()
+        del buf
+    del ref
+    torch.cuda.empty_cache()
+    return {"time_to_solution": {
+        "workload": f"{wl.name}, {TOTAL_STEPS} steps, create + steps + device readback",
+        "tcm_s": out["tcm"]["seconds"], "dense_s": out["dense"]["seconds"],
+        "speedup": out["dense"]["seconds"] / out["tcm"]["seconds"],
+        "tcm_cell_updates": out["tcm"]["cell_updates"],
+        "dense_cell_updates": out["dense"]["cell_updates"],
+        "max_abs_diff_tcm_vs_dense": out["max_abs_diff_tcm_vs_dense"],
+        "max_abs_field": out["max_abs_field"]}}
+
+
+def end_to_end(torch, tcm, W, wl, local_rank):
+    """The same metric through the public API with host buffers: velocity model
+    and wavelet from pinned host memory, 1500 steps, final field back to host."""
+    nz, ny, nx = wl.shape
+    c_host = torch.empty(wl.shape, dtype=torch.float32, pin_memory=True)
+    c_host.numpy()[...] = wl.media.c
+    out_host = torch.empty(wl.shape, dtype=torch.float32, pin_memory=True)
+    media = W.dense_media(c_host.numpy())
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s = tcm.Sim(wl.shape, media, wl.dx, wl.dt, threshold=wl.tau, brick=wl.brick,
+                thr_mode=wl.thr_mode, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps,
+                pool_bytes=3 * 1024 ** 3, device=local_rank)
+    for x, y, z, w in wl.sources:
+        s.add_source(x, y, z, np.asarray(w, np.float32))
+    s.step(TOTAL_STEPS)
+    rc = tcm.lib().tcm_read_field(s.handle, 0, 0, 0, 0, nx, ny, nz,
+                                  tcm.C.c_void_p(out_host.data_ptr()))
+    if rc != 0:
+        raise tcm.TCMError(rc, "tcm_read_field")
+    dt = time.perf_counter() - t
+    upd = s.updates
+    s.close()
+    h2d = c_host.numel() * 4 + sum(len(w) * 4 for *_, w in wl.sources)
+    d2h = out_host.numel() * 4
+    return {"value": upd / dt, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": h2d / TOTAL_STEPS, "d2h_bytes_per_step": d2h / TOTAL_STEPS,
+            "seconds": dt, "steps": TOTAL_STEPS,
+            "what": "tcm_create from host velocity + tcm_add_source + tcm_step(1500) + "
+                    "tcm_read_field of the whole grid to pinned host memory"}
+
+
+def cpu_baseline(W, args, budget_s: float = 15.0, wl=None):
+    """The oracle (plain C, as it stands) on the host cores: the layered 512^3
+    workload from step 0, as many steps as fit in the time budget."""
+    import oracle
+    threads = os.cpu_count() or 1
+    used = oracle.set_threads(threads)
+    if wl is None:
+        wl = W.layered(steps=TOTAL_STEPS)
+    o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, brick=wl.brick, thr_mode=wl.thr_mode,
+                         tau=wl.tau, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps)
+    for x, y, z, w in wl.sources:
+        o.add_source(x, y, z, np.asarray(w, np.float32))
+    t = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t < budget_s and steps < TOTAL_STEPS:
+        o.step(10)
+        steps += 10
+    dt = time.perf_counter() - t
+    upd = o.updates
+    o.close()
+    return {"value": upd / dt, "unit": "cell-updates/s", "cores": used, "kind": "oracle",
+            "sample": f"{wl.name}: steps 0..{steps} of {TOTAL_STEPS} ({upd} cell updates, "
+                      f"{dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm: K timed steps of the same workload
+    (from step W, after W warm-up steps), on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1702_00216_gb300 import workloads as W
+    oracle.lib()
+    threads = os.cpu_count() or 1
+    used = oracle.set_threads(threads)
+    wl = W.layered(steps=TOTAL_STEPS)
+    o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, brick=wl.brick, thr_mode=wl.thr_mode,
+                         tau=wl.tau, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps)
+    for x, y, z, w in wl.sources:
+        o.add_source(x, y, z, np.asarray(w, np.float32))
+    o.step(args.warmup)
+    u0 = o.updates
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    upd = o.updates - u0
+    v = upd / dt
+    line = {"metric": "active-cell updates/s", "value": v, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "grid": list(wl.shape[::-1]), "brick": list(wl.brick),
+                       "timed_steps": [args.warmup, args.warmup + args.steps]},
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": used, "kind": "oracle",
+                             "sample": f"steps {args.warmup}..{args.warmup + args.steps} of "
+                                       f"{wl.name} ({upd} cell updates)"},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    o.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="skip time-to-solution, e2e, CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

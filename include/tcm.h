@@ -1,0 +1,177 @@
+/*
+ * tcm.h -- C ABI of the GB300 Triggered Cells Method library (libtcm.so).
+ *
+ * Method: Naeh, "Handling massive spatial volumes in time domain simulations
+ * using Triggered Cells Method", arXiv:1702.00216.  One time step advances the
+ * 3D scalar wave equation (Eq. 1) with the second-order central-difference
+ * update of Eq. 3,
+ *     phi^{n+1} = 2 phi^n - phi^{n-1} + k (sum of 6 neighbours - 6 phi^n),
+ *     k = (c dt / dx)^2,
+ * but only on the triggered cells ("bricks"), each held in a box ("slot") of
+ * an on-device pool (Boxes, Fig. 1), with the media bulked once (Heterogenic
+ * Bulking Method, Media), sources inserted into forced-active cells (Source
+ * insertion), the trigger/retire procedure run every step (Updating active
+ * cells, Fig. 3a) and an optional time-domain shut-down (Eq. 6).
+ *
+ * Conventions
+ *  - All field and velocity arrays are x fastest: index = (z*ny + y)*nx + x.
+ *  - Every function returns a tcm_status; no exception, abort or device trap
+ *    crosses this interface.  After an error the simulation stays readable.
+ *  - Host pointers are read (or written) only during the call; the library
+ *    keeps its own copies.  Device memory passed in tcm_options.pool_ptr stays
+ *    owned by the caller and must outlive the simulation.
+ *  - Work is issued on tcm_options.stream (a cudaStream_t; NULL = the legacy
+ *    default stream) of device tcm_options.device.
+ *  - Arithmetic: binary32 round-to-nearest, no contraction into FMA, no
+ *    flush-to-zero, one fixed grouping of Eq. 3:
+ *        s = ((xm + xp) + (ym + yp)) + (zm + zp);  lap = s - 6 p;
+ *        q = (2 p - pm) + k lap;   then + source sample;  then * alpha in shut-down.
+ *    Results are bit-for-bit reproducible and independent of scheduling.
+ *  - Nodes outside the domain read as zero (zero Dirichlet boundary); the
+ *    domain need not be a multiple of the brick size.
+ */
+#ifndef TCM_H
+#define TCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tcm_sim tcm_sim; /* opaque, library-owned */
+
+typedef enum {
+    TCM_OK = 0,
+    TCM_EINVAL = 1,   /* bad argument (sizes, pointers, brick shape, source outside) */
+    TCM_ECFL = 2,     /* max(c) dt / dx > 1/sqrt(3): violates Eq. 4 */
+    TCM_ENOMEM = 3,   /* pool exhausted (or a device allocation failed) */
+    TCM_EDEVICE = 4,  /* a CUDA call failed */
+    TCM_ETIMEOUT = 5, /* a device-wide barrier gave up waiting (bounded spin) */
+    TCM_ESTATE = 6    /* call not allowed in this state (e.g. after ENOMEM) */
+} tcm_status;
+
+enum { TCM_MEDIA_DENSE = 0, TCM_MEDIA_RULES = 1 };
+enum { TCM_THR_ABSOLUTE = 0, TCM_THR_RELATIVE = 1 };
+enum { TCM_STORAGE_F32 = 0 };
+
+typedef struct {
+    int64_t nx, ny, nz; /* nodes */
+} tcm_domain;
+
+/* Velocity model (Media).  DENSE: c is a host array of nx*ny*nz floats.
+ * RULES: c = c_background; then for each layer m in order c = layer_c[m]
+ * where z >= layer_z[m]; then for each sphere s in order c = sphere_c[s] where
+ * (x-X)^2 + (y-Y)^2 + (z-Z)^2 <= R^2 with sphere_xyzr[4s..4s+3] = X,Y,Z,R
+ * (node-index units, FP64).  Rules are evaluated once, at tcm_create. */
+typedef struct {
+    int kind;
+    const float *c;
+    float c_background;
+    int n_layers;
+    const double *layer_z;
+    const float *layer_c;
+    int n_spheres;
+    const double *sphere_xyzr;
+    const float *sphere_c;
+} tcm_velocity_model;
+
+/* Brick ("cell") shape in nodes.  Supported: 8x8x8. */
+typedef struct {
+    int bx, by, bz;
+} tcm_brick;
+
+typedef struct {
+    int threshold_mode; /* TCM_THR_ABSOLUTE: level = threshold;
+                           TCM_THR_RELATIVE: level = threshold * max|phi^{n+1}| (FP64) */
+    float decay_alpha;  /* Eq. 6 factor per shut-down step */
+    int decay_steps;    /* Eq. 6 n; 0 = release a quiet brick at once */
+    void *pool_ptr;     /* device memory for the boxes, or NULL: library allocates */
+    size_t pool_bytes;  /* size of the pool (caps the number of boxes) */
+    void *stream;       /* cudaStream_t */
+    int storage;        /* TCM_STORAGE_F32 */
+    int dense;          /* 1: box every brick and never release (dense comparator) */
+    int device;         /* CUDA device ordinal */
+} tcm_options;
+
+/* Bytes of pool one box takes for this brick shape and storage (two field
+ * halves).  TCM_EINVAL for unsupported shapes. */
+tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out);
+
+/* Create a simulation (Cells construction, Media / HBM bulking, Boxes).
+ * dx, dt > 0; threshold >= 0.  Checks Eq. 4 on the largest velocity of the
+ * model (TCM_ECFL) before touching the GPU.  Allocates the brick tables
+ * (about 12 bytes per brick of the whole domain), per-box metadata, and the
+ * bulked coefficient arrays of heterogeneous bricks.  *out is NULL on error. */
+tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *velocity, double dx,
+                      double dt, double threshold, tcm_brick brick, const tcm_options *options,
+                      tcm_sim **out);
+
+/* Add a point source at node (x,y,z) (Source insertion): sample i of the
+ * wavelet is added to phi^{s+i+1} at that node, s = the step index at the time
+ * of the call, and the source's brick is forced active while samples remain.
+ * Only before the first tcm_step.  The wavelet is copied. */
+tcm_status tcm_add_source(tcm_sim *sim, int64_t x, int64_t y, int64_t z, const float *wavelet,
+                          int64_t n_samples);
+
+/* Initial fields phi^0 and phi^{-1} (host arrays, nx*ny*nz).  Bricks holding a
+ * non-zero value in either become active.  Only before the first tcm_step. */
+tcm_status tcm_set_field(tcm_sim *sim, const float *phi_now, const float *phi_prev);
+
+/* Advance n steps; returns when they are done (or failed).  TCM_ENOMEM: the
+ * pool ran out, the step completed without the bricks that found no box and
+ * the simulation is poisoned (later steps return TCM_ESTATE). */
+tcm_status tcm_step(tcm_sim *sim, int64_t n);
+
+/* Enqueue n steps on the stream and return at once; tcm_sync reports the
+ * status of everything enqueued. */
+tcm_status tcm_step_async(tcm_sim *sim, int64_t n);
+tcm_status tcm_sync(tcm_sim *sim);
+
+/* Copy a window of phi^n (which = 0) or phi^{n-1} (which = 1) into host_out
+ * (wx*wy*wz floats, x fastest).  Zeros where a brick is inactive or the window
+ * leaves the domain.  The _device variant writes device memory on the stream. */
+tcm_status tcm_read_field(const tcm_sim *sim, int which, int64_t x0, int64_t y0, int64_t z0,
+                          int64_t wx, int64_t wy, int64_t wz, float *host_out);
+tcm_status tcm_read_field_device(const tcm_sim *sim, int which, int64_t x0, int64_t y0,
+                                 int64_t z0, int64_t wx, int64_t wy, int64_t wz,
+                                 float *device_out);
+
+/* Active bricks for the next step, and the in-domain nodes they hold. */
+tcm_status tcm_active_count(const tcm_sim *sim, int64_t *bricks, int64_t *cells);
+
+/* Sorted ids (z*my*mx + y*mx + x over the brick grid) of the active bricks;
+ * *n = how many there are, at most cap are written. */
+tcm_status tcm_active_bricks(const tcm_sim *sim, int64_t *ids, int64_t cap, int64_t *n);
+
+/* Cumulative node updates (sum over steps of active in-domain nodes). */
+tcm_status tcm_updates(const tcm_sim *sim, int64_t *cell_updates);
+
+/* Discrete leapfrog energy between phi^n and phi^{n-1}:
+ *   E = sum (phi^n - phi^{n-1})^2 / k + sum phi^n (6 phi^{n-1} - sum of 6 neighbours of phi^{n-1})
+ * over active bricks, accumulated in FP64 on the device.  Constant once the
+ * sources have stopped while no brick is released (threshold 0). */
+tcm_status tcm_energy(const tcm_sim *sim, double *e);
+
+/* Heterogenic bulking result of brick b: *kind = 1 homogenic (*k = its
+ * coefficient) or 2 bulked (per-node coefficients). */
+tcm_status tcm_brick_media(const tcm_sim *sim, int64_t b, int *kind, float *k);
+
+/* Boxes: total in the pool, and currently free. */
+tcm_status tcm_pool_info(const tcm_sim *sim, int64_t *slots, int64_t *free_slots);
+
+/* Kernel launches issued so far (one per step). */
+int64_t tcm_launch_count(const tcm_sim *sim);
+
+/* Step index n of phi^n. */
+int64_t tcm_step_index(const tcm_sim *sim);
+
+const char *tcm_status_string(tcm_status s);
+
+void tcm_destroy(tcm_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCM_H */

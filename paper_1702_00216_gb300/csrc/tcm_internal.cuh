@@ -1,0 +1,150 @@
+// tcm_internal.cuh -- device-side data layout shared by the kernels and the host
+// runtime of libtcm (Triggered Cells Method, Naeh, arXiv:1702.00216).
+//
+// HBM layout of one engine (a set of simulations stepped by one launch):
+//   pool      phi[slot][half][z][y][x]   two binary32 halves of one brick per box
+//                                        (Boxes: "a space in memory ... called a box")
+//   per brick slot_of_brick[g]  int32    Cell2box (-1 inactive, -2 claim in flight)
+//             kscal[g]          float    homogenic coefficient (HBM)
+//             kslab_of_brick[g] int32    index of the bulked coefficient brick, -1 if homogenic
+//             bitmap[g/32]      bit      active for the next step (drives the compaction)
+//   per box   meta[slot]        16 B     Box2cell brick id, bulk index, scalar k, sim/sd flags
+//             rec[slot][8]      float    6 face maxima, cell maximum, max |phi^{n+1}|
+//             nbr[slot][8]      int32    slots of the 6 face neighbours seen this step
+//   lists     list[2][n_slots]  int32    active boxes in brick order (double-buffered)
+//             free_stack, retired, newslots  int32 per box
+// Global brick index g = sim.brick_base + local brick id; every sim's range
+// starts on a 32-brick boundary so bitmap words never straddle two sims.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tcm {
+
+constexpr int BX = 8, BY = 8, BZ = 8;
+constexpr int BVOL = BX * BY * BZ;          // nodes per brick
+constexpr int XQ = BX / 4;                  // float4 columns per brick row
+constexpr int TPB = XQ * BY;                // threads per brick (one float4 column, all z)
+constexpr int BLOCK = 256;                  // threads per CTA of the step kernel
+constexpr int BRICKS_PER_WARP = 32 / TPB;
+
+constexpr unsigned ERR_NOMEM = 1u;
+constexpr unsigned ERR_TIMEOUT = 2u;
+
+constexpr unsigned FLAG_HAS_SRC = 1u << 15;
+constexpr unsigned SD_MASK = 0x7fffu;
+
+enum { MEDIA_DENSE = 0, MEDIA_RULES = 1 };
+
+struct __align__(16) SlotMeta {
+    int brick;       // local brick id within its sim (Box2cell)
+    int kslab;       // bulked coefficient brick, or -1
+    float kscal;     // homogenic coefficient
+    unsigned flags;  // sim << 16 | has_src << 15 | shut-down steps left
+};
+
+struct SimDev {
+    // immutable after create
+    int nx, ny, nz;
+    int mx, my, mz;
+    long long brick_base;
+    long long n_bricks;
+    int thr_mode;
+    int dense;
+    double tau;
+    float alpha;
+    int decay_steps;
+    int src_begin, src_end;
+    // mutable (device-owned)
+    long long step;        // n of phi^n
+    unsigned gmax[2];      // max |phi^{n+1}| of step n in gmax[n & 1] (float bits)
+    unsigned poisoned;
+    unsigned pad;
+};
+
+struct SrcDev {
+    int sim;
+    int brick;           // local brick id
+    int local;           // node index within the brick
+    int pad;
+    long long start;     // first step that adds a sample
+    long long len;
+    long long w_off;     // offset into the concatenated wavelets
+};
+
+struct EngineState {
+    int free_top;          // entries on the free stack
+    int n_retired;         // boxes released this step (pushed by the compaction phase)
+    int n_new;             // boxes claimed this step (zeroed by the compaction phase)
+    int list_parity;       // which list holds the current active boxes
+    int n_active[2];
+    unsigned err;
+    unsigned bar_count;
+    unsigned bar_gen;
+    unsigned pad0;
+    unsigned long long updates;   // cumulative node updates
+    unsigned long long launches;
+};
+
+struct Engine {
+    float *phi;
+    int n_slots;
+    int *slot_of_brick;
+    const float *kscal;
+    const int *kslab_of_brick;
+    const float *kslabs;
+    unsigned *bitmap;
+    long long n_words;
+    int *blocktot;
+    int words_per_block;
+    SlotMeta *meta;
+    float *rec;
+    int *nbr;
+    int *list0, *list1;
+    int *free_stack, *retired, *newslots;
+    SimDev *sims;
+    int n_sims;
+    const SrcDev *src;
+    int n_src;
+    const float *wave;
+    EngineState *st;
+};
+
+struct MediaDev {
+    int kind;
+    const float *c;        // dense, device
+    float c_bg;
+    int n_layers;
+    const double *layer_z;
+    const float *layer_c;
+    int n_spheres;
+    const double *sph;
+    const float *sph_c;
+};
+
+// ---- launchers (tcm_kernels.cu) -------------------------------------------
+// Every launcher returns the cudaError_t of its launch.
+cudaError_t launch_bulk_classify(const MediaDev &m, int nx, int ny, int nz, int mx, int my, int mz,
+                                 double dt, double dx, float *kscal, int *kslab_of_brick,
+                                 int *n_kslabs, cudaStream_t s);
+cudaError_t launch_bulk_fill(const MediaDev &m, int nx, int ny, int nz, int mx, int my, int mz,
+                             double dt, double dx, const int *kslab_of_brick, float *kslabs,
+                             cudaStream_t s);
+cudaError_t launch_iota_desc(int *a, int n, int first, cudaStream_t s);
+cudaError_t launch_prime(const Engine &e, int sim, const long long *bricks, long long n,
+                         int slot0, int list_parity, cudaStream_t s);
+cudaError_t launch_zero_slots(const Engine &e, int slot0, long long n, cudaStream_t s);
+cudaError_t launch_scatter_field(const Engine &e, const float *packed, long long n, int slot0,
+                                 int now_half, cudaStream_t s);
+cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s);
+int step_grid_size(int device);
+cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
+                               long long z0, long long wx, long long wy, long long wz, float *out,
+                               cudaStream_t s);
+cudaError_t launch_energy(const Engine &e, int sim, int now_half, int list_parity, double *out,
+                          cudaStream_t s);
+cudaError_t launch_active_bricks(const Engine &e, int list_parity, long long *ids_out,
+                                 unsigned long long *cells_out, cudaStream_t s);
+
+}  // namespace tcm

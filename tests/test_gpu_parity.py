@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Floating point: binary32 round-to-nearest on both sides with one fixed
+grouping of Eq. 3, so fields must agree bit for bit (this is inside the
+stated tolerance max|d phi| <= 1e-5 max|phi|, asserted as well).  Active
+brick sets are compared as sorted id sets (box numbering depends on atomic
+order and is never compared).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00216_gb300 import tcm
+from paper_1702_00216_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+F32 = np.float32
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def pair(wl, dense=False, pool_bytes=None, **okw):
+    g = tcm.Sim.from_workload(wl, dense=dense, pool_bytes=pool_bytes)
+    o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, brick=wl.brick, thr_mode=wl.thr_mode,
+                         tau=wl.tau, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps,
+                         dense=dense, **okw)
+    for x, y, z, w in wl.sources:
+        o.add_source(x, y, z, np.asarray(w, F32))
+    return g, o
+
+
+def assert_same(g, o, window=None):
+    kw = {} if window is None else {"origin": window[0], "size": window[1]}
+    for which in (0, 1):
+        a, b = g.read_field(which, **kw), o.read_field(which, **kw)
+        scale = max(float(np.max(np.abs(b))), 1e-30)
+        assert float(np.max(np.abs(a - b))) <= TOL * scale
+        assert np.array_equal(a, b), f"half {which}: max |d| = {float(np.max(np.abs(a - b)))}"
+    assert np.array_equal(g.active_bricks(), o.active_bricks())
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_small_config_64cubed(dense):
+    """64^3, c = 1, Courant 0.5, centred Ricker, 100 steps, 8^3 bricks, threshold 0."""
+    wl = W.small()
+    g, o = pair(wl, dense=dense)
+    done = 0
+    for cp in (1, 2, 9, 33, 60, 100):
+        g.step(cp - done)
+        o.step(cp - done)
+        done = cp
+        assert_same(g, o)
+        assert g.active_count() == o.active_count()
+    assert g.updates == o.updates
+    assert g.launches == 100
+
+
+def test_threshold0_tcm_equals_dense_gpu():
+    wl = W.small()
+    g, _ = pair(wl)
+    d = tcm.Sim.from_workload(wl, dense=True)
+    g.step(100)
+    d.step(100)
+    assert np.array_equal(g.read_field(0), d.read_field(0))
+    assert np.array_equal(g.read_field(1), d.read_field(1))
+
+
+@pytest.mark.parametrize("shape", [(21, 29, 37), (8, 8, 8), (3, 5, 2), (17, 9, 33)])
+def test_heterogeneous_ragged_multisource(shape):
+    rng = np.random.default_rng(sum(shape))
+    media = W.random_dense_media(shape, 7, 1.0, 2.0)
+    dt = 0.5 / media.c_max()
+    nz, ny, nx = shape
+    srcs = [(int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz)),
+             W.ricker(1 / rng.uniform(4, 10), dt)) for _ in range(3)]
+    srcs.append((nx - 1, ny - 1, nz - 1, W.ricker(1 / 6, dt)))
+    srcs.append((srcs[0][0], srcs[0][1], srcs[0][2], W.ricker(1 / 5, dt)))   # two at one node
+    wl = W.Workload("het", shape, media, 1.0, dt, srcs, 70)
+    g, o = pair(wl)
+    for _ in range(7):
+        g.step(10)
+        o.step(10)
+        assert_same(g, o)
+
+
+def test_rules_media_bulking_matches_oracle():
+    """Heterogenic Bulking: the GPU's per-brick classification and scalar k
+    equal the oracle's for layers cutting bricks and a sphere."""
+    shape = (40, 48, 56)
+    media = W.Media(kind="rules", c_background=1.0, layers=[(12.0, 1.5), (29.5, 2.0)],
+                    spheres=[(27.3, 20.0, 21.0, 9.5, 0.7), (8.0, 8.0, 8.0, 8.0, 2.2)])
+    dt = 0.5 / media.c_max()
+    wl = W.Workload("rules", shape, media, 1.0, dt, [(20, 24, 18, W.ricker(1 / 8, dt))], 80)
+    g, o = pair(wl)
+    nb = g.mx * g.my * g.mz
+    kinds = set()
+    for b in range(nb):
+        gb, ob = g.brick_media(b), o.brick_media(b)
+        kinds.add(gb[0])
+        assert gb[0] == ob[0], b
+        if gb[0] == 1:
+            assert np.float32(gb[1]) == np.float32(ob[1]), b
+    assert kinds == {1, 2}
+    g.step(80)
+    o.step(80)
+    assert_same(g, o)
+
+
+@pytest.mark.parametrize("mode,tau,alpha,D", [(tcm.TCM_THR_ABSOLUTE, 3e-2, 1.0, 0),
+                                               (tcm.TCM_THR_ABSOLUTE, 1e-2, 0.8, 5),
+                                               (tcm.TCM_THR_RELATIVE, 1e-3, 0.7, 3),
+                                               (tcm.TCM_THR_RELATIVE, 1e-6, 0.8, 20)])
+def test_threshold_decay_retire_reuse(mode, tau, alpha, D):
+    """Thresholds above 0: triggering, shut-down (Eq. 6), release and box
+    reuse, step by step against the oracle."""
+    shape = (40, 48, 56)
+    media = W.Media(kind="rules", c_background=1.0, layers=[(20.0, 1.4)])
+    dt = 0.5 / media.c_max()
+    wl = W.Workload("thr", shape, media, 1.0, dt, [(20, 24, 10, W.ricker(1 / 8, dt))], 240,
+                    thr_mode=mode, tau=tau, decay_alpha=alpha, decay_steps=D)
+    g, o = pair(wl)
+    counts = []
+    for n in range(240):
+        g.step(1)
+        o.step(1)
+        if n % 7 == 0 or n > 230:
+            assert np.array_equal(g.active_bricks(), o.active_bricks()), n
+        counts.append(o.active_count()[0])
+    assert_same(g, o)
+    assert g.updates == o.updates
+
+
+def test_pool_exhaustion_reports_enomem():
+    wl = W.small(n=48, steps=60)
+    g = tcm.Sim.from_workload(wl, pool_bytes=5 * tcm.tcm_slot_bytes())
+    with pytest.raises(tcm.TCMError) as e:
+        g.step(60)
+    assert e.value.status == tcm.TCM_ENOMEM
+    with pytest.raises(tcm.TCMError) as e:
+        g.step(1)
+    assert e.value.status == tcm.TCM_ESTATE
+    assert g.active_count()[0] <= 5      # still readable
+    g.read_field(0)
+
+
+def test_energy_matches_oracle_and_is_conserved():
+    """FP64 energy reduction on the device equals the oracle's energy of the
+    same (bit-equal) fields; at threshold 0 it is constant after the source."""
+    shape = (24, 26, 30)
+    media = W.random_dense_media(shape, 3, 1.0, 1.6)
+    dt = 0.5 / media.c_max()
+    w = W.ricker(1 / 6, dt)
+    wl = W.Workload("energy", shape, media, 1.0, dt, [(12, 13, 11, w)], len(w) + 150)
+    g, o = pair(wl)
+    k = oracle.k_from_c(media.c, dt, 1.0, F32)
+    es = []
+    for n in (len(w) + 10, len(w) + 150):
+        g.step(n - g.step_index)
+        o.step(n - o.step_index)
+        e_ref = oracle.energy(k, o.read_field(0), o.read_field(1))
+        e_gpu = g.energy()
+        assert e_gpu == pytest.approx(e_ref, rel=1e-12)
+        es.append(e_gpu)
+    assert abs(es[1] - es[0]) / es[0] < 1e-5      # FP32 recursion, FP64 sum
+
+
+def test_set_field_eigenmode():
+    """Initial fields from tcm_set_field (an eigenmode on a ragged grid)."""
+    shape = (11, 9, 13)
+    v = W.eigenmode(shape, (1, 2, 3)).astype(F32)
+    wl = W.Workload("mode", shape, W.homogeneous(1.0), 1.0, 0.5, [], 50)
+    g, o = pair(wl)
+    g.set_field(v, (0.9 * v).astype(F32))
+    o.set_field(v, (0.9 * v).astype(F32))
+    g.step(50)
+    o.step(50)
+    assert_same(g, o)
+
+
+def test_mirror_symmetry_gpu():
+    n = 41
+    wl = W.Workload("sym", (n, n, n), W.homogeneous(1.0), 1.0, 0.5,
+                    [(20, 20, 20, W.ricker(1 / 8, 0.5))], 45)
+    g = tcm.Sim.from_workload(wl)
+    g.step(45)
+    a = g.read_field(0)
+    assert np.abs(a).max() > 0
+    for t in (a[::-1], a[:, ::-1], a[:, :, ::-1], a.transpose(0, 2, 1)):
+        assert np.array_equal(a, t)
+
+
+def test_empty_simulation():
+    wl = W.Workload("empty", (16, 24, 8), W.homogeneous(1.0), 1.0, 0.5, [], 5)
+    g = tcm.Sim.from_workload(wl)
+    g.step(5)
+    assert g.active_count() == (0, 0)
+    assert np.all(g.read_field(0) == 0)
+    assert g.updates == 0
+
+
+def test_causality_window_reads():
+    """Windows that leave the domain read zeros there; the cone of a source
+    ends at L1 distance n-1."""
+    shape = (30, 31, 32)
+    wl = W.Workload("cone", shape, W.homogeneous(1.0), 1.0, 0.5,
+                    [(3, 29, 15, W.ricker(1 / 8, 0.5))], 9)
+    g = tcm.Sim.from_workload(wl)
+    g.step(9)
+    win = g.read_field(0, origin=(-4, 20, 10), size=(12, 16, 12))
+    assert np.all(win[:, :, :4] == 0) and np.all(win[:, 11:, :] == 0)
+    full = g.read_field(0)
+    zz, yy, xx = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    dist = np.abs(xx - 3) + np.abs(yy - 29) + np.abs(zz - 15)
+    assert np.all(full[dist > 8] == 0) and np.any(full[dist == 8] != 0)
+    expect = np.zeros_like(win)
+    expect[:, :11, 4:] = full[10:22, 20:31, 0:8]
+    assert np.array_equal(win, expect)
+
+
+def test_layered_512_first_steps_full_size():
+    """The 512^3 layered, perturbed medium at full size in the benchmarked
+    launch configuration: the first 160 steps (relative threshold 1e-6,
+    20-step decay) against the oracle, on the window the wave occupies."""
+    wl = W.layered(steps=160)
+    g, o = pair(wl, pool_bytes=2 * 1024 ** 3)
+    g.step(160)
+    o.step(160)
+    ids = o.active_bricks()
+    assert np.array_equal(g.active_bricks(), ids)
+    assert len(ids) > 8
+    bx = ids % 64
+    by = (ids // 64) % 64
+    bz = ids // 4096
+    lo = [int(v.min()) * 8 for v in (bx, by, bz)]
+    hi = [int(v.max()) * 8 + 8 for v in (bx, by, bz)]
+    assert_same(g, o, window=(lo, [h - l for h, l in zip(hi, lo)]))
+    assert g.updates == o.updates
+
+
+def test_virtual_4096_first_steps():
+    """The virtual 4096^3 domain (never allocated densely): 120 steps of the
+    sphere-inclusion burst against the oracle, on the active window."""
+    wl = W.virtual(steps=120, pool_bytes=4 * 1024 ** 3)
+    g, o = pair(wl, pool_bytes=4 * 1024 ** 3)
+    g.step(120)
+    o.step(120)
+    ids = o.active_bricks()
+    assert np.array_equal(g.active_bricks(), ids)
+    m = 512
+    bx, by, bz = ids % m, (ids // m) % m, ids // (m * m)
+    lo = [int(v.min()) * 8 for v in (bx, by, bz)]
+    hi = [int(v.max()) * 8 + 8 for v in (bx, by, bz)]
+    assert_same(g, o, window=(lo, [h - l for h, l in zip(hi, lo)]))

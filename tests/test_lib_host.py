@@ -1,0 +1,126 @@
+"""Host-side checks of the C library that need no GPU: it builds, loads,
+exports every function include/tcm.h declares, and rejects bad arguments
+(including the CFL bound of Eq. 4) before touching a device."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1702_00216_gb300 import build as B
+from paper_1702_00216_gb300 import tcm
+from paper_1702_00216_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return tcm.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tcm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tcm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(tcm.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", tcm.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (tcm_\w+)", out))
+    missing = set(declared_functions()) - exported
+    assert not missing, missing
+    for name in declared_functions():
+        assert hasattr(lib, name)
+
+
+def test_slot_bytes(lib):
+    assert tcm.tcm_slot_bytes((8, 8, 8)) == 2 * 512 * 4
+    with pytest.raises(tcm.TCMError) as e:
+        tcm.tcm_slot_bytes((8, 8, 4))
+    assert e.value.status == tcm.TCM_EINVAL
+
+
+def _opts(**kw):
+    o = tcm.tcm_options()
+    o.pool_bytes = kw.get("pool_bytes", 1 << 20)
+    o.decay_alpha = 1.0
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@pytest.mark.parametrize("courant,expect", [(0.58, tcm.TCM_ECFL), (0.6, tcm.TCM_ECFL)])
+def test_create_rejects_cfl_violation(lib, courant, expect):
+    """Eq. 4: c dt / dx <= 1/sqrt(3), checked on the largest velocity."""
+    media = W.Media(kind="rules", c_background=1.0, spheres=[(4, 4, 4, 2.0, 2.0)])
+    with pytest.raises(tcm.TCMError) as e:
+        tcm.tcm_create((16, 16, 16), media, 1.0, courant / 2.0, 0.0, (8, 8, 8), _opts())
+    assert e.value.status == expect
+    dense = W.dense_media(np.full((8, 8, 8), 1.0, np.float32))
+    dense.c[3, 3, 3] = 3.0
+    with pytest.raises(tcm.TCMError) as e:
+        tcm.tcm_create((8, 8, 8), dense, 1.0, courant / 3.0, 0.0, (8, 8, 8), _opts())
+    assert e.value.status == expect
+
+
+@pytest.mark.parametrize("bad", ["shape", "dx", "dt", "thr", "brick", "decay", "mode", "cneg",
+                                 "pool"])
+def test_create_rejects_bad_arguments(lib, bad):
+    shape, dx, dt, thr, brick = (16, 16, 16), 1.0, 0.5, 0.0, (8, 8, 8)
+    media = W.homogeneous(1.0)
+    kw = {}
+    if bad == "shape":
+        shape = (0, 16, 16)
+    elif bad == "dx":
+        dx = 0.0
+    elif bad == "dt":
+        dt = -1.0
+    elif bad == "thr":
+        thr = -1.0
+    elif bad == "brick":
+        brick = (8, 8, 7)
+    elif bad == "decay":
+        kw["decay_steps"] = -1
+    elif bad == "mode":
+        kw["threshold_mode"] = 7
+    elif bad == "cneg":
+        media = W.homogeneous(-1.0)
+    elif bad == "pool":
+        kw["pool_bytes"] = 100
+    with pytest.raises(tcm.TCMError) as e:
+        tcm.tcm_create(shape, media, dx, dt, thr, brick, _opts(**kw))
+    assert e.value.status == tcm.TCM_EINVAL
+
+
+def test_status_strings(lib):
+    assert tcm.tcm_status_string(tcm.TCM_OK) == "ok"
+    assert "CFL" in tcm.tcm_status_string(tcm.TCM_ECFL)
+    assert tcm.tcm_status_string(99) == "unknown status"
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    """A valid simulation needs the GPU: without one, create fails loudly."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tcm.TCMError) as e:
+        tcm.tcm_create((16, 16, 16), W.homogeneous(1.0), 1.0, 0.5, 0.0, (8, 8, 8), _opts())
+    assert e.value.status == tcm.TCM_EDEVICE
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1702_00216_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "tcm_oracle" not in txt, f
