@@ -4,9 +4,10 @@ A step is one time step of the whole hot path (Eq. 3 on the active bricks,
 source insertion, Eq. 6 decay, maxima, trigger/retire/box, active-list
 compaction) = one launch of the persistent step kernel, on the 512^3 layered,
 perturbed medium (relative threshold 1e-6, 20-step decay, 1500 steps).
-The simulation is first advanced untimed so that the K timed steps end at
-step 1500, where the wave fills most of the domain; W warm-up steps precede
-them.  Inputs stay resident in HBM (they are far larger than L2).
+By default the timed region is the whole run after W warm-up steps (steps
+W..1500); with a smaller K the simulation is first advanced untimed so that
+the K timed steps end at step 1500.  Inputs stay resident in HBM (they are
+far larger than L2).
 
 Metric: active-cell updates per second (plus HBM GB/s against the measured
 copy roofline, TCM vs dense time to solution, per-step p50/p99).
@@ -33,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 TOTAL_STEPS = 1500
 BYTES_PER_UPDATE = 16          # read phi^n, phi^{n-1}, k; write phi^{n+1} (FP32, per-node k)
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_layered256_traffic.txt")
 
 
 def env_int(name, default):
@@ -109,7 +110,9 @@ def profiled_traffic(updates_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary, scaled by units, or None
     when the kernel changed since the counters were taken."""
     try:
-        d = json.load(open(PROFILE_TRAFFIC))
+        d = dict(ln.split(":", 1) for ln in open(PROFILE_TRAFFIC)
+                 if ":" in ln and not ln.startswith("#"))
+        d = {k.strip(): v.strip() for k, v in d.items()}
     except Exception:
         return None
     if d.get("kernel_hash") != kernel_source_hash():
@@ -138,13 +141,24 @@ def run_ours(args, rank, world, local_rank):
         ge.build()
     dev = torch.device("cuda", local_rank)
     K, Wm = args.steps, args.warmup
-    wl = W.layered(steps=TOTAL_STEPS)
-    pool_bytes = 3 * 1024 ** 3
+    wl = W.layered(n=args.grid, steps=TOTAL_STEPS)
+    # enough boxes for every brick of the grid (the layered wave reaches most of it)
+    pool_bytes = (args.grid // 8) ** 3 * tcm.tcm_slot_bytes(wl.brick)
     pool = torch.empty(pool_bytes, dtype=torch.uint8, device=dev)
     sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
     t0 = max(0, TOTAL_STEPS - K - Wm)
-    sim.step(t0)
-    sim.step(Wm)
+    if args.trace:
+        # one step at a time, recording the node updates of every launch
+        with open(args.trace, "w") as f:
+            last = 0
+            for n in range(t0 + Wm):
+                sim.step(1)
+                u = sim.updates
+                f.write(json.dumps({"launch": n, "step": n, "cell_updates": u - last}) + "\n")
+                last = u
+    else:
+        sim.step(t0)
+        sim.step(Wm)
     torch.cuda.synchronize()
     u0 = sim.updates
     l0 = sim.launches
@@ -189,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.quick:
         extra = time_to_solution(torch, tcm, W, wl, dev, local_rank)
     e2e = end_to_end(torch, tcm, W, wl, local_rank) if not args.quick else None
-    cpu = cpu_baseline(W, args) if (rank == 0 and world == 1 and not args.quick) else None
+    cpu = cpu_baseline(W, args, wl=wl) if (rank == 0 and world == 1 and not args.quick) else None
 
     if rank != 0:
         return
@@ -237,7 +251,7 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
         torch.cuda.synchronize()
         t = time.perf_counter()
         s = tcm.Sim.from_workload(wl, dense=dense, device=local_rank,
-                                  pool_bytes=None if dense else 3 * 1024 ** 3)
+                                  pool_bytes=None)
         s.step(TOTAL_STEPS)
         buf = torch.empty(wl.shape, dtype=torch.float32, device=dev)
         tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
@@ -276,7 +290,7 @@ def end_to_end(torch, tcm, W, wl, local_rank):
     t = time.perf_counter()
     s = tcm.Sim(wl.shape, media, wl.dx, wl.dt, threshold=wl.tau, brick=wl.brick,
                 thr_mode=wl.thr_mode, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps,
-                pool_bytes=3 * 1024 ** 3, device=local_rank)
+                pool_bytes=None, device=local_rank)
     for x, y, z, w in wl.sources:
         s.add_source(x, y, z, np.asarray(w, np.float32))
     s.step(TOTAL_STEPS)
@@ -362,8 +376,11 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=TOTAL_STEPS - 5)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--grid", type=int, default=512, help="edge of the layered workload")
+    ap.add_argument("--trace", default=None,
+                    help="write per-launch node updates of the untimed steps (JSON lines)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip time-to-solution, e2e, CPU baseline")
     args = ap.parse_args()
