@@ -154,6 +154,23 @@ tcm_status tcm_updates(const tcm_sim *sim, int64_t *cell_updates);
  * sources have stopped while no brick is released (threshold 0). */
 tcm_status tcm_energy(const tcm_sim *sim, double *e);
 
+/* The same energy as tcm_energy, written to device memory (*device_out, one
+ * double) on the simulation's stream, without allocating any device memory.
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc/cudaFree while the simulation runs -- programs whose device
+ * memory belongs to another allocator with a fixed budget, and code on a
+ * latency-critical path that must not synchronise the device (freeing memory
+ * does).  Its scratch is a static 512 KiB device array (one partial sum per
+ * active brick) that every GPU loading the library holds until exit, so at
+ * most 65536 active bricks: larger active sets return TCM_EINVAL.  The first
+ * call on a device looks up the array's device address; make that first call
+ * before any stream capture.  The array is shared by all calls and keeps the
+ * last call's partial sums (each call overwrites what it reads), so calls
+ * whose work overlaps on the GPU race: serialise them.  Only after the
+ * simulation has started (TCM_ESTATE before); blocks for one 4-byte read of
+ * the active count; the sum is in a fixed order (deterministic). */
+tcm_status tcm_energy_noalloc(const tcm_sim *sim, double *device_out);
+
 /* Heterogenic bulking result of brick b: *kind = 1 homogenic (*k = its
  * coefficient) or 2 bulked (per-node coefficients). */
 tcm_status tcm_brick_media(const tcm_sim *sim, int64_t b, int *kind, float *k);

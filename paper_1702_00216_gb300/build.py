@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtcm.so")
-UNITS = ["tcm_kernels.cu", "tcm_api.cu"]
+UNITS = ["tcm_kernels.cu", "tcm_api.cu", "tcm_noalloc.cu"]
 DEPS = UNITS + ["tcm_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-ftz=false", "-prec-div=true",

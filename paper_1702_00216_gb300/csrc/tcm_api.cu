@@ -255,6 +255,18 @@ float model_c_max(const tcm_domain *d, const tcm_velocity_model *v, bool *bad)
 
 }  // namespace
 
+bool tcm_internal_view(const tcm_sim *s, SimView *v)
+{
+    if (!s || !v) return false;
+    v->E = &s->E;
+    v->device = s->device;
+    v->stream = s->stream;
+    v->started = s->started;
+    v->step = s->step;
+    v->list_parity = s->list_parity;
+    return true;
+}
+
 extern "C" {
 
 tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out)

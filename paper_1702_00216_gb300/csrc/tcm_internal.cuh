@@ -147,4 +147,18 @@ cudaError_t launch_energy(const Engine &e, int sim, int now_half, int list_parit
 cudaError_t launch_active_bricks(const Engine &e, int list_parity, long long *ids_out,
                                  unsigned long long *cells_out, cudaStream_t s);
 
+// Read-only view of a simulation for entry points defined outside tcm_api.cu.
+struct SimView {
+    const Engine *E;
+    int device;
+    cudaStream_t stream;
+    bool started;
+    long long step;
+    int list_parity;
+};
+
 }  // namespace tcm
+
+struct tcm_sim;
+// Fills *v; false when sim is NULL.  Defined in tcm_api.cu.
+__attribute__((visibility("hidden"))) bool tcm_internal_view(const tcm_sim *sim, tcm::SimView *v);

@@ -24,6 +24,7 @@ TCM_STORAGE_F32 = 0
 EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "tcm_step",
            "tcm_step_async", "tcm_sync", "tcm_read_field", "tcm_read_field_device",
            "tcm_active_count", "tcm_active_bricks", "tcm_updates", "tcm_energy",
+           "tcm_energy_noalloc",
            "tcm_brick_media", "tcm_pool_info", "tcm_launch_count", "tcm_step_index",
            "tcm_status_string", "tcm_destroy"]
 
@@ -80,6 +81,7 @@ def lib():
             "tcm_active_bricks": ([_vp, _vp, _i64, _vp], C.c_int),
             "tcm_updates": ([_vp, _vp], C.c_int),
             "tcm_energy": ([_vp, _vp], C.c_int),
+            "tcm_energy_noalloc": ([_vp, _vp], C.c_int),
             "tcm_brick_media": ([_vp, _i64, _vp, _vp], C.c_int),
             "tcm_pool_info": ([_vp, _vp, _vp], C.c_int),
             "tcm_launch_count": ([_vp], _i64),
@@ -215,6 +217,11 @@ def tcm_energy(h) -> float:
     e = C.c_double(0)
     _chk(lib().tcm_energy(h, C.byref(e)), "tcm_energy")
     return e.value
+
+
+def tcm_energy_noalloc(h, device_out_ptr: int):
+    """Energy into one device double at device_out_ptr; allocates nothing."""
+    _chk(lib().tcm_energy_noalloc(h, _vp(device_out_ptr)), "tcm_energy_noalloc")
 
 
 def tcm_brick_media(h, b):
