@@ -162,6 +162,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     u0 = sim.updates
     l0 = sim.launches
+    ph0 = sim.phase_ns()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     if world > 1:
         torch.distributed.barrier()
@@ -179,6 +180,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms = ev[0].elapsed_time(ev[K])
     updates = sim.updates - u0
     launches = sim.launches - l0
+    ph = [b - a for a, b in zip(ph0, sim.phase_ns())]
     active_end = sim.active_count()
 
     t_max = total_ms
@@ -232,6 +234,8 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": "k_step (persistent, one launch per step)"},
         "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                     "min": float(min(step_ms)), "max": float(max(step_ms))},
+        "phase_ms": {"time_stepping": ph[0] / 1e6, "update_active": ph[1] / 1e6,
+                     "compaction": ph[2] / 1e6},
         "active_bricks_end": active_end[0],
         "active_cells_end": active_end[1],
         "gpu_launches": launches,

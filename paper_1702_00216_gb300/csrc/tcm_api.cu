@@ -46,6 +46,7 @@ struct tcm_sim {
     long long launches = 0;
     int list_parity = 0;
     unsigned *h_err = nullptr;  // pinned
+    PoolMaps maps{};
 };
 
 namespace {
@@ -185,7 +186,7 @@ tcm_status start(tcm_sim *s)
         TRY(cudaMalloc(&d_init, n_init * sizeof(long long)));
         TRY(cudaMemcpyAsync(d_init, init.data(), n_init * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
     }
-    TRY(launch_prime(s->E, 0, d_init, n_init, 0, 0, s->stream));
+    TRY(launch_prime(s->E, 0, d_init, n_init, 0, s->stream));
     TRY(launch_zero_slots(s->E, 0, n_init, s->stream));
     if (s->have_field && n_init > 0) {
         // pack the initial values of the boxed bricks
@@ -219,6 +220,7 @@ tcm_status start(tcm_sim *s)
     es.list_parity = 0;
     es.n_active[0] = (int)n_init;
     TRY(cudaMemcpyAsync(s->E.st, &es, sizeof(es), cudaMemcpyHostToDevice, s->stream));
+    TRY(launch_compact(s->E, s->grid, 0, s->stream));
     TRY(cudaStreamSynchronize(s->stream));
     if (d_init) cudaFree(d_init);
     s->list_parity = 0;
@@ -360,6 +362,7 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     }
     Engine &E = s->E;
     E.phi = static_cast<float *>(s->pool);
+    if (!make_pool_maps(E.phi, n_slots, &s->maps)) return fail(TCM_EDEVICE);
     E.n_slots = n_slots;
     E.n_words = s->n_words;
     E.words_per_block = (int)((s->n_words + s->grid - 1) / s->grid);
@@ -376,9 +379,9 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     if ((st = dalloc(s, &E.blocktot, s->grid)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.meta, n_slots)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.rec, (size_t)n_slots * 8)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.nbr, (size_t)n_slots * 8)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.list0, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.list1, n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(s, &E.items0, n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(s, &E.items1, n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(s, &E.listids, n_slots)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.free_stack, n_slots)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.retired, n_slots)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.newslots, n_slots)) != TCM_OK) return fail(st);
@@ -527,7 +530,7 @@ tcm_status tcm_step_async(tcm_sim *s, int64_t n)
     tcm_status st = start(s);
     if (st != TCM_OK) return st;
     for (int64_t i = 0; i < n; ++i) {
-        cudaError_t e = launch_step(s->E, s->grid, s->stream);
+        cudaError_t e = launch_step(s->E, s->maps, s->grid, s->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             s->poisoned = true;
@@ -709,6 +712,24 @@ tcm_status tcm_pool_info(const tcm_sim *cs, int64_t *slots, int64_t *free_slots)
     TRY(cudaMemcpyAsync(&es, s->E.st, sizeof(es), cudaMemcpyDeviceToHost, s->stream));
     TRY(cudaStreamSynchronize(s->stream));
     *free_slots = std::max(es.free_top, 0) + es.n_retired;
+    return TCM_OK;
+}
+
+tcm_status tcm_phase_ns(const tcm_sim *cs, int64_t *stepping, int64_t *update, int64_t *compaction)
+{
+    tcm_sim *s = const_cast<tcm_sim *>(cs);
+    if (!s) return TCM_EINVAL;
+    int64_t v[3] = {0, 0, 0};
+    if (s->started) {
+        DeviceGuard g(s->device);
+        EngineState es{};
+        TRY(cudaMemcpyAsync(&es, s->E.st, sizeof(es), cudaMemcpyDeviceToHost, s->stream));
+        TRY(cudaStreamSynchronize(s->stream));
+        for (int i = 0; i < 3; ++i) v[i] = (int64_t)es.phase_ns[i];
+    }
+    if (stepping) *stepping = v[0];
+    if (update) *update = v[1];
+    if (compaction) *compaction = v[2];
     return TCM_OK;
 }
 

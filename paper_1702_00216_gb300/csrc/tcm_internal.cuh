@@ -10,14 +10,15 @@
 //             bitmap[g/32]      bit      active for the next step (drives the compaction)
 //   per box   meta[slot]        16 B     Box2cell brick id, bulk index, scalar k, sim/sd flags
 //             rec[slot][8]      float    6 face maxima, cell maximum, max |phi^{n+1}|
-//             nbr[slot][8]      int32    slots of the 6 face neighbours seen this step
-//   lists     list[2][n_slots]  int32    active boxes in brick order (double-buffered)
-//             free_stack, retired, newslots  int32 per box
+//   lists     items[2][n_slots] 48 B     active bricks in brick order (double-buffered): box,
+//                                        brick, k, flags and the boxes of the 6 face neighbours
+//             listids, free_stack, retired, newslots  int32 per box
 // Global brick index g = sim.brick_base + local brick id; every sim's range
 // starts on a 32-brick boundary so bitmap words never straddle two sims.
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace tcm {
@@ -26,8 +27,19 @@ constexpr int BX = 8, BY = 8, BZ = 8;
 constexpr int BVOL = BX * BY * BZ;          // nodes per brick
 constexpr int XQ = BX / 4;                  // float4 columns per brick row
 constexpr int TPB = XQ * BY;                // threads per brick (one float4 column, all z)
-constexpr int BLOCK = 256;                  // threads per CTA of the step kernel
+constexpr int P1_WARPS = 6;                 // warps per CTA of the step kernel
+constexpr int BLOCK = 32 * P1_WARPS;        // threads per CTA of the step kernel
 constexpr int BRICKS_PER_WARP = 32 / TPB;
+
+// Shared-memory staging of one brick (bytes, 128-byte aligned): phi^n,
+// phi^{n-1}, k, and the neighbours' boundary layers.  The x faces arrive as
+// 4-wide columns (the narrowest tensor-copy box), the others exactly.
+constexpr int OFF_P = 0, OFF_M = 2048, OFF_K = 4096, OFF_XM = 6144, OFF_XP = 7168;
+constexpr int OFF_ZM = 8192, OFF_ZP = 8448, OFF_YM = 8704, OFF_YP = 8960;
+constexpr int BRICK_SMEM = 9216;
+constexpr int STAGE_SMEM = BRICKS_PER_WARP * BRICK_SMEM;   // one warp's bricks
+constexpr int WARP_SMEM = 2 * STAGE_SMEM;                  // double-buffered
+constexpr int STEP_DYN_SMEM = P1_WARPS * WARP_SMEM;        // 221184 B
 
 constexpr unsigned ERR_NOMEM = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -43,6 +55,18 @@ struct __align__(16) SlotMeta {
     float kscal;     // homogenic coefficient
     unsigned flags;  // sim << 16 | has_src << 15 | shut-down steps left
 };
+
+// One active brick of the list (built by the compaction phase).
+struct __align__(16) WorkItem {
+    int slot;
+    int brick;
+    int kslab;
+    float kscal;
+    unsigned flags;
+    int nb[6];       // boxes of the face neighbours x-, x+, y-, y+, z-, z+ (-1 none, -3 outside)
+    int nh;          // field half holding phi^n for the step that processes this item
+};
+static_assert(sizeof(WorkItem) == 48, "work item layout");
 
 struct SimDev {
     // immutable after create
@@ -82,9 +106,11 @@ struct EngineState {
     unsigned err;
     unsigned bar_count;
     unsigned bar_gen;
-    unsigned pad0;
+    unsigned p3_done;      // blocks finished with the compaction phase this launch
     unsigned long long updates;   // cumulative node updates
     unsigned long long launches;
+    unsigned long long t_start, t_p1, t_p2;   // globaltimer stamps of the current launch
+    unsigned long long phase_ns[3];           // cumulative: time stepping, update, compaction
 };
 
 struct Engine {
@@ -100,8 +126,8 @@ struct Engine {
     int words_per_block;
     SlotMeta *meta;
     float *rec;
-    int *nbr;
-    int *list0, *list1;
+    WorkItem *items0, *items1;
+    int *listids;
     int *free_stack, *retired, *newslots;
     SimDev *sims;
     int n_sims;
@@ -133,11 +159,20 @@ cudaError_t launch_bulk_fill(const MediaDev &m, int nx, int ny, int nz, int mx, 
                              cudaStream_t s);
 cudaError_t launch_iota_desc(int *a, int n, int first, cudaStream_t s);
 cudaError_t launch_prime(const Engine &e, int sim, const long long *bricks, long long n,
-                         int slot0, int list_parity, cudaStream_t s);
+                         int slot0, cudaStream_t s);
+// Rebuild the active list `list_parity` from the bitmap (same grid as the step).
+cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStream_t s);
 cudaError_t launch_zero_slots(const Engine &e, int slot0, long long n, cudaStream_t s);
 cudaError_t launch_scatter_field(const Engine &e, const float *packed, long long n, int slot0,
                                  int now_half, cudaStream_t s);
-cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s);
+// Tensor maps over the pool viewed as [2 * boxes][z][y][x] floats: boxes of
+// one x-face column block (4 x 8 x 8) and of one y-face row block (8 x 1 x 8).
+struct PoolMaps {
+    CUtensorMap xface;
+    CUtensorMap yface;
+};
+bool make_pool_maps(float *pool, int n_slots, PoolMaps *out);
+cudaError_t launch_step(const Engine &e, const PoolMaps &maps, int grid, cudaStream_t s);
 int step_grid_size(int device);
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,

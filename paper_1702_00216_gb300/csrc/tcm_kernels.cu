@@ -149,115 +149,242 @@ __device__ __forceinline__ float seg_max(float v)
     return v;
 }
 
-__device__ __forceinline__ const float4 *half4(const Engine &E, int slot, int half)
+
+// ---------------------------------------------------------------------------
+// Asynchronous bulk copies (TMA engine) and mbarriers.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long TMA_TIMEOUT_NS = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
 {
-    return reinterpret_cast<const float4 *>(E.phi + ((size_t)slot * 2 + half) * BVOL);
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for one phase of an mbarrier.  On timeout: record
+// ERR_TIMEOUT, wait once more (bounded) for the copies still in flight, and
+// report failure so the caller stops using the buffer.
+__device__ bool mbar_wait(unsigned bar, unsigned parity, EngineState *st)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > TMA_TIMEOUT_NS) {
+            atomicOr(&st->err, ERR_TIMEOUT);
+            const unsigned long long t1 = globaltimer();
+            while (!mbar_try_wait(bar, parity) && globaltimer() - t1 < TMA_TIMEOUT_NS) {
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
+// Global -> shared bulk copy; completion is counted on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Global -> shared tensor copy of one box of a 4-D tensor map (coordinates
+// innermost first); completion is counted on the mbarrier.
+__device__ __forceinline__ void tensor_g2s(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                           unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Orders this thread's earlier generic accesses to shared memory before
+// later asynchronous-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ WorkItem load_item(const WorkItem *L, int i)
+{
+    const int4 *p = reinterpret_cast<const int4 *>(L + i);
+    const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    WorkItem w;
+    w.slot = a.x;
+    w.brick = a.y;
+    w.kslab = a.z;
+    w.kscal = __int_as_float(a.w);
+    w.flags = (unsigned)b.x;
+    w.nb[0] = b.y;
+    w.nb[1] = b.z;
+    w.nb[2] = b.w;
+    w.nb[3] = c.x;
+    w.nb[4] = c.y;
+    w.nb[5] = c.z;
+    w.nh = c.w;
+    return w;
+}
+
+__device__ __forceinline__ const float *half_ptr(const Engine &E, int slot, int half)
+{
+    return E.phi + ((size_t)slot * 2 + half) * BVOL;
 }
 
 // ---------------------------------------------------------------------------
-// P1: one brick per TPB-lane segment.  Every lane of the warp calls this (with
-// valid = false on a missing brick) so the shuffles see full warps.
+// P1 staging: the lanes of one brick segment issue the bulk copies of its
+// phi^n, phi^{n-1}, k and the z/y boundary layers of its neighbours into
+// `sb`; lane 0 of the warp has already announced the byte count.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void p1_brick(const Engine &E, int slot, bool valid, int t,
-                                         unsigned long long &cells)
+__device__ __forceinline__ unsigned stage_bytes(const WorkItem &w, bool valid)
+{
+    if (!valid) return 0u;
+    unsigned b = 2u * 2048u + (w.kslab >= 0 ? 2048u : 0u);
+    b += (w.nb[0] >= 0 ? 1024u : 0u) + (w.nb[1] >= 0 ? 1024u : 0u);
+    b += (w.nb[2] >= 0 ? 256u : 0u) + (w.nb[3] >= 0 ? 256u : 0u);
+    b += (w.nb[4] >= 0 ? 256u : 0u) + (w.nb[5] >= 0 ? 256u : 0u);
+    return b;
+}
+
+// Lanes 0..8 of a brick segment each issue one copy into the stage at sb:
+// phi^n, phi^{n-1}, k (bulk, 2 KiB each), the boundary planes of z- and z+
+// (bulk, 256 B), the boundary rows of y- and y+ (one tensor box 8x1x8 each)
+// and the boundary columns of x- and x+ (one tensor box 4x8x8 each, whose
+// last / first column is the face).  Tensor x coordinates are 0 or 4, so
+// every box starts on a 16-byte boundary.
+__device__ __forceinline__ void stage_issue(const Engine &E, const PoolMaps &maps, const WorkItem &w, bool valid,
+                                            int nh, unsigned sb, unsigned bar, int t)
+{
+    if (!valid) return;
+    switch (t) {
+    case 0: bulk_g2s(sb + OFF_P, half_ptr(E, w.slot, nh), 2048u, bar); break;
+    case 1: bulk_g2s(sb + OFF_M, half_ptr(E, w.slot, nh ^ 1), 2048u, bar); break;
+    case 2:
+        if (w.kslab >= 0) bulk_g2s(sb + OFF_K, E.kslabs + (size_t)w.kslab * BVOL, 2048u, bar);
+        break;
+    case 3:
+        if (w.nb[4] >= 0) bulk_g2s(sb + OFF_ZM, half_ptr(E, w.nb[4], nh) + (BZ - 1) * BY * BX, 256u, bar);
+        break;
+    case 4:
+        if (w.nb[5] >= 0) bulk_g2s(sb + OFF_ZP, half_ptr(E, w.nb[5], nh), 256u, bar);
+        break;
+    case 5:
+        if (w.nb[2] >= 0) tensor_g2s(sb + OFF_YM, &maps.yface, 0, BY - 1, 0, w.nb[2] * 2 + nh, bar);
+        break;
+    case 6:
+        if (w.nb[3] >= 0) tensor_g2s(sb + OFF_YP, &maps.yface, 0, 0, 0, w.nb[3] * 2 + nh, bar);
+        break;
+    case 7:
+        if (w.nb[0] >= 0) tensor_g2s(sb + OFF_XM, &maps.xface, BX - 4, 0, 0, w.nb[0] * 2 + nh, bar);
+        break;
+    case 8:
+        if (w.nb[1] >= 0) tensor_g2s(sb + OFF_XP, &maps.xface, 0, 0, 0, w.nb[1] * 2 + nh, bar);
+        break;
+    default: break;
+    }
+}
+
+// Merge a lane's running max |phi^{n+1}| into its sim's domain maximum.  The
+// step being computed has phi^n in half nh, so its maximum lives in gmax[nh].
+__device__ __forceinline__ void flush_gmax(const Engine &E, float gacc, int gsim, int nh)
+{
+    if (gsim >= 0 && gacc > 0.f) atomicMax(&E.sims[gsim].gmax[nh], __float_as_uint(gacc));
+}
+
+// ---------------------------------------------------------------------------
+// P1 compute: Eq. 3 on one brick from its staged copy.  Every lane of the
+// warp calls this (valid = false on a missing brick) so shuffles see full
+// warps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, bool valid, int t,
+                                           const unsigned char *sb, unsigned long long &cells, float &gacc,
+                                           int &gsim, int &gnh)
 {
     const int x4 = t % XQ;
     const int y = t / XQ;
-    SlotMeta m;
-    if (valid) {
-        m = load_meta(E.meta + slot);
-    } else {
-        m.brick = 0;
-        m.kslab = -1;
-        m.kscal = 0.f;
-        m.flags = 0u;
-    }
-    const int sim = (int)(m.flags >> 16);
+    const int sim = valid ? (int)(w.flags >> 16) : 0;
     SimDev *S = E.sims + sim;
-    const int mx = S->mx, my = S->my, mz = S->mz;
-    const int nx = S->nx, ny = S->ny, nz = S->nz;
-    const long long bb = S->brick_base;
-    const long long step = __ldcg(&S->step);
-    const int b = m.brick;
+    const int mx = __ldg(&S->mx), my = __ldg(&S->my);
+    const int nx = __ldg(&S->nx), ny = __ldg(&S->ny), nz = __ldg(&S->nz);
+    const int nh = w.nh;
+    const int b = w.brick;
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
+    const float4 *P4 = reinterpret_cast<const float4 *>(sb + OFF_P);
+    const float4 *M4 = reinterpret_cast<const float4 *>(sb + OFF_M);
+    const float4 *K4 = reinterpret_cast<const float4 *>(sb + OFF_K);
+    const bool het = w.kslab >= 0;
+    const bool hzm = w.nb[4] >= 0, hzp = w.nb[5] >= 0;
+    // lanes on the y = 0 / y = BY-1 rows take their y neighbour from the
+    // staged boundary row of y- / y+ (zero if that neighbour has no box)
+    const bool yedge = (y == 0 && w.nb[2] >= 0) || (y == BY - 1 && w.nb[3] >= 0);
+    const float4 *YH4 = reinterpret_cast<const float4 *>(sb + (y == 0 ? OFF_YM : OFF_YP)) + x4;
+    // lanes on the x = 0 / x = BX-1 columns take their x neighbour from the
+    // staged 4-wide column block of x- (its last column) / x+ (its first)
+    const bool xedge = (x4 == 0 && w.nb[0] >= 0) || (x4 == XQ - 1 && w.nb[1] >= 0);
+    const float *XH = reinterpret_cast<const float *>(sb + (x4 == 0 ? OFF_XM : OFF_XP)) + y * 4 +
+                      (x4 == 0 ? 3 : 0);
 
-    // Cell2box of the six face neighbours (lanes 0..5 look one up each).
-    int nslot = -3;
-    if (valid && t < 6) {
-        const int ax = cx + (t == 0 ? -1 : (t == 1 ? 1 : 0));
-        const int ay = cy + (t == 2 ? -1 : (t == 3 ? 1 : 0));
-        const int az = cz + (t == 4 ? -1 : (t == 5 ? 1 : 0));
-        if (ax >= 0 && ay >= 0 && az >= 0 && ax < mx && ay < my && az < mz)
-            nslot = E.slot_of_brick[bb + ((long long)az * my + ay) * mx + ax];
+    // Stage -> registers: all planes first, so the shared loads overlap.
+    float4 P[BZ], M[BZ], K[BZ], YH[BZ];
+    float xf[BZ];
+#pragma unroll
+    for (int z = 0; z < BZ; ++z) {
+        P[z] = P4[z * TPB + t];
+        M[z] = M4[z * TPB + t];
+        K[z] = het ? K4[z * TPB + t] : make_float4(w.kscal, w.kscal, w.kscal, w.kscal);
+        YH[z] = yedge ? YH4[z * XQ] : f4zero();
+        xf[z] = xedge ? XH[z * BY * 4] : 0.f;
     }
-    const int s_xm = __shfl_sync(FULL, nslot, 0, TPB);
-    const int s_xp = __shfl_sync(FULL, nslot, 1, TPB);
-    const int s_ym = __shfl_sync(FULL, nslot, 2, TPB);
-    const int s_yp = __shfl_sync(FULL, nslot, 3, TPB);
-    const int s_zm = __shfl_sync(FULL, nslot, 4, TPB);
-    const int s_zp = __shfl_sync(FULL, nslot, 5, TPB);
+    const float4 Zm = hzm ? reinterpret_cast<const float4 *>(sb + OFF_ZM)[t] : f4zero();
+    const float4 Zp = hzp ? reinterpret_cast<const float4 *>(sb + OFF_ZP)[t] : f4zero();
 
-    const int nh = (int)(step & 1);
-    float4 P[BZ], Q[BZ], K[BZ];
-    if (valid) {
-        const float4 *now4 = half4(E, slot, nh);
-        const float4 *prv4 = half4(E, slot, nh ^ 1);
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) {
-            P[z] = __ldg(now4 + z * TPB + t);
-            Q[z] = __ldcs(prv4 + z * TPB + t);
-        }
-        if (m.kslab >= 0) {
-            const float4 *k4 = reinterpret_cast<const float4 *>(E.kslabs + (size_t)m.kslab * BVOL);
-#pragma unroll
-            for (int z = 0; z < BZ; ++z) K[z] = __ldg(k4 + z * TPB + t);
-        } else {
-#pragma unroll
-            for (int z = 0; z < BZ; ++z) K[z] = make_float4(m.kscal, m.kscal, m.kscal, m.kscal);
-        }
-    } else {
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) {
-            P[z] = f4zero();
-            Q[z] = f4zero();
-            K[z] = f4zero();
-        }
-    }
-    // Halo ("padding the box ... by the boundaries of its relevant neighbors").
-    float4 Zm = f4zero(), Zp = f4zero();
-    if (s_zm >= 0) Zm = __ldg(half4(E, s_zm, nh) + (BZ - 1) * TPB + t);
-    if (s_zp >= 0) Zp = __ldg(half4(E, s_zp, nh) + t);
-    const int ys = (y == 0) ? s_ym : ((y == BY - 1) ? s_yp : -1);
-    const int yrow = (y == 0) ? BY - 1 : 0;
-    const int xs = (x4 == 0) ? s_xm : ((x4 == XQ - 1) ? s_xp : -1);
-    const int xcol = (x4 == 0) ? BX - 1 : 0;
-    float4 Yh[BZ];
-    float Xh[BZ];
-    if (ys >= 0) {
-        const float4 *yb = half4(E, ys, nh) + yrow * XQ + x4;
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) Yh[z] = __ldg(yb + z * TPB);
-    } else {
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) Yh[z] = f4zero();
-    }
-    if (xs >= 0) {
-        const float *xb = E.phi + ((size_t)xs * 2 + nh) * BVOL + y * BX + xcol;
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) Xh[z] = __ldg(xb + z * BY * BX);
-    } else {
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) Xh[z] = 0.f;
-    }
+    const float alpha = __ldg(&S->alpha);
+    const bool decay = (w.flags & SD_MASK) != 0u;
+    const bool ragged = (cx + 1) * BX > nx || (cy + 1) * BY > ny || (cz + 1) * BZ > nz;
+    const int gx0 = cx * BX + 4 * x4, gy = cy * BY + y, gz0 = cz * BZ;
+    float4 *out = reinterpret_cast<float4 *>(E.phi + ((size_t)w.slot * 2 + (nh ^ 1)) * BVOL);
+    const bool src = valid && (w.flags & FLAG_HAS_SRC);
+    const long long step = src ? __ldcg(&S->step) : 0;
 
-    // Eq. 3, plane by plane.
+    float mc = 0.f, qm = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 0.f;
 #pragma unroll
     for (int z = 0; z < BZ; ++z) {
         const float4 p = P[z];
+        // x neighbours inside the brick through shuffles, x faces from registers
         const float lw = __shfl_up_sync(FULL, p.w, 1, TPB);
         const float rx = __shfl_down_sync(FULL, p.x, 1, TPB);
-        const float xm0 = (x4 == 0) ? Xh[z] : lw;
-        const float xp3 = (x4 == XQ - 1) ? Xh[z] : rx;
+        const float xm0 = (x4 == 0) ? xf[z] : lw;
+        const float xp3 = (x4 == XQ - 1) ? xf[z] : rx;
+        // y neighbours inside the brick through shuffles
         float4 ym, yp;
         ym.x = __shfl_up_sync(FULL, p.x, XQ, TPB);
         ym.y = __shfl_up_sync(FULL, p.y, XQ, TPB);
@@ -267,71 +394,47 @@ __device__ __forceinline__ void p1_brick(const Engine &E, int slot, bool valid, 
         yp.y = __shfl_down_sync(FULL, p.y, XQ, TPB);
         yp.z = __shfl_down_sync(FULL, p.z, XQ, TPB);
         yp.w = __shfl_down_sync(FULL, p.w, XQ, TPB);
-        if (y == 0) ym = Yh[z];
-        if (y == BY - 1) yp = Yh[z];
+        if (y == 0) ym = YH[z];
+        if (y == BY - 1) yp = YH[z];
         const float4 zm = (z > 0) ? P[z > 0 ? z - 1 : 0] : Zm;
         const float4 zp = (z < BZ - 1) ? P[z < BZ - 1 ? z + 1 : 0] : Zp;
-        Q[z] = eq3v(p, Q[z], K[z], xm0, xp3, ym, yp, zm, zp);
-    }
-
-    // Source insertion in box coordinates.
-    if (valid && (m.flags & FLAG_HAS_SRC)) {
-        for (int s = S->src_begin; s < S->src_end; ++s) {
-            const SrcDev sd = E.src[s];
-            if (sd.brick != b) continue;
-            const long long tt = step - sd.start;
-            if (tt < 0 || tt >= sd.len) continue;
-            const int lx = sd.local % BX, ly = (sd.local / BX) % BY, lz = sd.local / (BX * BY);
-            if (ly != y || (lx >> 2) != x4) continue;
-            const float w = E.wave[sd.w_off + tt];
-#pragma unroll
-            for (int z = 0; z < BZ; ++z)
-                if (z == lz) add_comp(Q[z], lx & 3, w);
+        float4 q = eq3v(p, M[z], K[z], xm0, xp3, ym, yp, zm, zp);
+        if (src) {
+            // Source insertion in box coordinates: every sample of this
+            // plane, in source order.
+            for (int s = S->src_begin; s < S->src_end; ++s) {
+                const SrcDev sd = E.src[s];
+                if (sd.brick != b) continue;
+                const long long tt = step - sd.start;
+                if (tt < 0 || tt >= sd.len) continue;
+                const int lx = sd.local % BX, ly = (sd.local / BX) % BY, lz = sd.local / (BX * BY);
+                if (lz != z || ly != y || (lx >> 2) != x4) continue;
+                add_comp(q, lx & 3, E.wave[sd.w_off + tt]);
+            }
         }
-    }
-    // Time-domain shut-down (Eq. 6).
-    if ((m.flags & SD_MASK) != 0u) {
-        const float a = S->alpha;
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) {
-            Q[z].x = __fmul_rn(a, Q[z].x);
-            Q[z].y = __fmul_rn(a, Q[z].y);
-            Q[z].z = __fmul_rn(a, Q[z].z);
-            Q[z].w = __fmul_rn(a, Q[z].w);
+        if (decay) {
+            q.x = __fmul_rn(alpha, q.x);
+            q.y = __fmul_rn(alpha, q.y);
+            q.z = __fmul_rn(alpha, q.z);
+            q.w = __fmul_rn(alpha, q.w);
         }
-    }
-    // Nodes outside the domain stay zero.
-    const int gx0 = cx * BX + 4 * x4, gy = cy * BY + y, gz0 = cz * BZ;
-    if ((cx + 1) * BX > nx || (cy + 1) * BY > ny || (cz + 1) * BZ > nz) {
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) {
+        if (ragged) {
             const bool rowin = gy < ny && gz0 + z < nz;
-            if (!rowin || gx0 + 0 >= nx) Q[z].x = 0.f;
-            if (!rowin || gx0 + 1 >= nx) Q[z].y = 0.f;
-            if (!rowin || gx0 + 2 >= nx) Q[z].z = 0.f;
-            if (!rowin || gx0 + 3 >= nx) Q[z].w = 0.f;
+            if (!rowin || gx0 + 0 >= nx) q.x = 0.f;
+            if (!rowin || gx0 + 1 >= nx) q.y = 0.f;
+            if (!rowin || gx0 + 2 >= nx) q.z = 0.f;
+            if (!rowin || gx0 + 3 >= nx) q.w = 0.f;
         }
-    }
-    if (valid) {
-        float4 *prv4 = reinterpret_cast<float4 *>(E.phi + ((size_t)slot * 2 + (nh ^ 1)) * BVOL);
-#pragma unroll
-        for (int z = 0; z < BZ; ++z) prv4[z * TPB + t] = Q[z];
-    }
-
-    // Max_cell_val, face maxima, domain maximum.
-    float mc = 0.f, qm = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 0.f;
-#pragma unroll
-    for (int z = 0; z < BZ; ++z) {
-        const float mq = max4abs(Q[z]);
-        const float mp = max4abs(P[z]);
+        if (valid) __stcg(out + z * TPB + t, q);
+        const float mq = max4abs(q);
         qm = fmaxf(qm, mq);
-        mc = fmaxf(mc, fmaxf(mq, mp));
+        mc = fmaxf(mc, fmaxf(mq, max4abs(p)));
         if (z == 0) f4 = mq;
         if (z == BZ - 1) f5 = mq;
-        if (y == 0) f2 = fmaxf(f2, mq);
-        if (y == BY - 1) f3 = fmaxf(f3, mq);
-        if (x4 == 0) f0 = fmaxf(f0, fabsf(Q[z].x));
-        if (x4 == XQ - 1) f1 = fmaxf(f1, fabsf(Q[z].w));
+        f2 = fmaxf(f2, y == 0 ? mq : 0.f);
+        f3 = fmaxf(f3, y == BY - 1 ? mq : 0.f);
+        f0 = fmaxf(f0, x4 == 0 ? fabsf(q.x) : 0.f);
+        f1 = fmaxf(f1, x4 == XQ - 1 ? fabsf(q.w) : 0.f);
     }
     mc = seg_max(mc);
     qm = seg_max(qm);
@@ -341,18 +444,21 @@ __device__ __forceinline__ void p1_brick(const Engine &E, int slot, bool valid, 
     f3 = seg_max(f3);
     f4 = seg_max(f4);
     f5 = seg_max(f5);
-    if (valid) {
-        if (t < 6) E.nbr[(size_t)slot * 8 + t] = nslot;
-        if (t == 0) {
-            float4 *r = reinterpret_cast<float4 *>(E.rec + (size_t)slot * 8);
-            r[0] = make_float4(f0, f1, f2, f3);
-            r[1] = make_float4(f4, f5, mc, qm);
-            unsigned *gp = &S->gmax[step & 1];
-            const unsigned bits = __float_as_uint(qm);
-            if (bits > __ldcg(gp)) atomicMax(gp, bits);
-            const int ex = min(BX, nx - cx * BX), ey = min(BY, ny - cy * BY), ez = min(BZ, nz - cz * BZ);
-            cells += (unsigned long long)(ex * ey * ez);
+    if (valid && t == 0) {
+        float4 *r = reinterpret_cast<float4 *>(E.rec + (size_t)w.slot * 8);
+        __stcg(r, make_float4(f0, f1, f2, f3));
+        __stcg(r + 1, make_float4(f4, f5, mc, qm));
+        // running domain maximum of this lane's sim, flushed when the sim
+        // (or its step parity) changes
+        if (sim != gsim || nh != gnh) {
+            flush_gmax(E, gacc, gsim, gnh);
+            gsim = sim;
+            gnh = nh;
+            gacc = 0.f;
         }
+        gacc = fmaxf(gacc, qm);
+        const int ex = min(BX, nx - cx * BX), ey = min(BY, ny - cy * BY), ez = min(BZ, nz - cz * BZ);
+        cells += (unsigned long long)(ex * ey * ez);
     }
 }
 
@@ -447,21 +553,95 @@ __device__ long long block_sum(long long v)
     return r;
 }
 
+// Work item of the boxed global brick g (state after the update procedure).
+// The sim is found from g (brick ranges), so the box, its metadata and the
+// six neighbour lookups are independent loads.
+__device__ __forceinline__ void build_item(const Engine &E, long long g, WorkItem *out, int step_ahead)
+{
+    int si = 0;
+    for (int s = 1; s < E.n_sims; ++s)
+        if (g >= __ldg(&E.sims[s].brick_base)) si = s;
+    const SimDev *S = E.sims + si;
+    const int mx = __ldg(&S->mx), my = __ldg(&S->my), mz = __ldg(&S->mz);
+    const long long bb = __ldg(&S->brick_base);
+    const int b = (int)(g - bb);
+    const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
+    const int slot = __ldcg(E.slot_of_brick + g);
+    int nb[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+        const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
+        const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
+        nb[f] = (ax >= 0 && ay >= 0 && az >= 0 && ax < mx && ay < my && az < mz)
+                    ? __ldcg(E.slot_of_brick + bb + ((long long)az * my + ay) * mx + ax)
+                    : -3;
+    }
+    const SlotMeta m = load_meta(E.meta + slot);
+    // The item is processed by the next launch, which steps from phi^{n+1}.
+    const int nh = (int)((__ldcg(&S->step) + step_ahead) & 1);
+    int4 *p = reinterpret_cast<int4 *>(out);
+    p[0] = make_int4(slot, b, m.kslab, __float_as_int(m.kscal));
+    p[1] = make_int4((int)m.flags, nb[0], nb[1], nb[2]);
+    p[2] = make_int4(nb[3], nb[4], nb[5], nh);
+}
+
+// Active list from the bitmap, in brick order: this block's word range gets
+// positions after the active bricks of all earlier ranges (per-range counts
+// are kept by the update procedure); ballot/popc + block scan place each set
+// bit, then the block builds the work items of its positions.
+__device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int step_ahead)
+{
+    long long before = 0, all = 0;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) {
+        const int v = __ldcg(E.blocktot + j);
+        all += v;
+        if (j < (int)blockIdx.x) before += v;
+    }
+    before = block_sum(before);
+    all = block_sum(all);
+    const long long w0 = (long long)blockIdx.x * E.words_per_block;
+    const long long w1 = min(w0 + E.words_per_block, E.n_words);
+    int off = (int)before;
+    for (long long wb = w0; wb < w1; wb += BLOCK) {
+        const long long w = wb + threadIdx.x;
+        unsigned bits = w < w1 ? __ldcg(E.bitmap + w) : 0u;
+        int total;
+        int pos = off + block_excl_scan(__popc(bits), &total);
+        while (bits) {
+            const int bit = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (pos < E.n_slots) E.listids[pos] = (int)(w * 32 + bit);
+            ++pos;
+        }
+        off += total;
+    }
+    __syncthreads();
+    const int end = min(off, E.n_slots);
+    for (int pos = (int)before + threadIdx.x; pos < end; pos += BLOCK)
+        build_item(E, (long long)E.listids[pos], Lout + pos, step_ahead);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_out = (int)all;
+}
+
 // ---------------------------------------------------------------------------
 // The step kernel.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BLOCK, 2) k_step(Engine E)
+__global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, const __grid_constant__ PoolMaps maps)
 {
+    extern __shared__ __align__(128) unsigned char dsmem[];
+    __shared__ __align__(8) unsigned long long s_bar[P1_WARPS][2];
     EngineState *st = E.st;
     const int cur = __ldcg(&st->list_parity);
-    const int *L = cur ? E.list1 : E.list0;
-    int *Lnext = cur ? E.list0 : E.list1;
+    const WorkItem *L = cur ? E.items1 : E.items0;
+    WorkItem *Lnext = cur ? E.items0 : E.items1;
     const int nact = __ldcg(&st->n_active[cur]);
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const int gwarp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * BLOCK) >> 5;
 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->t_start = globaltimer();
         // Boxes released last step were pushed above max(free_top, 0).
         const int ft = max(__ldcg(&st->free_top), 0) + __ldcg(&st->n_retired);
         st->free_top = ft;
@@ -472,28 +652,97 @@ __global__ void __launch_bounds__(BLOCK, 2) k_step(Engine E)
     // ---- P1: time stepping of every active brick -------------------------
     {
         unsigned long long cells = 0;
+        float gacc = 0.f;
+        int gsim = -1;
+        int gnh = 0;
         const int seg = lane / TPB;
         const int t = lane % TPB;
-        for (int base = gwarp * BRICKS_PER_WARP; base < nact; base += nwarps * BRICKS_PER_WARP) {
-            const int i = base + seg;
-            const bool valid = i < nact;
-            const int slot = valid ? __ldg(L + i) : 0;
-            p1_brick(E, slot, valid, t, cells);
+        // tensor copies need 128-byte aligned destinations: align the base
+        unsigned char *sbase = dsmem + ((128u - (smem_u32(dsmem) & 127u)) & 127u);
+        unsigned char *wsm = sbase + wib * WARP_SMEM;
+        const unsigned bar[2] = {smem_u32(&s_bar[wib][0]), smem_u32(&s_bar[wib][1])};
+        if (lane == 0) {
+            mbar_init(bar[0], 1);
+            mbar_init(bar[1], 1);
+            mbar_fence_init();
         }
+        __syncwarp();
+        const int npairs = (nact + BRICKS_PER_WARP - 1) / BRICKS_PER_WARP;
+        int pr = gwarp;
+        if (pr < npairs) {
+            unsigned phase = 0u;
+            int stage = 0;
+            // stage the first group of bricks
+            int i = pr * BRICKS_PER_WARP + seg;
+            bool v_cur = i < nact;
+            WorkItem w_cur = load_item(L, v_cur ? i : 0);
+            const int nh_cur = w_cur.nh;
+            {
+                unsigned bytes = stage_bytes(w_cur, v_cur);
+                bytes += __shfl_down_sync(FULL, bytes, TPB);
+                if (lane == 0) mbar_arrive_expect_tx(bar[0], bytes);
+                __syncwarp();
+                stage_issue(E, maps, w_cur, v_cur, nh_cur, smem_u32(wsm + seg * BRICK_SMEM), bar[0], t);
+            }
+            // item of the following group, loaded one iteration ahead
+            int pn = pr + nwarps;
+            int in = pn * BRICKS_PER_WARP + seg;
+            bool v_nxt = pn < npairs && in < nact;
+            WorkItem w_nxt = load_item(L, v_nxt ? in : 0);
+            while (true) {
+                const bool has_next = pn < npairs;
+                int nh_nxt = 0;
+                WorkItem w_nn;
+                bool v_nn = false;
+                int pnn = pn + nwarps;
+                if (has_next) {
+                    nh_nxt = w_nxt.nh;
+                    unsigned bytes = stage_bytes(w_nxt, v_nxt);
+                    bytes += __shfl_down_sync(FULL, bytes, TPB);
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_expect_tx(bar[stage ^ 1], bytes);
+                    __syncwarp();
+                    stage_issue(E, maps, w_nxt, v_nxt, nh_nxt,
+                                smem_u32(wsm + (stage ^ 1) * STAGE_SMEM + seg * BRICK_SMEM), bar[stage ^ 1], t);
+                    const int inn = pnn * BRICKS_PER_WARP + seg;
+                    v_nn = pnn < npairs && inn < nact;
+                    w_nn = load_item(L, v_nn ? inn : 0);
+                }
+                if (!mbar_wait(bar[stage], (phase >> stage) & 1u, st)) {
+                    // also drain the copies issued for the next group (bounded)
+                    if (has_next) mbar_wait(bar[stage ^ 1], (phase >> (stage ^ 1)) & 1u, st);
+                    break;
+                }
+                phase ^= 1u << stage;
+                p1_compute(E, w_cur, v_cur, t, wsm + stage * STAGE_SMEM + seg * BRICK_SMEM, cells, gacc, gsim,
+                           gnh);
+                __syncwarp();
+                if (!has_next) break;
+                w_cur = w_nxt;
+                v_cur = v_nxt;
+                stage ^= 1;
+                pn = pnn;
+                w_nxt = w_nn;
+                v_nxt = v_nn;
+            }
+        }
+        flush_gmax(E, gacc, gsim, gnh);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(FULL, cells, o);
         if (lane == 0 && cells) atomicAdd(&st->updates, cells);
     }
     if (!grid_barrier(st)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_p1 = globaltimer();
 
     // ---- P2: updating active cells ---------------------------------------
     {
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
         for (int i = gtid; i < nact; i += nthr) {
-            const int slot = __ldg(L + i);
-            const SlotMeta m = load_meta(E.meta + slot);
-            const int sim = (int)(m.flags >> 16);
+            const WorkItem w = load_item(L, i);
+            const int slot = w.slot;
+            const int sim = (int)(w.flags >> 16);
             SimDev *S = E.sims + sim;
             if (S->dense) continue;
             const long long step = __ldcg(&S->step);
@@ -501,21 +750,18 @@ __global__ void __launch_bounds__(BLOCK, 2) k_step(Engine E)
             const double thr = S->thr_mode == 1 ? S->tau * G : S->tau;
             const float4 r0 = __ldcg(reinterpret_cast<const float4 *>(E.rec + (size_t)slot * 8));
             const float4 r1 = __ldcg(reinterpret_cast<const float4 *>(E.rec + (size_t)slot * 8) + 1);
-            const int4 n0 = __ldcg(reinterpret_cast<const int4 *>(E.nbr + (size_t)slot * 8));
-            const int4 n1 = __ldcg(reinterpret_cast<const int4 *>(E.nbr + (size_t)slot * 8) + 1);
             const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
-            const int ns[6] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y};
             bool hot = (double)r1.z > thr;
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
-                if (!hot && ns[f] >= 0) {
-                    const float v = __ldcg(E.rec + (size_t)ns[f] * 8 + (f ^ 1));
+                if (!hot && w.nb[f] >= 0) {
+                    const float v = __ldcg(E.rec + (size_t)w.nb[f] * 8 + (f ^ 1));
                     if ((double)v > thr) hot = true;
                 }
             }
-            const int b = m.brick;
-            if (!hot && (m.flags & FLAG_HAS_SRC) && forced_at(E, S, b, step + 1)) hot = true;
-            unsigned sd = m.flags & SD_MASK;
+            const int b = w.brick;
+            if (!hot && (w.flags & FLAG_HAS_SRC) && forced_at(E, S, b, step + 1)) hot = true;
+            unsigned sd = w.flags & SD_MASK;
             bool keep;
             if (hot) {
                 sd = 0;
@@ -531,8 +777,8 @@ __global__ void __launch_bounds__(BLOCK, 2) k_step(Engine E)
             }
             const long long g = S->brick_base + b;
             if (keep) {
-                const unsigned nf = (m.flags & ~SD_MASK) | sd;
-                if (nf != m.flags) E.meta[slot].flags = nf;
+                const unsigned nf = (w.flags & ~SD_MASK) | sd;
+                if (nf != w.flags) E.meta[slot].flags = nf;
             } else {
                 atomicExch(E.slot_of_brick + g, -1);
                 atomicAnd(E.bitmap + (g >> 5), ~(1u << (unsigned)(g & 31)));
@@ -544,7 +790,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_step(Engine E)
             const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
-                if (ns[f] == -1 && (double)fc[f] > thr) {
+                if (w.nb[f] == -1 && (double)fc[f] > thr) {
                     const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
                     const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
                     const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
@@ -564,6 +810,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_step(Engine E)
         }
     }
     if (!grid_barrier(st)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_p2 = globaltimer();
 
     // ---- P3: box recycling and compaction of the active list -------------
     {
@@ -577,44 +824,38 @@ __global__ void __launch_bounds__(BLOCK, 2) k_step(Engine E)
         const int n_ret = __ldcg(&st->n_retired);
         const int base = max(__ldcg(&st->free_top), 0);
         for (int i = gtid; i < n_ret; i += nthr) E.free_stack[base + i] = __ldcg(E.retired + i);
-
-        // Offset of this block's bitmap range = active bricks in earlier ranges.
-        long long before = 0, all = 0;
-        for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) {
-            const int v = __ldcg(E.blocktot + j);
-            all += v;
-            if (j < (int)blockIdx.x) before += v;
-        }
-        before = block_sum(before);
-        all = block_sum(all);
-        const long long w0 = (long long)blockIdx.x * E.words_per_block;
-        const long long w1 = min(w0 + E.words_per_block, E.n_words);
-        int off = (int)before;
-        for (long long wb = w0; wb < w1; wb += BLOCK) {
-            const long long w = wb + threadIdx.x;
-            unsigned bits = w < w1 ? __ldcg(E.bitmap + w) : 0u;
-            int total;
-            int pos = off + block_excl_scan(__popc(bits), &total);
-            while (bits) {
-                const int bit = __ffs(bits) - 1;
-                bits &= bits - 1;
-                if (pos < E.n_slots) Lnext[pos] = __ldcg(E.slot_of_brick + (w * 32 + bit));
-                ++pos;
+        compact_list(E, Lnext, &st->n_active[cur ^ 1], 1);
+        // The last block to finish advances the step: every block has read
+        // the step counters by then.
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&st->p3_done, 1u) == gridDim.x - 1) {
+                __threadfence();
+                for (int s = 0; s < E.n_sims; ++s) {
+                    SimDev *S = E.sims + s;
+                    const long long n = __ldcg(&S->step);
+                    S->gmax[(n + 1) & 1] = 0u;
+                    S->step = n + 1;
+                }
+                st->list_parity = cur ^ 1;
+                st->launches += 1;
+                st->p3_done = 0u;
+                const unsigned long long t3 = globaltimer();
+                const unsigned long long t0 = __ldcg(&st->t_start), t1 = __ldcg(&st->t_p1),
+                                         t2 = __ldcg(&st->t_p2);
+                st->phase_ns[0] += t1 - t0;
+                st->phase_ns[1] += t2 - t1;
+                st->phase_ns[2] += t3 - t2;
             }
-            off += total;
-        }
-        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) st->n_active[cur ^ 1] = (int)all;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            for (int s = 0; s < E.n_sims; ++s) {
-                SimDev *S = E.sims + s;
-                const long long n = S->step;
-                S->gmax[(n + 1) & 1] = 0u;
-                S->step = n + 1;
-            }
-            st->list_parity = cur ^ 1;
-            st->launches += 1;
         }
     }
+}
+
+// Build active list `parity` from the bitmap (start of a simulation).
+__global__ void __launch_bounds__(BLOCK, 1) k_compact(Engine E, int parity)
+{
+    compact_list(E, parity ? E.items1 : E.items0, &E.st->n_active[parity], 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -737,11 +978,10 @@ __global__ void k_iota_desc(int *a, int n, int first)
 }
 
 // Box the initial bricks: bricks[i] (or brick i when bricks == nullptr) gets
-// box slot0 + i and list position slot0 + i.
-__global__ void k_prime(Engine E, int sim, const long long *bricks, long long n, int slot0, int parity)
+// box slot0 + i; the active list is then built from the bitmap (k_compact).
+__global__ void k_prime(Engine E, int sim, const long long *bricks, long long n, int slot0)
 {
     SimDev *S = E.sims + sim;
-    int *L = parity ? E.list1 : E.list0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int b = bricks ? (int)bricks[i] : (int)i;
         const int slot = slot0 + (int)i;
@@ -755,7 +995,6 @@ __global__ void k_prime(Engine E, int sim, const long long *bricks, long long n,
         store_meta(E.meta + slot, m);
         atomicOr(E.bitmap + (g >> 5), 1u << (unsigned)(g & 31));
         atomicAdd(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
-        L[slot] = slot;
     }
 }
 
@@ -814,12 +1053,12 @@ __device__ __forceinline__ double prev_at(const Engine &E, const SimDev *S, int 
 __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *out)
 {
     const SimDev *S = E.sims + sim;
-    const int *L = parity ? E.list1 : E.list0;
+    const WorkItem *L = parity ? E.items1 : E.items0;
     const long long n = (long long)E.st->n_active[parity] * BVOL;
     const int ph = now_half ^ 1;
     double acc = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int slot = L[i / BVOL];
+        const int slot = L[i / BVOL].slot;
         const int e = (int)(i % BVOL);
         const SlotMeta m = load_meta(E.meta + slot);
         if ((int)(m.flags >> 16) != sim) continue;
@@ -844,10 +1083,10 @@ __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *ou
 
 __global__ void k_active_bricks(Engine E, int parity, long long *ids, unsigned long long *cells)
 {
-    const int *L = parity ? E.list1 : E.list0;
+    const WorkItem *L = parity ? E.items1 : E.items0;
     const int n = E.st->n_active[parity];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const SlotMeta m = load_meta(E.meta + L[i]);
+        const SlotMeta m = load_meta(E.meta + L[i].slot);
         const SimDev *S = E.sims + (m.flags >> 16);
         const int b = m.brick;
         if (ids) ids[i] = b;
@@ -898,10 +1137,16 @@ cudaError_t launch_iota_desc(int *a, int n, int first, cudaStream_t s)
 }
 
 cudaError_t launch_prime(const Engine &e, int sim, const long long *bricks, long long n, int slot0,
-                         int list_parity, cudaStream_t s)
+                         cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_prime<<<grid_for(n, 256), 256, 0, s>>>(e, sim, bricks, n, slot0, list_parity);
+    k_prime<<<grid_for(n, 256), 256, 0, s>>>(e, sim, bricks, n, slot0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStream_t s)
+{
+    k_compact<<<grid, BLOCK, 0, s>>>(e, list_parity);
     return cudaGetLastError();
 }
 
@@ -924,16 +1169,54 @@ int step_grid_size(int device)
 {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, BLOCK, 0) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, STEP_DYN_SMEM + 128) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, BLOCK, STEP_DYN_SMEM + 128) != cudaSuccess)
+        return 0;
     return sms * per_sm;
 }
 
-cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s)
+cudaError_t launch_step(const Engine &e, const PoolMaps &maps, int grid, cudaStream_t s)
 {
     Engine copy = e;
-    void *args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void *)k_step, dim3(grid), dim3(BLOCK), args, 0, s);
+    PoolMaps mcopy = maps;
+    void *args[] = {&copy, &mcopy};
+    return cudaLaunchCooperativeKernel((const void *)k_step, dim3(grid), dim3(BLOCK), args, STEP_DYN_SMEM + 128, s);
 }
+
+// Tensor maps over the pool: dims (x, y, z, half-brick) = (8, 8, 8, 2 * boxes),
+// byte strides 32 / 256 / 2048.
+bool make_pool_maps(float *pool, int n_slots, PoolMaps *out)
+{
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
+    const cuuint64_t dims[4] = {BX, BY, BZ, 2ull * (cuuint64_t)n_slots};
+    const cuuint64_t strides[3] = {BX * sizeof(float), BX * BY * sizeof(float), BVOL * sizeof(float)};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    const cuuint32_t box_x[4] = {4, BY, BZ, 1};
+    const cuuint32_t box_y[4] = {BX, 1, BZ, 1};
+    if (encode(&out->xface, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pool, dims, strides, box_x, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (encode(&out->yface, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pool, dims, strides, box_y, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    return true;
+}
+
 
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,

@@ -46,11 +46,11 @@ __global__ void k_energy_partials(tcm::Engine E, int now_half, int parity, int n
 {
     using namespace tcm;
     const int lane = threadIdx.x & 31;
-    const int *L = parity ? E.list1 : E.list0;
+    const WorkItem *L = parity ? E.items1 : E.items0;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int ph = now_half ^ 1;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
-        const int slot = L[i];
+        const int slot = L[i].slot;
         const int4 mv = *reinterpret_cast<const int4 *>(E.meta + slot);
         const int b = mv.x, kslab = mv.y;
         const double kscal = (double)__int_as_float(mv.z);

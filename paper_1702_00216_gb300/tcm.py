@@ -25,7 +25,7 @@ EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "t
            "tcm_step_async", "tcm_sync", "tcm_read_field", "tcm_read_field_device",
            "tcm_active_count", "tcm_active_bricks", "tcm_updates", "tcm_energy",
            "tcm_energy_noalloc",
-           "tcm_brick_media", "tcm_pool_info", "tcm_launch_count", "tcm_step_index",
+           "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_step_index",
            "tcm_status_string", "tcm_destroy"]
 
 
@@ -84,6 +84,7 @@ def lib():
             "tcm_energy_noalloc": ([_vp, _vp], C.c_int),
             "tcm_brick_media": ([_vp, _i64, _vp, _vp], C.c_int),
             "tcm_pool_info": ([_vp, _vp, _vp], C.c_int),
+            "tcm_phase_ns": ([_vp, _vp, _vp, _vp], C.c_int),
             "tcm_launch_count": ([_vp], _i64),
             "tcm_step_index": ([_vp], _i64),
             "tcm_status_string": ([C.c_int], C.c_char_p),
@@ -236,6 +237,13 @@ def tcm_pool_info(h):
     return s.value, f.value
 
 
+def tcm_phase_ns(h):
+    """(time stepping, updating active cells, compaction) cumulative device ns."""
+    a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _chk(lib().tcm_phase_ns(h, C.byref(a), C.byref(b), C.byref(c)), "tcm_phase_ns")
+    return a.value, b.value, c.value
+
+
 def tcm_launch_count(h) -> int:
     return int(lib().tcm_launch_count(h))
 
@@ -346,6 +354,9 @@ class Sim:
 
     def pool_info(self):
         return tcm_pool_info(self._h)
+
+    def phase_ns(self):
+        return tcm_phase_ns(self._h)
 
     @property
     def launches(self):
