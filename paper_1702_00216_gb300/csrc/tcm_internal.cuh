@@ -30,6 +30,10 @@ constexpr int TPB = XQ * BY;                // threads per brick (one float4 col
 constexpr int P1_WARPS = 6;                 // warps per CTA of the step kernel
 constexpr int BLOCK = 32 * P1_WARPS;        // threads per CTA of the step kernel
 constexpr int BRICKS_PER_WARP = 32 / TPB;
+#ifndef TCM_P1_RUN
+#define TCM_P1_RUN 4
+#endif
+constexpr int P1_RUN = TCM_P1_RUN;          // brick pairs a warp takes in a row
 
 // Shared-memory staging of one brick (bytes, 128-byte aligned): phi^n,
 // phi^{n-1}, k, and the neighbours' boundary layers.  The x faces arrive as

@@ -265,11 +265,11 @@ __device__ __forceinline__ const float *half_ptr(const Engine &E, int slot, int 
 // phi^n, phi^{n-1}, k and the z/y boundary layers of its neighbours into
 // `sb`; lane 0 of the warp has already announced the byte count.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned stage_bytes(const WorkItem &w, bool valid)
+__device__ __forceinline__ unsigned stage_bytes(const WorkItem &w, bool valid, bool cxm, bool cxp)
 {
     if (!valid) return 0u;
     unsigned b = 2u * 2048u + (w.kslab >= 0 ? 2048u : 0u);
-    b += (w.nb[0] >= 0 ? 1024u : 0u) + (w.nb[1] >= 0 ? 1024u : 0u);
+    b += (cxm ? 1024u : 0u) + (cxp ? 1024u : 0u);
     b += (w.nb[2] >= 0 ? 256u : 0u) + (w.nb[3] >= 0 ? 256u : 0u);
     b += (w.nb[4] >= 0 ? 256u : 0u) + (w.nb[5] >= 0 ? 256u : 0u);
     return b;
@@ -278,11 +278,11 @@ __device__ __forceinline__ unsigned stage_bytes(const WorkItem &w, bool valid)
 // Lanes 0..8 of a brick segment each issue one copy into the stage at sb:
 // phi^n, phi^{n-1}, k (bulk, 2 KiB each), the boundary planes of z- and z+
 // (bulk, 256 B), the boundary rows of y- and y+ (one tensor box 8x1x8 each)
-// and the boundary columns of x- and x+ (one tensor box 4x8x8 each, whose
-// last / first column is the face).  Tensor x coordinates are 0 or 4, so
-// every box starts on a 16-byte boundary.
+// and, when cxm / cxp, the boundary columns of x- and x+ (one tensor box
+// 4x8x8 each, whose last / first column is the face).  Tensor x coordinates
+// are 0 or 4, so every box starts on a 16-byte boundary.
 __device__ __forceinline__ void stage_issue(const Engine &E, const PoolMaps &maps, const WorkItem &w, bool valid,
-                                            int nh, unsigned sb, unsigned bar, int t)
+                                            bool cxm, bool cxp, int nh, unsigned sb, unsigned bar, int t)
 {
     if (!valid) return;
     switch (t) {
@@ -304,13 +304,52 @@ __device__ __forceinline__ void stage_issue(const Engine &E, const PoolMaps &map
         if (w.nb[3] >= 0) tensor_g2s(sb + OFF_YP, &maps.yface, 0, 0, 0, w.nb[3] * 2 + nh, bar);
         break;
     case 7:
-        if (w.nb[0] >= 0) tensor_g2s(sb + OFF_XM, &maps.xface, BX - 4, 0, 0, w.nb[0] * 2 + nh, bar);
+        if (cxm) tensor_g2s(sb + OFF_XM, &maps.xface, BX - 4, 0, 0, w.nb[0] * 2 + nh, bar);
         break;
     case 8:
-        if (w.nb[1] >= 0) tensor_g2s(sb + OFF_XP, &maps.xface, 0, 0, 0, w.nb[1] * 2 + nh, bar);
+        if (cxp) tensor_g2s(sb + OFF_XP, &maps.xface, 0, 0, 0, w.nb[1] * 2 + nh, bar);
         break;
     default: break;
     }
+}
+
+// Where each x face of a brick pair comes from.  A warp walks a contiguous
+// run of the active list, which is in brick order, so the two bricks of a
+// pair -- and the second brick of one pair and the first of the next -- are
+// usually x neighbours: their shared faces are exchanged between lanes
+// (lane ^ 17 holds the touching column) instead of being copied.  Only the
+// remaining faces are staged.  edge: 0 no neighbour (zero), 1 staged copy,
+// 2 from the partner lane.
+struct XPlan {
+    bool cxm, cxp;   // stage the x- / x+ column block of this segment's brick
+    int edge;        // source of this lane's edge value
+};
+
+__device__ __forceinline__ XPlan x_plan(const WorkItem &w, bool valid, int seg, int x4, int prev_b1_slot)
+{
+    const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
+    const bool other_valid = __shfl_xor_sync(FULL, (int)valid, TPB) != 0;
+    XPlan p;
+    bool share_m, share_p;
+    if (seg == 0) {
+        share_m = w.nb[0] >= 0 && w.nb[0] == prev_b1_slot;
+        share_p = w.nb[1] >= 0 && other_valid && w.nb[1] == other_slot;
+    } else {
+        share_m = w.nb[0] >= 0 && other_valid && w.nb[0] == other_slot;
+        share_p = false;
+    }
+    p.cxm = valid && w.nb[0] >= 0 && !share_m;
+    p.cxp = valid && w.nb[1] >= 0 && !share_p;
+    if (x4 == 0) p.edge = w.nb[0] < 0 ? 0 : (share_m ? 2 : 1);
+    else p.edge = w.nb[1] < 0 ? 0 : (share_p ? 2 : 1);
+    return p;
+}
+
+// The pair a warp processes after pair p: the next one of its run, or the
+// first of its next run.
+__device__ __forceinline__ int next_pair(int p, int run_jump)
+{
+    return ((p + 1) % P1_RUN != 0) ? p + 1 : p + 1 + run_jump;
 }
 
 // Merge a lane's running max |phi^{n+1}| into its sim's domain maximum.  The
@@ -325,9 +364,9 @@ __device__ __forceinline__ void flush_gmax(const Engine &E, float gacc, int gsim
 // warp calls this (valid = false on a missing brick) so shuffles see full
 // warps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, bool valid, int t,
-                                           const unsigned char *sb, unsigned long long &cells, float &gacc,
-                                           int &gsim, int &gnh)
+__device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
+                                           int xedge_src, float carry[BZ], const unsigned char *sb,
+                                           unsigned long long &cells, float &gacc, int &gsim, int &gnh)
 {
     const int x4 = t % XQ;
     const int y = t / XQ;
@@ -348,8 +387,9 @@ __device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, b
     const bool yedge = (y == 0 && w.nb[2] >= 0) || (y == BY - 1 && w.nb[3] >= 0);
     const float4 *YH4 = reinterpret_cast<const float4 *>(sb + (y == 0 ? OFF_YM : OFF_YP)) + x4;
     // lanes on the x = 0 / x = BX-1 columns take their x neighbour from the
-    // staged 4-wide column block of x- (its last column) / x+ (its first)
-    const bool xedge = (x4 == 0 && w.nb[0] >= 0) || (x4 == XQ - 1 && w.nb[1] >= 0);
+    // staged 4-wide column block of x- (its last column) / x+ (its first), or
+    // from the partner lane (see x_plan)
+    const bool xedge = xedge_src == 1;
     const float *XH = reinterpret_cast<const float *>(sb + (x4 == 0 ? OFF_XM : OFF_XP)) + y * 4 +
                       (x4 == 0 ? 3 : 0);
 
@@ -379,11 +419,17 @@ __device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, b
 #pragma unroll
     for (int z = 0; z < BZ; ++z) {
         const float4 p = P[z];
-        // x neighbours inside the brick through shuffles, x faces from registers
+        // x neighbours inside the brick through shuffles; the edge value from
+        // the staged face, or from the partner lane lane ^ 17: the x = 7 column
+        // of the pair's first brick, the x = 0 column of its second brick, or
+        // (carry) the x = 7 column of the previous pair's second brick
         const float lw = __shfl_up_sync(FULL, p.w, 1, TPB);
         const float rx = __shfl_down_sync(FULL, p.x, 1, TPB);
-        const float xm0 = (x4 == 0) ? xf[z] : lw;
-        const float xp3 = (x4 == XQ - 1) ? xf[z] : rx;
+        const float send = (x4 == XQ - 1) ? (seg == 0 ? p.w : carry[z]) : (seg == 1 ? p.x : 0.f);
+        const float recv = __shfl_xor_sync(FULL, send, TPB + 1);
+        const float xe = xedge_src == 1 ? xf[z] : (xedge_src == 2 ? recv : 0.f);
+        const float xm0 = (x4 == 0) ? xe : lw;
+        const float xp3 = (x4 == XQ - 1) ? xe : rx;
         // y neighbours inside the brick through shuffles
         float4 ym, yp;
         ym.x = __shfl_up_sync(FULL, p.x, XQ, TPB);
@@ -436,6 +482,8 @@ __device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, b
         f0 = fmaxf(f0, x4 == 0 ? fabsf(q.x) : 0.f);
         f1 = fmaxf(f1, x4 == XQ - 1 ? fabsf(q.w) : 0.f);
     }
+#pragma unroll
+    for (int z = 0; z < BZ; ++z) carry[z] = P[z].w;
     mc = seg_max(mc);
     qm = seg_max(qm);
     f0 = seg_max(f0);
@@ -667,60 +715,74 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, const __grid_consta
             mbar_fence_init();
         }
         __syncwarp();
+        // Each warp walks runs of P1_RUN consecutive brick pairs; runs are
+        // dealt round-robin to the warps, so the whole grid sweeps the list
+        // in order (neighbour halos stay in L2) while consecutive bricks of a
+        // run share their x faces (x_plan).
         const int npairs = (nact + BRICKS_PER_WARP - 1) / BRICKS_PER_WARP;
-        int pr = gwarp;
-        if (pr < npairs) {
+        const int run_jump = (nwarps - 1) * P1_RUN;
+        const int p_begin = gwarp * P1_RUN;
+        const int x4 = t % XQ;
+        if (p_begin < npairs) {
             unsigned phase = 0u;
             int stage = 0;
-            // stage the first group of bricks
+            float carry[BZ];
+#pragma unroll
+            for (int z = 0; z < BZ; ++z) carry[z] = 0.f;
+            // stage the first pair
+            int pr = p_begin;
             int i = pr * BRICKS_PER_WARP + seg;
             bool v_cur = i < nact;
             WorkItem w_cur = load_item(L, v_cur ? i : 0);
-            const int nh_cur = w_cur.nh;
+            XPlan x_cur = x_plan(w_cur, v_cur, seg, x4, -100);
             {
-                unsigned bytes = stage_bytes(w_cur, v_cur);
+                unsigned bytes = stage_bytes(w_cur, v_cur, x_cur.cxm, x_cur.cxp);
                 bytes += __shfl_down_sync(FULL, bytes, TPB);
                 if (lane == 0) mbar_arrive_expect_tx(bar[0], bytes);
                 __syncwarp();
-                stage_issue(E, maps, w_cur, v_cur, nh_cur, smem_u32(wsm + seg * BRICK_SMEM), bar[0], t);
+                stage_issue(E, maps, w_cur, v_cur, x_cur.cxm, x_cur.cxp, w_cur.nh, smem_u32(wsm + seg * BRICK_SMEM),
+                            bar[0], t);
             }
-            // item of the following group, loaded one iteration ahead
-            int pn = pr + nwarps;
+            // item of the following pair, loaded one iteration ahead
+            int pn = next_pair(pr, run_jump);
             int in = pn * BRICKS_PER_WARP + seg;
             bool v_nxt = pn < npairs && in < nact;
             WorkItem w_nxt = load_item(L, v_nxt ? in : 0);
             while (true) {
                 const bool has_next = pn < npairs;
-                int nh_nxt = 0;
                 WorkItem w_nn;
                 bool v_nn = false;
-                int pnn = pn + nwarps;
+                const int pnn = next_pair(pn, run_jump);
+                XPlan x_nxt{false, false, 0};
                 if (has_next) {
-                    nh_nxt = w_nxt.nh;
-                    unsigned bytes = stage_bytes(w_nxt, v_nxt);
+                    // the current pair's second brick precedes the next pair
+                    const int b1_slot = __shfl_sync(FULL, v_cur ? w_cur.slot : -100, TPB);
+                    x_nxt = x_plan(w_nxt, v_nxt, seg, x4, b1_slot);
+                    unsigned bytes = stage_bytes(w_nxt, v_nxt, x_nxt.cxm, x_nxt.cxp);
                     bytes += __shfl_down_sync(FULL, bytes, TPB);
                     fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) mbar_arrive_expect_tx(bar[stage ^ 1], bytes);
                     __syncwarp();
-                    stage_issue(E, maps, w_nxt, v_nxt, nh_nxt,
+                    stage_issue(E, maps, w_nxt, v_nxt, x_nxt.cxm, x_nxt.cxp, w_nxt.nh,
                                 smem_u32(wsm + (stage ^ 1) * STAGE_SMEM + seg * BRICK_SMEM), bar[stage ^ 1], t);
                     const int inn = pnn * BRICKS_PER_WARP + seg;
                     v_nn = pnn < npairs && inn < nact;
                     w_nn = load_item(L, v_nn ? inn : 0);
                 }
                 if (!mbar_wait(bar[stage], (phase >> stage) & 1u, st)) {
-                    // also drain the copies issued for the next group (bounded)
+                    // also drain the copies issued for the next pair (bounded)
                     if (has_next) mbar_wait(bar[stage ^ 1], (phase >> (stage ^ 1)) & 1u, st);
                     break;
                 }
                 phase ^= 1u << stage;
-                p1_compute(E, w_cur, v_cur, t, wsm + stage * STAGE_SMEM + seg * BRICK_SMEM, cells, gacc, gsim,
-                           gnh);
+                p1_compute(E, w_cur, v_cur, t, seg, x_cur.edge, carry, wsm + stage * STAGE_SMEM + seg * BRICK_SMEM,
+                           cells, gacc, gsim, gnh);
                 __syncwarp();
                 if (!has_next) break;
                 w_cur = w_nxt;
                 v_cur = v_nxt;
+                x_cur = x_nxt;
                 stage ^= 1;
                 pn = pnn;
                 w_nxt = w_nn;
