@@ -46,7 +46,6 @@ struct tcm_sim {
     long long launches = 0;
     int list_parity = 0;
     unsigned *h_err = nullptr;  // pinned
-    PoolMaps maps{};
 };
 
 namespace {
@@ -362,7 +361,6 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     }
     Engine &E = s->E;
     E.phi = static_cast<float *>(s->pool);
-    if (!make_pool_maps(E.phi, n_slots, &s->maps)) return fail(TCM_EDEVICE);
     E.n_slots = n_slots;
     E.n_words = s->n_words;
     E.words_per_block = (int)((s->n_words + s->grid - 1) / s->grid);
@@ -530,7 +528,7 @@ tcm_status tcm_step_async(tcm_sim *s, int64_t n)
     tcm_status st = start(s);
     if (st != TCM_OK) return st;
     for (int64_t i = 0; i < n; ++i) {
-        cudaError_t e = launch_step(s->E, s->maps, s->grid, s->stream);
+        cudaError_t e = launch_step(s->E, s->grid, s->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             s->poisoned = true;

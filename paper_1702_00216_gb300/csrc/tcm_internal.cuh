@@ -18,7 +18,6 @@
 #pragma once
 
 #include <cstdint>
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace tcm {
@@ -27,23 +26,12 @@ constexpr int BX = 8, BY = 8, BZ = 8;
 constexpr int BVOL = BX * BY * BZ;          // nodes per brick
 constexpr int XQ = BX / 4;                  // float4 columns per brick row
 constexpr int TPB = XQ * BY;                // threads per brick (one float4 column, all z)
-constexpr int P1_WARPS = 6;                 // warps per CTA of the step kernel
+#ifndef TCM_P1_WARPS
+#define TCM_P1_WARPS 8
+#endif
+constexpr int P1_WARPS = TCM_P1_WARPS;      // warps per CTA of the step kernel
 constexpr int BLOCK = 32 * P1_WARPS;        // threads per CTA of the step kernel
 constexpr int BRICKS_PER_WARP = 32 / TPB;
-#ifndef TCM_P1_RUN
-#define TCM_P1_RUN 4
-#endif
-constexpr int P1_RUN = TCM_P1_RUN;          // brick pairs a warp takes in a row
-
-// Shared-memory staging of one brick (bytes, 128-byte aligned): phi^n,
-// phi^{n-1}, k, and the neighbours' boundary layers.  The x faces arrive as
-// 4-wide columns (the narrowest tensor-copy box), the others exactly.
-constexpr int OFF_P = 0, OFF_M = 2048, OFF_K = 4096, OFF_XM = 6144, OFF_XP = 7168;
-constexpr int OFF_ZM = 8192, OFF_ZP = 8448, OFF_YM = 8704, OFF_YP = 8960;
-constexpr int BRICK_SMEM = 9216;
-constexpr int STAGE_SMEM = BRICKS_PER_WARP * BRICK_SMEM;   // one warp's bricks
-constexpr int WARP_SMEM = 2 * STAGE_SMEM;                  // double-buffered
-constexpr int STEP_DYN_SMEM = P1_WARPS * WARP_SMEM;        // 221184 B
 
 constexpr unsigned ERR_NOMEM = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -169,14 +157,7 @@ cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStrea
 cudaError_t launch_zero_slots(const Engine &e, int slot0, long long n, cudaStream_t s);
 cudaError_t launch_scatter_field(const Engine &e, const float *packed, long long n, int slot0,
                                  int now_half, cudaStream_t s);
-// Tensor maps over the pool viewed as [2 * boxes][z][y][x] floats: boxes of
-// one x-face column block (4 x 8 x 8) and of one y-face row block (8 x 1 x 8).
-struct PoolMaps {
-    CUtensorMap xface;
-    CUtensorMap yface;
-};
-bool make_pool_maps(float *pool, int n_slots, PoolMaps *out);
-cudaError_t launch_step(const Engine &e, const PoolMaps &maps, int grid, cudaStream_t s);
+cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s);
 int step_grid_size(int device);
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,

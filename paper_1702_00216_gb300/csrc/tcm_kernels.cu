@@ -150,91 +150,6 @@ __device__ __forceinline__ float seg_max(float v)
 }
 
 
-// ---------------------------------------------------------------------------
-// Asynchronous bulk copies (TMA engine) and mbarriers.
-// ---------------------------------------------------------------------------
-constexpr unsigned long long TMA_TIMEOUT_NS = 4000000000ull;  // 4 s
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for one phase of an mbarrier.  On timeout: record
-// ERR_TIMEOUT, wait once more (bounded) for the copies still in flight, and
-// report failure so the caller stops using the buffer.
-__device__ bool mbar_wait(unsigned bar, unsigned parity, EngineState *st)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > TMA_TIMEOUT_NS) {
-            atomicOr(&st->err, ERR_TIMEOUT);
-            const unsigned long long t1 = globaltimer();
-            while (!mbar_try_wait(bar, parity) && globaltimer() - t1 < TMA_TIMEOUT_NS) {
-            }
-            return false;
-        }
-    }
-    return true;
-}
-
-// Global -> shared bulk copy; completion is counted on the mbarrier.
-// dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-// Global -> shared tensor copy of one box of a 4-D tensor map (coordinates
-// innermost first); completion is counted on the mbarrier.
-__device__ __forceinline__ void tensor_g2s(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                           unsigned bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
-// Orders this thread's earlier generic accesses to shared memory before
-// later asynchronous-proxy (bulk copy) writes to it.
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 __device__ __forceinline__ WorkItem load_item(const WorkItem *L, int i)
 {
     const int4 *p = reinterpret_cast<const int4 *>(L + i);
@@ -260,98 +175,6 @@ __device__ __forceinline__ const float *half_ptr(const Engine &E, int slot, int 
     return E.phi + ((size_t)slot * 2 + half) * BVOL;
 }
 
-// ---------------------------------------------------------------------------
-// P1 staging: the lanes of one brick segment issue the bulk copies of its
-// phi^n, phi^{n-1}, k and the z/y boundary layers of its neighbours into
-// `sb`; lane 0 of the warp has already announced the byte count.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned stage_bytes(const WorkItem &w, bool valid, bool cxm, bool cxp)
-{
-    if (!valid) return 0u;
-    unsigned b = 2u * 2048u + (w.kslab >= 0 ? 2048u : 0u);
-    b += (cxm ? 1024u : 0u) + (cxp ? 1024u : 0u);
-    b += (w.nb[2] >= 0 ? 256u : 0u) + (w.nb[3] >= 0 ? 256u : 0u);
-    b += (w.nb[4] >= 0 ? 256u : 0u) + (w.nb[5] >= 0 ? 256u : 0u);
-    return b;
-}
-
-// Lanes 0..8 of a brick segment each issue one copy into the stage at sb:
-// phi^n, phi^{n-1}, k (bulk, 2 KiB each), the boundary planes of z- and z+
-// (bulk, 256 B), the boundary rows of y- and y+ (one tensor box 8x1x8 each)
-// and, when cxm / cxp, the boundary columns of x- and x+ (one tensor box
-// 4x8x8 each, whose last / first column is the face).  Tensor x coordinates
-// are 0 or 4, so every box starts on a 16-byte boundary.
-__device__ __forceinline__ void stage_issue(const Engine &E, const PoolMaps &maps, const WorkItem &w, bool valid,
-                                            bool cxm, bool cxp, int nh, unsigned sb, unsigned bar, int t)
-{
-    if (!valid) return;
-    switch (t) {
-    case 0: bulk_g2s(sb + OFF_P, half_ptr(E, w.slot, nh), 2048u, bar); break;
-    case 1: bulk_g2s(sb + OFF_M, half_ptr(E, w.slot, nh ^ 1), 2048u, bar); break;
-    case 2:
-        if (w.kslab >= 0) bulk_g2s(sb + OFF_K, E.kslabs + (size_t)w.kslab * BVOL, 2048u, bar);
-        break;
-    case 3:
-        if (w.nb[4] >= 0) bulk_g2s(sb + OFF_ZM, half_ptr(E, w.nb[4], nh) + (BZ - 1) * BY * BX, 256u, bar);
-        break;
-    case 4:
-        if (w.nb[5] >= 0) bulk_g2s(sb + OFF_ZP, half_ptr(E, w.nb[5], nh), 256u, bar);
-        break;
-    case 5:
-        if (w.nb[2] >= 0) tensor_g2s(sb + OFF_YM, &maps.yface, 0, BY - 1, 0, w.nb[2] * 2 + nh, bar);
-        break;
-    case 6:
-        if (w.nb[3] >= 0) tensor_g2s(sb + OFF_YP, &maps.yface, 0, 0, 0, w.nb[3] * 2 + nh, bar);
-        break;
-    case 7:
-        if (cxm) tensor_g2s(sb + OFF_XM, &maps.xface, BX - 4, 0, 0, w.nb[0] * 2 + nh, bar);
-        break;
-    case 8:
-        if (cxp) tensor_g2s(sb + OFF_XP, &maps.xface, 0, 0, 0, w.nb[1] * 2 + nh, bar);
-        break;
-    default: break;
-    }
-}
-
-// Where each x face of a brick pair comes from.  A warp walks a contiguous
-// run of the active list, which is in brick order, so the two bricks of a
-// pair -- and the second brick of one pair and the first of the next -- are
-// usually x neighbours: their shared faces are exchanged between lanes
-// (lane ^ 17 holds the touching column) instead of being copied.  Only the
-// remaining faces are staged.  edge: 0 no neighbour (zero), 1 staged copy,
-// 2 from the partner lane.
-struct XPlan {
-    bool cxm, cxp;   // stage the x- / x+ column block of this segment's brick
-    int edge;        // source of this lane's edge value
-};
-
-__device__ __forceinline__ XPlan x_plan(const WorkItem &w, bool valid, int seg, int x4, int prev_b1_slot)
-{
-    const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
-    const bool other_valid = __shfl_xor_sync(FULL, (int)valid, TPB) != 0;
-    XPlan p;
-    bool share_m, share_p;
-    if (seg == 0) {
-        share_m = w.nb[0] >= 0 && w.nb[0] == prev_b1_slot;
-        share_p = w.nb[1] >= 0 && other_valid && w.nb[1] == other_slot;
-    } else {
-        share_m = w.nb[0] >= 0 && other_valid && w.nb[0] == other_slot;
-        share_p = false;
-    }
-    p.cxm = valid && w.nb[0] >= 0 && !share_m;
-    p.cxp = valid && w.nb[1] >= 0 && !share_p;
-    if (x4 == 0) p.edge = w.nb[0] < 0 ? 0 : (share_m ? 2 : 1);
-    else p.edge = w.nb[1] < 0 ? 0 : (share_p ? 2 : 1);
-    return p;
-}
-
-// The pair a warp processes after pair p: the next one of its run, or the
-// first of its next run.
-__device__ __forceinline__ int next_pair(int p, int run_jump)
-{
-    return ((p + 1) % P1_RUN != 0) ? p + 1 : p + 1 + run_jump;
-}
-
 // Merge a lane's running max |phi^{n+1}| into its sim's domain maximum.  The
 // step being computed has phi^n in half nh, so its maximum lives in gmax[nh].
 __device__ __forceinline__ void flush_gmax(const Engine &E, float gacc, int gsim, int nh)
@@ -360,13 +183,19 @@ __device__ __forceinline__ void flush_gmax(const Engine &E, float gacc, int gsim
 }
 
 // ---------------------------------------------------------------------------
-// P1 compute: Eq. 3 on one brick from its staged copy.  Every lane of the
-// warp calls this (valid = false on a missing brick) so shuffles see full
-// warps.
+// P1: Eq. 3 on one brick per TPB-lane segment, straight from global memory.
+// Each lane owns one float4 column (x4, y) of all BZ planes: it issues every
+// load of the brick up front (phi^n, phi^{n-1}, k, and the halo values it
+// needs from the six neighbours' boxes), so a warp keeps two bricks' worth of
+// 16-byte loads in flight; x/y neighbours inside the brick come through warp
+// shuffles.  When the pair's second brick is the x+ neighbour of the first
+// (consecutive bricks of a row), their touching columns are exchanged between
+// lanes (lane ^ 17) instead of being loaded.  Every lane of the warp calls
+// this (valid = false on a missing brick) so shuffles see full warps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
-                                           int xedge_src, float carry[BZ], const unsigned char *sb,
-                                           unsigned long long &cells, float &gacc, int &gsim, int &gnh)
+__device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
+                                         bool share_xm, bool share_xp, unsigned long long &cells, float &gacc,
+                                         int &gsim, int &gnh)
 {
     const int x4 = t % XQ;
     const int y = t / XQ;
@@ -377,35 +206,55 @@ __device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, b
     const int nh = w.nh;
     const int b = w.brick;
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
-    const float4 *P4 = reinterpret_cast<const float4 *>(sb + OFF_P);
-    const float4 *M4 = reinterpret_cast<const float4 *>(sb + OFF_M);
-    const float4 *K4 = reinterpret_cast<const float4 *>(sb + OFF_K);
-    const bool het = w.kslab >= 0;
-    const bool hzm = w.nb[4] >= 0, hzp = w.nb[5] >= 0;
-    // lanes on the y = 0 / y = BY-1 rows take their y neighbour from the
-    // staged boundary row of y- / y+ (zero if that neighbour has no box)
-    const bool yedge = (y == 0 && w.nb[2] >= 0) || (y == BY - 1 && w.nb[3] >= 0);
-    const float4 *YH4 = reinterpret_cast<const float4 *>(sb + (y == 0 ? OFF_YM : OFF_YP)) + x4;
-    // lanes on the x = 0 / x = BX-1 columns take their x neighbour from the
-    // staged 4-wide column block of x- (its last column) / x+ (its first), or
-    // from the partner lane (see x_plan)
-    const bool xedge = xedge_src == 1;
-    const float *XH = reinterpret_cast<const float *>(sb + (x4 == 0 ? OFF_XM : OFF_XP)) + y * 4 +
-                      (x4 == 0 ? 3 : 0);
 
-    // Stage -> registers: all planes first, so the shared loads overlap.
     float4 P[BZ], M[BZ], K[BZ], YH[BZ];
-    float xf[BZ];
+    float XH[BZ];
+    float4 Zm = f4zero(), Zp = f4zero();
+    // y-edge lanes read the touching row of y- / y+, x-edge lanes the
+    // touching column of x- / x+ (unless exchanged within the pair)
+    const int ys = !valid ? -1 : (y == 0 ? w.nb[2] : (y == BY - 1 ? w.nb[3] : -1));
+    const int xs = !valid ? -1 : (x4 == 0 ? (share_xm ? -1 : w.nb[0]) : (x4 == XQ - 1 ? (share_xp ? -1 : w.nb[1]) : -1));
+    if (valid) {
+        const float4 *now4 = reinterpret_cast<const float4 *>(half_ptr(E, w.slot, nh));
+        const float4 *prv4 = reinterpret_cast<const float4 *>(half_ptr(E, w.slot, nh ^ 1));
 #pragma unroll
-    for (int z = 0; z < BZ; ++z) {
-        P[z] = P4[z * TPB + t];
-        M[z] = M4[z * TPB + t];
-        K[z] = het ? K4[z * TPB + t] : make_float4(w.kscal, w.kscal, w.kscal, w.kscal);
-        YH[z] = yedge ? YH4[z * XQ] : f4zero();
-        xf[z] = xedge ? XH[z * BY * 4] : 0.f;
+        for (int z = 0; z < BZ; ++z) P[z] = __ldg(now4 + z * TPB + t);
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) M[z] = __ldcs(prv4 + z * TPB + t);
+        if (w.kslab >= 0) {
+            const float4 *k4 = reinterpret_cast<const float4 *>(E.kslabs + (size_t)w.kslab * BVOL);
+#pragma unroll
+            for (int z = 0; z < BZ; ++z) K[z] = __ldg(k4 + z * TPB + t);
+        } else {
+#pragma unroll
+            for (int z = 0; z < BZ; ++z) K[z] = make_float4(w.kscal, w.kscal, w.kscal, w.kscal);
+        }
+        if (w.nb[4] >= 0) Zm = __ldg(reinterpret_cast<const float4 *>(half_ptr(E, w.nb[4], nh)) + (BZ - 1) * TPB + t);
+        if (w.nb[5] >= 0) Zp = __ldg(reinterpret_cast<const float4 *>(half_ptr(E, w.nb[5], nh)) + t);
+    } else {
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) {
+            P[z] = f4zero();
+            M[z] = f4zero();
+            K[z] = f4zero();
+        }
     }
-    const float4 Zm = hzm ? reinterpret_cast<const float4 *>(sb + OFF_ZM)[t] : f4zero();
-    const float4 Zp = hzp ? reinterpret_cast<const float4 *>(sb + OFF_ZP)[t] : f4zero();
+    if (ys >= 0) {
+        const float4 *yb = reinterpret_cast<const float4 *>(half_ptr(E, ys, nh)) + (y == 0 ? BY - 1 : 0) * XQ + x4;
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) YH[z] = __ldg(yb + z * TPB);
+    } else {
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) YH[z] = f4zero();
+    }
+    if (xs >= 0) {
+        const float *xb = half_ptr(E, xs, nh) + y * BX + (x4 == 0 ? BX - 1 : 0);
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) XH[z] = __ldg(xb + z * BY * BX);
+    } else {
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) XH[z] = 0.f;
+    }
 
     const float alpha = __ldg(&S->alpha);
     const bool decay = (w.flags & SD_MASK) != 0u;
@@ -414,20 +263,20 @@ __device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, b
     float4 *out = reinterpret_cast<float4 *>(E.phi + ((size_t)w.slot * 2 + (nh ^ 1)) * BVOL);
     const bool src = valid && (w.flags & FLAG_HAS_SRC);
     const long long step = src ? __ldcg(&S->step) : 0;
+    const bool xrecv = (x4 == 0 && share_xm) || (x4 == XQ - 1 && share_xp);
 
     float mc = 0.f, qm = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 0.f;
 #pragma unroll
     for (int z = 0; z < BZ; ++z) {
         const float4 p = P[z];
         // x neighbours inside the brick through shuffles; the edge value from
-        // the staged face, or from the partner lane lane ^ 17: the x = 7 column
-        // of the pair's first brick, the x = 0 column of its second brick, or
-        // (carry) the x = 7 column of the previous pair's second brick
+        // the loaded face column or, within a pair, from lane ^ 17 (the x = 7
+        // column of the first brick / the x = 0 column of the second)
         const float lw = __shfl_up_sync(FULL, p.w, 1, TPB);
         const float rx = __shfl_down_sync(FULL, p.x, 1, TPB);
-        const float send = (x4 == XQ - 1) ? (seg == 0 ? p.w : carry[z]) : (seg == 1 ? p.x : 0.f);
+        const float send = (x4 == XQ - 1) ? p.w : p.x;
         const float recv = __shfl_xor_sync(FULL, send, TPB + 1);
-        const float xe = xedge_src == 1 ? xf[z] : (xedge_src == 2 ? recv : 0.f);
+        const float xe = xrecv ? recv : XH[z];
         const float xm0 = (x4 == 0) ? xe : lw;
         const float xp3 = (x4 == XQ - 1) ? xe : rx;
         // y neighbours inside the brick through shuffles
@@ -482,8 +331,6 @@ __device__ __forceinline__ void p1_compute(const Engine &E, const WorkItem &w, b
         f0 = fmaxf(f0, x4 == 0 ? fabsf(q.x) : 0.f);
         f1 = fmaxf(f1, x4 == XQ - 1 ? fabsf(q.w) : 0.f);
     }
-#pragma unroll
-    for (int z = 0; z < BZ; ++z) carry[z] = P[z].w;
     mc = seg_max(mc);
     qm = seg_max(qm);
     f0 = seg_max(f0);
@@ -674,17 +521,14 @@ __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int st
 // ---------------------------------------------------------------------------
 // The step kernel.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, const __grid_constant__ PoolMaps maps)
+__global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
 {
-    extern __shared__ __align__(128) unsigned char dsmem[];
-    __shared__ __align__(8) unsigned long long s_bar[P1_WARPS][2];
     EngineState *st = E.st;
     const int cur = __ldcg(&st->list_parity);
     const WorkItem *L = cur ? E.items1 : E.items0;
     WorkItem *Lnext = cur ? E.items0 : E.items1;
     const int nact = __ldcg(&st->n_active[cur]);
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
     const int gwarp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * BLOCK) >> 5;
 
@@ -705,89 +549,26 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, const __grid_consta
         int gnh = 0;
         const int seg = lane / TPB;
         const int t = lane % TPB;
-        // tensor copies need 128-byte aligned destinations: align the base
-        unsigned char *sbase = dsmem + ((128u - (smem_u32(dsmem) & 127u)) & 127u);
-        unsigned char *wsm = sbase + wib * WARP_SMEM;
-        const unsigned bar[2] = {smem_u32(&s_bar[wib][0]), smem_u32(&s_bar[wib][1])};
-        if (lane == 0) {
-            mbar_init(bar[0], 1);
-            mbar_init(bar[1], 1);
-            mbar_fence_init();
-        }
-        __syncwarp();
-        // Each warp walks runs of P1_RUN consecutive brick pairs; runs are
-        // dealt round-robin to the warps, so the whole grid sweeps the list
-        // in order (neighbour halos stay in L2) while consecutive bricks of a
-        // run share their x faces (x_plan).
         const int npairs = (nact + BRICKS_PER_WARP - 1) / BRICKS_PER_WARP;
-        const int run_jump = (nwarps - 1) * P1_RUN;
-        const int p_begin = gwarp * P1_RUN;
-        const int x4 = t % XQ;
-        if (p_begin < npairs) {
-            unsigned phase = 0u;
-            int stage = 0;
-            float carry[BZ];
-#pragma unroll
-            for (int z = 0; z < BZ; ++z) carry[z] = 0.f;
-            // stage the first pair
-            int pr = p_begin;
-            int i = pr * BRICKS_PER_WARP + seg;
-            bool v_cur = i < nact;
-            WorkItem w_cur = load_item(L, v_cur ? i : 0);
-            XPlan x_cur = x_plan(w_cur, v_cur, seg, x4, -100);
-            {
-                unsigned bytes = stage_bytes(w_cur, v_cur, x_cur.cxm, x_cur.cxp);
-                bytes += __shfl_down_sync(FULL, bytes, TPB);
-                if (lane == 0) mbar_arrive_expect_tx(bar[0], bytes);
-                __syncwarp();
-                stage_issue(E, maps, w_cur, v_cur, x_cur.cxm, x_cur.cxp, w_cur.nh, smem_u32(wsm + seg * BRICK_SMEM),
-                            bar[0], t);
-            }
-            // item of the following pair, loaded one iteration ahead
-            int pn = next_pair(pr, run_jump);
-            int in = pn * BRICKS_PER_WARP + seg;
-            bool v_nxt = pn < npairs && in < nact;
-            WorkItem w_nxt = load_item(L, v_nxt ? in : 0);
-            while (true) {
-                const bool has_next = pn < npairs;
-                WorkItem w_nn;
-                bool v_nn = false;
-                const int pnn = next_pair(pn, run_jump);
-                XPlan x_nxt{false, false, 0};
-                if (has_next) {
-                    // the current pair's second brick precedes the next pair
-                    const int b1_slot = __shfl_sync(FULL, v_cur ? w_cur.slot : -100, TPB);
-                    x_nxt = x_plan(w_nxt, v_nxt, seg, x4, b1_slot);
-                    unsigned bytes = stage_bytes(w_nxt, v_nxt, x_nxt.cxm, x_nxt.cxp);
-                    bytes += __shfl_down_sync(FULL, bytes, TPB);
-                    fence_proxy_async();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive_expect_tx(bar[stage ^ 1], bytes);
-                    __syncwarp();
-                    stage_issue(E, maps, w_nxt, v_nxt, x_nxt.cxm, x_nxt.cxp, w_nxt.nh,
-                                smem_u32(wsm + (stage ^ 1) * STAGE_SMEM + seg * BRICK_SMEM), bar[stage ^ 1], t);
-                    const int inn = pnn * BRICKS_PER_WARP + seg;
-                    v_nn = pnn < npairs && inn < nact;
-                    w_nn = load_item(L, v_nn ? inn : 0);
-                }
-                if (!mbar_wait(bar[stage], (phase >> stage) & 1u, st)) {
-                    // also drain the copies issued for the next pair (bounded)
-                    if (has_next) mbar_wait(bar[stage ^ 1], (phase >> (stage ^ 1)) & 1u, st);
-                    break;
-                }
-                phase ^= 1u << stage;
-                p1_compute(E, w_cur, v_cur, t, seg, x_cur.edge, carry, wsm + stage * STAGE_SMEM + seg * BRICK_SMEM,
-                           cells, gacc, gsim, gnh);
-                __syncwarp();
-                if (!has_next) break;
-                w_cur = w_nxt;
-                v_cur = v_nxt;
-                x_cur = x_nxt;
-                stage ^= 1;
-                pn = pnn;
-                w_nxt = w_nn;
-                v_nxt = v_nn;
-            }
+        int pr = gwarp;
+        int i = pr * BRICKS_PER_WARP + seg;
+        bool v = pr < npairs && i < nact;
+        WorkItem w = load_item(L, v ? i : 0);
+        while (pr < npairs) {
+            // the next pair's item, loaded while this pair is stepped
+            const int pn = pr + nwarps;
+            const int in = pn * BRICKS_PER_WARP + seg;
+            const bool vn = pn < npairs && in < nact;
+            const WorkItem wn = load_item(L, vn ? in : 0);
+            // is the second brick of the pair the x+ neighbour of the first?
+            const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
+            const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
+            const bool pair_x = seg == 0 ? (other_v && w.nb[1] >= 0 && w.nb[1] == other_slot)
+                                         : (v && w.nb[0] >= 0 && w.nb[0] == other_slot);
+            p1_brick(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, cells, gacc, gsim, gnh);
+            pr = pn;
+            w = wn;
+            v = vn;
         }
         flush_gmax(E, gacc, gsim, gnh);
 #pragma unroll
@@ -1231,54 +1012,16 @@ int step_grid_size(int device)
 {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, STEP_DYN_SMEM + 128) !=
-        cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, BLOCK, STEP_DYN_SMEM + 128) != cudaSuccess)
-        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, BLOCK, 0) != cudaSuccess) return 0;
     return sms * per_sm;
 }
 
-cudaError_t launch_step(const Engine &e, const PoolMaps &maps, int grid, cudaStream_t s)
+cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s)
 {
     Engine copy = e;
-    PoolMaps mcopy = maps;
-    void *args[] = {&copy, &mcopy};
-    return cudaLaunchCooperativeKernel((const void *)k_step, dim3(grid), dim3(BLOCK), args, STEP_DYN_SMEM + 128, s);
+    void *args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void *)k_step, dim3(grid), dim3(BLOCK), args, 0, s);
 }
-
-// Tensor maps over the pool: dims (x, y, z, half-brick) = (8, 8, 8, 2 * boxes),
-// byte strides 32 / 256 / 2048.
-bool make_pool_maps(float *pool, int n_slots, PoolMaps *out)
-{
-    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-        cudaGetLastError();
-        return false;
-    }
-    EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
-    const cuuint64_t dims[4] = {BX, BY, BZ, 2ull * (cuuint64_t)n_slots};
-    const cuuint64_t strides[3] = {BX * sizeof(float), BX * BY * sizeof(float), BVOL * sizeof(float)};
-    const cuuint32_t ones[4] = {1, 1, 1, 1};
-    const cuuint32_t box_x[4] = {4, BY, BZ, 1};
-    const cuuint32_t box_y[4] = {BX, 1, BZ, 1};
-    if (encode(&out->xface, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pool, dims, strides, box_x, ones,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-    if (encode(&out->yface, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pool, dims, strides, box_y, ones,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-    return true;
-}
-
 
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,
