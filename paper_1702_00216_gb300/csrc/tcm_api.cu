@@ -145,6 +145,13 @@ tcm_status start(tcm_sim *s)
         TRY(cudaMemcpyAsync(d_src, src.data(), src.size() * sizeof(SrcDev), cudaMemcpyHostToDevice, s->stream));
     if (!wave.empty())
         TRY(cudaMemcpyAsync(d_wave, wave.data(), wave.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    // mark the source bricks in the per-brick state word
+    for (const auto &q : s->sources) {
+        const unsigned short bit = (unsigned short)FLAG_HAS_SRC;
+        TRY(cudaMemcpyAsync(s->E.sd_of_brick + s->simh.brick_base + q.brick, &bit, sizeof(bit),
+                            cudaMemcpyHostToDevice, s->stream));
+        TRY(cudaStreamSynchronize(s->stream));
+    }
     s->E.src = d_src;
     s->E.n_src = (int)src.size();
     s->E.wave = d_wave;
@@ -373,6 +380,7 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     if ((st = dalloc(s, &kslab_of_brick, nb_pad)) != TCM_OK) return fail(st);
     E.kscal = kscal;
     E.kslab_of_brick = kslab_of_brick;
+    if ((st = dalloc(s, &E.sd_of_brick, nb_pad)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.bitmap, s->n_words)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.blocktot, s->grid)) != TCM_OK) return fail(st);
     if ((st = dalloc(s, &E.meta, n_slots)) != TCM_OK) return fail(st);
@@ -389,6 +397,7 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     cudaStream_t q = s->stream;
     if (cudaMemsetAsync(E.slot_of_brick, 0xff, nb_pad * sizeof(int), q) != cudaSuccess ||
         cudaMemsetAsync(E.bitmap, 0, s->n_words * sizeof(unsigned), q) != cudaSuccess ||
+        cudaMemsetAsync(E.sd_of_brick, 0, nb_pad * sizeof(unsigned short), q) != cudaSuccess ||
         cudaMemsetAsync(E.blocktot, 0, s->grid * sizeof(int), q) != cudaSuccess ||
         cudaMemsetAsync(E.st, 0, sizeof(EngineState), q) != cudaSuccess)
         return fail(TCM_EDEVICE);

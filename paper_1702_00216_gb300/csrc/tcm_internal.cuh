@@ -7,6 +7,8 @@
 //   per brick slot_of_brick[g]  int32    Cell2box (-1 inactive, -2 claim in flight)
 //             kscal[g]          float    homogenic coefficient (HBM)
 //             kslab_of_brick[g] int32    index of the bulked coefficient brick, -1 if homogenic
+//             sd_of_brick[g]    uint16   Shutdown_log: shut-down steps left (bits 0-14) and
+//                                        "holds a source" (bit 15)
 //             bitmap[g/32]      bit      active for the next step (drives the compaction)
 //   per box   meta[slot]        16 B     Box2cell brick id, bulk index, scalar k, sim/sd flags
 //             rec[slot][8]      float    6 face maxima, cell maximum, max |phi^{n+1}|
@@ -112,6 +114,7 @@ struct Engine {
     const float *kscal;
     const int *kslab_of_brick;
     const float *kslabs;
+    unsigned short *sd_of_brick;
     unsigned *bitmap;
     long long n_words;
     int *blocktot;

@@ -21,7 +21,12 @@
 //       block prefix scan), in brick order, for the next launch.
 // Arithmetic: binary32, every + - * an explicit round-to-nearest intrinsic
 // (no FMA contraction), no flush-to-zero.
+#include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
+
 #include "tcm_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tcm {
 
@@ -376,30 +381,74 @@ __device__ __forceinline__ bool forced_at(const Engine &E, const SimDev *S, int 
     return false;
 }
 
-// Trigger brick b_local of sim: box it unless it is already boxed or being
-// boxed by another thread (Boxes: "Boxing new cells in vacant boxes").
-__device__ void claim_brick(const Engine &E, int sim, SimDev *S, int b_local)
+// Warp-aggregated counter update: the converged lanes calling this together
+// take consecutive values with one atomic; returns this lane's old value.
+__device__ __forceinline__ int agg_add(int *ctr, int sign)
 {
-    const long long g = S->brick_base + b_local;
-    if (atomicCAS(E.slot_of_brick + g, -1, -2) != -1) return;
-    const int top = atomicSub(&E.st->free_top, 1) - 1;
-    if (top < 0) {
-        atomicExch(E.slot_of_brick + g, -1);
-        atomicOr(&E.st->err, ERR_NOMEM);
-        atomicOr(&S->poisoned, 1u);
-        return;
+    cg::coalesced_group g = cg::coalesced_threads();
+    int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(ctr, sign * (int)g.size());
+    base = g.shfl(base, 0);
+    return base + sign * (int)g.thread_rank();
+}
+
+// Warp-aggregated reservation of n consecutive counter values per lane
+// (lanes may ask for different n); returns this lane's first value.
+__device__ __forceinline__ int agg_add_n(int *ctr, int n)
+{
+    cg::coalesced_group g = cg::coalesced_threads();
+    const int incl = cg::inclusive_scan(g, n);
+    int base = 0;
+    if (g.thread_rank() == g.size() - 1) base = atomicAdd(ctr, incl);
+    base = g.shfl(base, g.size() - 1);
+    return base + incl - n;
+}
+
+// Trigger up to six bricks of one sim (Boxes: "Boxing new cells in vacant
+// boxes"): claim each with a CAS on Cell2box (-1 -> -2; another thread may
+// be boxing it), pop one vacant box per claim won, then publish.  The
+// steps are batched so the thread waits for each kind of atomic once.
+__device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_local, int n)
+{
+    const long long bb = S->brick_base;
+    bool won[6];
+    int nw = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) won[i] = i < n && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) nw += won[i] ? 1 : 0;
+    if (nw == 0) return;
+    // vacant boxes free_stack[top - nw .. top - 1]
+    const int top = atomicSub(&E.st->free_top, nw);
+    const int nn = agg_add_n(&E.st->n_new, nw);
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (!won[i]) continue;
+        const long long g = bb + b_local[i];
+        const int idx = top - 1 - k;
+        if (idx < 0) {
+            atomicExch(E.slot_of_brick + g, -1);
+            atomicOr(&E.st->err, ERR_NOMEM);
+            atomicOr(&S->poisoned, 1u);
+            E.newslots[nn + k] = -1;
+            ++k;
+            continue;
+        }
+        const int ns = __ldcg(E.free_stack + idx);
+        SlotMeta m;
+        m.brick = b_local[i];
+        m.kslab = E.kslab_of_brick[g];
+        m.kscal = E.kscal[g];
+        m.flags = ((unsigned)sim << 16) | (brick_has_src(E, S, b_local[i]) ? FLAG_HAS_SRC : 0u);
+        store_meta(E.meta + ns, m);
+        E.sd_of_brick[g] &= (unsigned short)FLAG_HAS_SRC;   // not shutting down
+        atomicOr(E.bitmap + (g >> 5), 1u << (unsigned)(g & 31));
+        atomicAdd(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
+        E.newslots[nn + k] = ns;
+        atomicExch(E.slot_of_brick + g, ns);
+        ++k;
     }
-    const int ns = __ldcg(E.free_stack + top);
-    SlotMeta m;
-    m.brick = b_local;
-    m.kslab = E.kslab_of_brick[g];
-    m.kscal = E.kscal[g];
-    m.flags = ((unsigned)sim << 16) | (brick_has_src(E, S, b_local) ? FLAG_HAS_SRC : 0u);
-    store_meta(E.meta + ns, m);
-    atomicOr(E.bitmap + (g >> 5), 1u << (unsigned)(g & 31));
-    atomicAdd(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
-    E.newslots[atomicAdd(&E.st->n_new, 1)] = ns;
-    atomicExch(E.slot_of_brick + g, ns);
 }
 
 __device__ __forceinline__ int warp_incl_scan(int x)
@@ -451,17 +500,25 @@ __device__ long long block_sum(long long v)
 // Work item of the boxed global brick g (state after the update procedure).
 // The sim is found from g (brick ranges), so the box, its metadata and the
 // six neighbour lookups are independent loads.
-__device__ __forceinline__ void build_item(const Engine &E, long long g, WorkItem *out, int step_ahead)
+__device__ __forceinline__ void build_item(const Engine &E, long long g, WorkItem *out, int step_ahead,
+                                           int &c_sim, long long &c_step)
 {
     int si = 0;
     for (int s = 1; s < E.n_sims; ++s)
         if (g >= __ldg(&E.sims[s].brick_base)) si = s;
     const SimDev *S = E.sims + si;
+    if (si != c_sim) {
+        c_sim = si;
+        c_step = __ldcg(&S->step);
+    }
     const int mx = __ldg(&S->mx), my = __ldg(&S->my), mz = __ldg(&S->mz);
     const long long bb = __ldg(&S->brick_base);
     const int b = (int)(g - bb);
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
     const int slot = __ldcg(E.slot_of_brick + g);
+    const int kslab = __ldg(E.kslab_of_brick + g);
+    const float kscal = __ldg(E.kscal + g);
+    const unsigned sd = __ldcg(E.sd_of_brick + g);
     int nb[6];
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
@@ -472,13 +529,36 @@ __device__ __forceinline__ void build_item(const Engine &E, long long g, WorkIte
                     ? __ldcg(E.slot_of_brick + bb + ((long long)az * my + ay) * mx + ax)
                     : -3;
     }
-    const SlotMeta m = load_meta(E.meta + slot);
+    const unsigned flags = ((unsigned)si << 16) | sd;   // sd word carries the has-source bit
     // The item is processed by the next launch, which steps from phi^{n+1}.
-    const int nh = (int)((__ldcg(&S->step) + step_ahead) & 1);
+    const int nh = (int)((c_step + step_ahead) & 1);
     int4 *p = reinterpret_cast<int4 *>(out);
-    p[0] = make_int4(slot, b, m.kslab, __float_as_int(m.kscal));
-    p[1] = make_int4((int)m.flags, nb[0], nb[1], nb[2]);
+    p[0] = make_int4(slot, b, kslab, __float_as_int(kscal));
+    p[1] = make_int4((int)flags, nb[0], nb[1], nb[2]);
     p[2] = make_int4(nb[3], nb[4], nb[5], nh);
+}
+
+// Two work items at once (independent loads interleaved); g2 < 0: one.
+__device__ __forceinline__ void build_item2(const Engine &E, long long g1, WorkItem *o1, long long g2, WorkItem *o2,
+                                            int step_ahead, int &c_sim, long long &c_step)
+{
+    if (g2 < 0) {
+        build_item(E, g1, o1, step_ahead, c_sim, c_step);
+        return;
+    }
+    WorkItem tmp1, tmp2;
+    build_item(E, g1, &tmp1, step_ahead, c_sim, c_step);
+    build_item(E, g2, &tmp2, step_ahead, c_sim, c_step);
+    const int4 *a = reinterpret_cast<const int4 *>(&tmp1);
+    const int4 *c = reinterpret_cast<const int4 *>(&tmp2);
+    int4 *p1 = reinterpret_cast<int4 *>(o1);
+    int4 *p2 = reinterpret_cast<int4 *>(o2);
+    p1[0] = a[0];
+    p1[1] = a[1];
+    p1[2] = a[2];
+    p2[0] = c[0];
+    p2[1] = c[1];
+    p2[2] = c[2];
 }
 
 // Active list from the bitmap, in brick order: this block's word range gets
@@ -513,9 +593,102 @@ __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int st
     }
     __syncthreads();
     const int end = min(off, E.n_slots);
-    for (int pos = (int)before + threadIdx.x; pos < end; pos += BLOCK)
-        build_item(E, (long long)E.listids[pos], Lout + pos, step_ahead);
+    int c_sim = -1;
+    long long c_step = 0;
+    for (int pos = (int)before + threadIdx.x; pos < end; pos += 2 * BLOCK) {
+        const int pos2 = pos + BLOCK;
+        const long long g1 = E.listids[pos];
+        const long long g2 = pos2 < end ? (long long)E.listids[pos2] : -1;
+        build_item2(E, g1, Lout + pos, g2, g2 >= 0 ? Lout + pos2 : nullptr, step_ahead, c_sim, c_step);
+    }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_out = (int)all;
+}
+
+// Updating active cells for one active brick (item w, its own maxima r0/r1):
+// keep / shut down / release it, and trigger its neighbours across faces
+// above the level (Fig. 3a).
+// Per-thread copy of one sim's step state (step counter, level): every
+// item of the same sim reuses it instead of re-reading one shared address.
+struct SimCache {
+    int sim = -1;
+    bool dense = false;
+    long long step = 0;
+    double thr = 0.0;
+};
+
+__device__ __forceinline__ void sim_cache(const Engine &E, int sim, SimCache &c)
+{
+    if (sim == c.sim) return;
+    const SimDev *S = E.sims + sim;
+    c.sim = sim;
+    c.dense = __ldg(&S->dense) != 0;
+    c.step = __ldcg(&S->step);
+    const double G = (double)__uint_as_float(__ldcg(&S->gmax[c.step & 1]));
+    c.thr = __ldg(&S->thr_mode) == 1 ? __ldg(&S->tau) * G : __ldg(&S->tau);
+}
+
+__device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, const float4 &r0, const float4 &r1,
+                                        SimCache &c)
+{
+    const int slot = w.slot;
+    const int sim = (int)(w.flags >> 16);
+    SimDev *S = E.sims + sim;
+    sim_cache(E, sim, c);
+    if (c.dense) return;
+    const long long step = c.step;
+    const double thr = c.thr;
+    const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
+    bool hot = (double)r1.z > thr;
+    if (!hot) {
+        // the touching faces of the boxed neighbours (loads in parallel)
+        float nf[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) nf[f] = w.nb[f] >= 0 ? __ldcg(E.rec + (size_t)w.nb[f] * 8 + (f ^ 1)) : 0.f;
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+            if (w.nb[f] >= 0 && (double)nf[f] > thr) hot = true;
+    }
+    const int b = w.brick;
+    if (!hot && (w.flags & FLAG_HAS_SRC) && forced_at(E, S, b, step + 1)) hot = true;
+    unsigned sd = w.flags & SD_MASK;
+    const unsigned sd0 = sd;
+    bool keep;
+    if (hot) {
+        sd = 0;
+        keep = true;
+    } else if (sd > 0) {
+        sd -= 1;
+        keep = sd > 0;
+    } else if (__ldg(&S->decay_steps) > 0) {
+        sd = (unsigned)__ldg(&S->decay_steps);
+        keep = true;
+    } else {
+        keep = false;
+    }
+    const long long g = __ldg(&S->brick_base) + b;
+    if (keep) {
+        if (sd != sd0) E.sd_of_brick[g] = (unsigned short)((w.flags & FLAG_HAS_SRC) | sd);
+    } else {
+        if (sd0 != 0) E.sd_of_brick[g] = (unsigned short)(w.flags & FLAG_HAS_SRC);
+        atomicExch(E.slot_of_brick + g, -1);
+        atomicAnd(E.bitmap + (g >> 5), ~(1u << (unsigned)(g & 31)));
+        atomicSub(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
+        E.retired[agg_add(&E.st->n_retired, 1)] = slot;
+    }
+    const int mx = __ldg(&S->mx), my = __ldg(&S->my);
+    const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
+    int nbs[6];
+    int n = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        if (w.nb[f] == -1 && (double)fc[f] > thr) {
+            const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+            const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
+            const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
+            nbs[n++] = (az * my + ay) * mx + ax;
+        }
+    }
+    if (n > 0) claim_bricks(E, sim, S, nbs, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -582,64 +755,26 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
     {
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
-        for (int i = gtid; i < nact; i += nthr) {
-            const WorkItem w = load_item(L, i);
-            const int slot = w.slot;
-            const int sim = (int)(w.flags >> 16);
-            SimDev *S = E.sims + sim;
-            if (S->dense) continue;
-            const long long step = __ldcg(&S->step);
-            const double G = (double)__uint_as_float(__ldcg(&S->gmax[step & 1]));
-            const double thr = S->thr_mode == 1 ? S->tau * G : S->tau;
-            const float4 r0 = __ldcg(reinterpret_cast<const float4 *>(E.rec + (size_t)slot * 8));
-            const float4 r1 = __ldcg(reinterpret_cast<const float4 *>(E.rec + (size_t)slot * 8) + 1);
-            const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
-            bool hot = (double)r1.z > thr;
+        // Eight items per thread at a time, so their loads overlap.
+        constexpr int U = 8;
+        SimCache sc;
+        for (int base = gtid; base < nact; base += U * nthr) {
+            WorkItem w[U];
+            float4 r0[U], r1[U];
 #pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                if (!hot && w.nb[f] >= 0) {
-                    const float v = __ldcg(E.rec + (size_t)w.nb[f] * 8 + (f ^ 1));
-                    if ((double)v > thr) hot = true;
-                }
+            for (int u = 0; u < U; ++u) {
+                const int i = base + u * nthr;
+                w[u] = load_item(L, i < nact ? i : 0);
             }
-            const int b = w.brick;
-            if (!hot && (w.flags & FLAG_HAS_SRC) && forced_at(E, S, b, step + 1)) hot = true;
-            unsigned sd = w.flags & SD_MASK;
-            bool keep;
-            if (hot) {
-                sd = 0;
-                keep = true;
-            } else if (sd > 0) {
-                sd -= 1;
-                keep = sd > 0;
-            } else if (S->decay_steps > 0) {
-                sd = (unsigned)S->decay_steps;
-                keep = true;
-            } else {
-                keep = false;
-            }
-            const long long g = S->brick_base + b;
-            if (keep) {
-                const unsigned nf = (w.flags & ~SD_MASK) | sd;
-                if (nf != w.flags) E.meta[slot].flags = nf;
-            } else {
-                atomicExch(E.slot_of_brick + g, -1);
-                atomicAnd(E.bitmap + (g >> 5), ~(1u << (unsigned)(g & 31)));
-                atomicSub(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
-                E.retired[atomicAdd(&st->n_retired, 1)] = slot;
-            }
-            // Trigger the neighbours across faces above the level (Fig. 3a).
-            const int mx = S->mx, my = S->my;
-            const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
 #pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                if (w.nb[f] == -1 && (double)fc[f] > thr) {
-                    const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
-                    const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
-                    const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
-                    claim_brick(E, sim, S, (az * my + ay) * mx + ax);
-                }
+            for (int u = 0; u < U; ++u) {
+                const float4 *r = reinterpret_cast<const float4 *>(E.rec + (size_t)w[u].slot * 8);
+                r0[u] = __ldcg(r);
+                r1[u] = __ldcg(r + 1);
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (base + u * nthr < nact) p2_item(E, w[u], r0[u], r1[u], sc);
         }
         // Manual activation of source bricks still being fed at step n+1.
         if (blockIdx.x == 0) {
@@ -648,7 +783,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
                 SimDev *S = E.sims + sd.sim;
                 if (S->dense) continue;
                 const long long n1 = __ldcg(&S->step) + 1;
-                if (n1 >= sd.start && n1 < sd.start + sd.len) claim_brick(E, sd.sim, S, sd.brick);
+                if (n1 >= sd.start && n1 < sd.start + sd.len) claim_bricks(E, sd.sim, S, &sd.brick, 1);
             }
         }
     }
@@ -661,7 +796,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
         const int nthr = gridDim.x * BLOCK;
         const int n_new = __ldcg(&st->n_new);
         for (int i = gwarp; i < n_new; i += nwarps) {
-            float4 *p = reinterpret_cast<float4 *>(E.phi + (size_t)__ldcg(E.newslots + i) * 2 * BVOL);
+            const int ns = __ldcg(E.newslots + i);
+            if (ns < 0) continue;   // a claim that found no vacant box
+            float4 *p = reinterpret_cast<float4 *>(E.phi + (size_t)ns * 2 * BVOL);
             for (int e = lane; e < 2 * BVOL / 4; e += 32) p[e] = f4zero();
         }
         const int n_ret = __ldcg(&st->n_retired);
