@@ -138,7 +138,8 @@ tcm_status tcm_read_field_device(const tcm_sim *sim, int which, int64_t x0, int6
                                  int64_t z0, int64_t wx, int64_t wy, int64_t wz,
                                  float *device_out);
 
-/* Active bricks for the next step, and the in-domain nodes they hold. */
+/* Active (boxed) bricks for the next step, and the in-domain nodes they
+ * hold; a frozen batch simulation reports the set it ended with. */
 tcm_status tcm_active_count(const tcm_sim *sim, int64_t *bricks, int64_t *cells);
 
 /* Sorted ids (z*my*mx + y*mx + x over the brick grid) of the active bricks;
@@ -193,7 +194,60 @@ int64_t tcm_step_index(const tcm_sim *sim);
 
 const char *tcm_status_string(tcm_status s);
 
+/* Destroy a simulation made by tcm_create (and its device memory).  On a
+ * simulation of a batch it is tcm_batch_remove. */
 void tcm_destroy(tcm_sim *sim);
+
+/* ---- Batches: many simulations stepped by one launch per step -----------
+ * A batch owns one box pool and one brick-table space shared by its
+ * simulations (each gets a contiguous range of brick slots).  Every launch
+ * steps all live simulations of the batch by one step; each keeps its own
+ * step counter, media, sources, threshold and shut-down settings, so results
+ * are bit-for-bit those of the same simulation run alone.  Simulations may
+ * be added and removed between steps (continuous batching); a simulation
+ * with n_steps > 0 stops stepping (is frozen, its fields kept) when it has
+ * done them.  Simulation handles from tcm_batch_add are owned by the batch:
+ * the per-simulation functions above (add_source, set_field, read_field,
+ * active_count, active_bricks, updates, energy, brick_media, step_index)
+ * accept them; tcm_step / tcm_step_async on them return TCM_ESTATE. */
+typedef struct tcm_batch tcm_batch;
+
+typedef struct {
+    void *pool_ptr;     /* device memory for the boxes, or NULL: library allocates */
+    size_t pool_bytes;  /* pool size (number of boxes = pool_bytes / tcm_slot_bytes) */
+    void *stream;       /* cudaStream_t */
+    int device;         /* CUDA device ordinal */
+    int storage;        /* TCM_STORAGE_F32 */
+    int64_t max_bricks; /* brick-table capacity summed over simulations (12 B per brick) */
+    int max_sims;       /* simulation-table capacity */
+} tcm_batch_options;
+
+tcm_status tcm_batch_create(const tcm_batch_options *options, tcm_batch **out);
+
+/* Add a simulation (arguments as tcm_create, dense = 1 boxes every brick).
+ * TCM_ENOMEM when the brick-table space or the simulation table is full.
+ * Sources and initial fields may be added until the next step. */
+tcm_status tcm_batch_add(tcm_batch *batch, const tcm_domain *domain, const tcm_velocity_model *velocity,
+                         double dx, double dt, double threshold, tcm_brick brick, int threshold_mode,
+                         float decay_alpha, int decay_steps, int dense, int64_t n_steps, tcm_sim **out);
+
+/* Step every live simulation n times (tcm_batch_step waits and reports the
+ * status; _async only enqueues, tcm_batch_sync reports). */
+tcm_status tcm_batch_step(tcm_batch *batch, int64_t n);
+tcm_status tcm_batch_step_async(tcm_batch *batch, int64_t n);
+tcm_status tcm_batch_sync(tcm_batch *batch);
+
+/* Whether a simulation has done its n_steps (and no longer steps). */
+tcm_status tcm_sim_done(const tcm_sim *sim, int *done);
+
+/* Remove a simulation: its boxes return to the pool, its brick range and
+ * table entry are reused; the handle is invalid afterwards. */
+tcm_status tcm_batch_remove(tcm_batch *batch, tcm_sim *sim);
+
+/* Boxes in the pool and free now; simulations alive. */
+tcm_status tcm_batch_info(const tcm_batch *batch, int64_t *slots, int64_t *free_slots, int *sims);
+
+void tcm_batch_destroy(tcm_batch *batch);
 
 #ifdef __cplusplus
 }

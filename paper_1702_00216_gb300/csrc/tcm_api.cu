@@ -1,11 +1,12 @@
 // tcm_api.cu -- host runtime and C ABI of libtcm (see include/tcm.h).
 //
-// One tcm_sim owns one engine: the brick tables of its domain, the per-box
-// metadata, the active lists and the step state, all resident in HBM; the
-// boxes themselves live in the caller's pool (or one the library allocates).
-// Everything a step needs stays on the device between calls; the host only
-// launches one cooperative kernel per step and reads a status word per call.
+// The runtime is a batch engine: one box pool, one brick-table space split
+// into per-simulation ranges, one simulation table and one active list, all
+// resident in HBM.  Every step is one cooperative launch of the step kernel
+// over all live simulations; the host only launches, and reads a status
+// word per call.  tcm_create makes a batch holding exactly one simulation.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -17,44 +18,76 @@
 
 using namespace tcm;
 
-struct tcm_sim {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    Engine E{};
-    SimDev simh{};
-    long long nx = 0, ny = 0, nz = 0;
-    int mx = 0, my = 0, mz = 0;
-    long long n_bricks = 0, n_words = 0;
-    int n_slots = 0;
-    int grid = 0;
-    bool own_pool = false;
-    void *pool = nullptr;
-    std::vector<void *> allocs;
-    long long n_kslabs = 0;
-    struct Source {
-        int brick, local;
-        long long start;
-        std::vector<float> w;
-    };
-    std::vector<Source> sources;
-    std::vector<float> init_now, init_prev;
-    bool have_field = false;
-    bool started = false;
-    bool poisoned = false;
-    tcm_status sticky = TCM_OK;
-    long long step = 0;
-    long long launches = 0;
-    int list_parity = 0;
-    unsigned *h_err = nullptr;  // pinned
-};
-
 namespace {
 
 constexpr double INV_SQRT3 = 0.57735026918962576451;
 
+struct HostSrc {
+    int brick, local;
+    long long start;
+    std::vector<float> w;
+};
+
+struct HostSim {
+    bool used = false;     // this table entry holds a simulation
+    bool primed = false;   // its initial bricks are boxed
+    bool live = false;     // steps with the batch
+    long long nx = 0, ny = 0, nz = 0;
+    int mx = 0, my = 0, mz = 0;
+    long long n_bricks = 0, range_len = 0, brick_base = 0;
+    int dense = 0;
+    float *kslabs = nullptr;
+    long long n_kslabs = 0;
+    std::vector<HostSrc> sources;
+    std::vector<float> init_now, init_prev;
+    bool have_field = false;
+    long long step = 0;
+    long long target = -1;   // freeze after this many steps (-1: never)
+    SimDev dev{};
+};
+
+struct Range {
+    long long base, len;
+};
+
+}  // namespace
+
+struct tcm_sim {
+    tcm_batch *b = nullptr;
+    int id = 0;
+    bool owns_batch = false;
+};
+
+struct tcm_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int grid = 0;
+    Engine E{};
+    long long cap_bricks = 0, n_words = 0;
+    int max_sims = 0;
+    int n_slots = 0;
+    void *pool = nullptr;
+    bool own_pool = false;
+    std::vector<void *> allocs;
+    std::vector<HostSim> sims;
+    std::vector<tcm_sim *> handles;
+    std::vector<Range> free_ranges;
+    SrcDev *d_src = nullptr;
+    float *d_wave = nullptr;
+    unsigned *h_err = nullptr;  // pinned
+    bool poisoned = false;
+    tcm_status sticky = TCM_OK;
+    long long launches = 0;
+    int list_parity = 0;
+    bool dirty_list = false;   // the active list must be rebuilt before the next step
+};
+
+namespace {
+
 tcm_status dev_err(cudaError_t e)
 {
     if (e == cudaSuccess) return TCM_OK;
+    cudaGetLastError();
     if (e == cudaErrorMemoryAllocation) return TCM_ENOMEM;
     return TCM_EDEVICE;
 }
@@ -65,8 +98,14 @@ tcm_status dev_err(cudaError_t e)
         if (_s != TCM_OK) return _s;                       \
     } while (0)
 
+#define TRYS(expr)                                         \
+    do {                                                   \
+        tcm_status _s = (expr);                            \
+        if (_s != TCM_OK) return _s;                       \
+    } while (0)
+
 template <typename T>
-tcm_status dalloc(tcm_sim *s, T **p, size_t count)
+tcm_status dalloc(tcm_batch *b, T **p, size_t count)
 {
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
@@ -74,7 +113,7 @@ tcm_status dalloc(tcm_sim *s, T **p, size_t count)
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? TCM_ENOMEM : TCM_EDEVICE;
     }
-    s->allocs.push_back(q);
+    b->allocs.push_back(q);
     *p = static_cast<T *>(q);
     return TCM_OK;
 }
@@ -84,154 +123,112 @@ struct DeviceGuard {
     explicit DeviceGuard(int d)
     {
         if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        cudaSetDevice(d);
+        if (prev != d) cudaSetDevice(d);
     }
     ~DeviceGuard()
     {
-        if (prev >= 0) cudaSetDevice(prev);
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
 
-tcm_status sync_status(tcm_sim *s)
+tcm_status poison(tcm_batch *b, tcm_status s)
 {
-    cudaError_t e = cudaMemcpyAsync(s->h_err, &s->E.st->err, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                    s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    b->poisoned = true;
+    if (b->sticky == TCM_OK) b->sticky = s;
+    return s;
+}
+
+tcm_status sync_status(tcm_batch *b)
+{
+    cudaError_t e = cudaMemcpyAsync(b->h_err, &b->E.st->err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
-        s->poisoned = true;
-        s->sticky = TCM_EDEVICE;
-        return TCM_EDEVICE;
+        cudaGetLastError();
+        return poison(b, TCM_EDEVICE);
     }
-    const unsigned err = *s->h_err;
-    if (err & ERR_TIMEOUT) {
-        s->poisoned = true;
-        s->sticky = TCM_ETIMEOUT;
-        return TCM_ETIMEOUT;
-    }
-    if (err & ERR_NOMEM) {
-        s->poisoned = true;
-        s->sticky = TCM_ENOMEM;
-        return TCM_ENOMEM;
-    }
+    const unsigned err = *b->h_err;
+    if (err & ERR_TIMEOUT) return poison(b, TCM_ETIMEOUT);
+    if (err & ERR_NOMEM) return poison(b, TCM_ENOMEM);
     return TCM_OK;
 }
 
-// Box the initial bricks (source bricks and bricks holding initial values),
-// in brick order, and hand every other box to the free stack.
-tcm_status start(tcm_sim *s)
+// Immutable part of a SimDev (everything before the device-owned counters).
+tcm_status upload_sim_header(tcm_batch *b, int id)
 {
-    if (s->started) return TCM_OK;
-    DeviceGuard g(s->device);
-    // sources -> device
+    TRY(cudaMemcpyAsync(b->E.sims + id, &b->sims[id].dev, offsetof(SimDev, step), cudaMemcpyHostToDevice,
+                        b->stream));
+    return TCM_OK;
+}
+
+// Concatenate the sources of every simulation into the device table.
+tcm_status upload_sources(tcm_batch *b)
+{
     std::vector<SrcDev> src;
     std::vector<float> wave;
-    for (const auto &q : s->sources) {
-        SrcDev d{};
-        d.sim = 0;
-        d.brick = q.brick;
-        d.local = q.local;
-        d.start = q.start;
-        d.len = (long long)q.w.size();
-        d.w_off = (long long)wave.size();
-        wave.insert(wave.end(), q.w.begin(), q.w.end());
-        src.push_back(d);
+    for (int id = 0; id < (int)b->sims.size(); ++id) {
+        HostSim &h = b->sims[id];
+        if (!h.used) continue;
+        h.dev.src_begin = (int)src.size();
+        for (const auto &q : h.sources) {
+            SrcDev d{};
+            d.sim = id;
+            d.brick = q.brick;
+            d.local = q.local;
+            d.start = q.start;
+            d.len = (long long)q.w.size();
+            d.w_off = (long long)wave.size();
+            wave.insert(wave.end(), q.w.begin(), q.w.end());
+            src.push_back(d);
+        }
+        h.dev.src_end = (int)src.size();
     }
-    SrcDev *d_src = nullptr;
-    float *d_wave = nullptr;
-    tcm_status st;
-    if ((st = dalloc(s, &d_src, src.size())) != TCM_OK) return st;
-    if ((st = dalloc(s, &d_wave, wave.size())) != TCM_OK) return st;
+    TRY(cudaStreamSynchronize(b->stream));
+    if (b->d_src) cudaFree(b->d_src);
+    if (b->d_wave) cudaFree(b->d_wave);
+    b->d_src = nullptr;
+    b->d_wave = nullptr;
+    TRY(cudaMalloc(&b->d_src, std::max<size_t>(src.size(), 1) * sizeof(SrcDev)));
+    TRY(cudaMalloc(&b->d_wave, std::max<size_t>(wave.size(), 1) * sizeof(float)));
     if (!src.empty())
-        TRY(cudaMemcpyAsync(d_src, src.data(), src.size() * sizeof(SrcDev), cudaMemcpyHostToDevice, s->stream));
+        TRY(cudaMemcpyAsync(b->d_src, src.data(), src.size() * sizeof(SrcDev), cudaMemcpyHostToDevice, b->stream));
     if (!wave.empty())
-        TRY(cudaMemcpyAsync(d_wave, wave.data(), wave.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    // mark the source bricks in the per-brick state word
-    for (const auto &q : s->sources) {
-        const unsigned short bit = (unsigned short)FLAG_HAS_SRC;
-        TRY(cudaMemcpyAsync(s->E.sd_of_brick + s->simh.brick_base + q.brick, &bit, sizeof(bit),
-                            cudaMemcpyHostToDevice, s->stream));
-        TRY(cudaStreamSynchronize(s->stream));
-    }
-    s->E.src = d_src;
-    s->E.n_src = (int)src.size();
-    s->E.wave = d_wave;
-    s->simh.src_begin = 0;
-    s->simh.src_end = (int)src.size();
-    TRY(cudaMemcpyAsync(s->E.sims, &s->simh, sizeof(SimDev), cudaMemcpyHostToDevice, s->stream));
-
-    // initial active set
-    std::vector<long long> init;
-    long long n_init = 0;
-    const long long bvol = BVOL;
-    if (s->simh.dense) {
-        n_init = s->n_bricks;
-    } else {
-        std::vector<char> mark((size_t)s->n_bricks, 0);
-        for (const auto &q : s->sources)
-            if (!q.w.empty()) mark[(size_t)q.brick] = 1;
-        if (s->have_field) {
-            for (long long z = 0; z < s->nz; ++z)
-                for (long long y = 0; y < s->ny; ++y)
-                    for (long long x = 0; x < s->nx; ++x) {
-                        const size_t id = (size_t)((z * s->ny + y) * s->nx + x);
-                        if (s->init_now[id] != 0.f || s->init_prev[id] != 0.f)
-                            mark[(size_t)(((z / BZ) * s->my + (y / BY)) * s->mx + (x / BX))] = 1;
-                    }
-        }
-        for (long long b = 0; b < s->n_bricks; ++b)
-            if (mark[(size_t)b]) init.push_back(b);
-        n_init = (long long)init.size();
-    }
-    if (n_init > s->n_slots) {
-        s->poisoned = true;
-        s->sticky = TCM_ENOMEM;
-        return TCM_ENOMEM;
-    }
-    long long *d_init = nullptr;
-    if (!s->simh.dense && n_init > 0) {
-        TRY(cudaMalloc(&d_init, n_init * sizeof(long long)));
-        TRY(cudaMemcpyAsync(d_init, init.data(), n_init * sizeof(long long), cudaMemcpyHostToDevice, s->stream));
-    }
-    TRY(launch_prime(s->E, 0, d_init, n_init, 0, s->stream));
-    TRY(launch_zero_slots(s->E, 0, n_init, s->stream));
-    if (s->have_field && n_init > 0) {
-        // pack the initial values of the boxed bricks
-        std::vector<float> packed((size_t)(n_init * 2 * bvol), 0.f);
-        for (long long i = 0; i < n_init; ++i) {
-            const long long b = s->simh.dense ? i : init[(size_t)i];
-            const long long cx = b % s->mx, cy = (b / s->mx) % s->my, cz = b / ((long long)s->mx * s->my);
-            for (int e = 0; e < BVOL; ++e) {
-                const long long x = cx * BX + e % BX, y = cy * BY + (e / BX) % BY, z = cz * BZ + e / (BX * BY);
-                if (x >= s->nx || y >= s->ny || z >= s->nz) continue;
-                const size_t id = (size_t)((z * s->ny + y) * s->nx + x);
-                packed[(size_t)(i * 2 * bvol + e)] = s->init_now[id];
-                packed[(size_t)(i * 2 * bvol + bvol + e)] = s->init_prev[id];
-            }
-        }
-        float *d_packed = nullptr;
-        TRY(cudaMalloc(&d_packed, packed.size() * sizeof(float)));
-        TRY(cudaMemcpyAsync(d_packed, packed.data(), packed.size() * sizeof(float), cudaMemcpyHostToDevice,
-                            s->stream));
-        TRY(launch_scatter_field(s->E, d_packed, n_init, 0, (int)(s->step & 1), s->stream));
-        TRY(cudaStreamSynchronize(s->stream));
-        cudaFree(d_packed);
-        std::vector<float>().swap(s->init_now);
-        std::vector<float>().swap(s->init_prev);
-    }
-    // free stack: boxes n_init .. n_slots-1, lowest on top
-    const int n_free = s->n_slots - (int)n_init;
-    TRY(launch_iota_desc(s->E.free_stack, n_free, s->n_slots - 1, s->stream));
-    EngineState es{};
-    es.free_top = n_free;
-    es.list_parity = 0;
-    es.n_active[0] = (int)n_init;
-    TRY(cudaMemcpyAsync(s->E.st, &es, sizeof(es), cudaMemcpyHostToDevice, s->stream));
-    TRY(launch_compact(s->E, s->grid, 0, s->stream));
-    TRY(cudaStreamSynchronize(s->stream));
-    if (d_init) cudaFree(d_init);
-    s->list_parity = 0;
-    s->started = true;
+        TRY(cudaMemcpyAsync(b->d_wave, wave.data(), wave.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            b->stream));
+    b->E.src = b->d_src;
+    b->E.n_src = (int)src.size();
+    b->E.wave = b->d_wave;
+    for (int id = 0; id < (int)b->sims.size(); ++id)
+        if (b->sims[id].used) TRYS(upload_sim_header(b, id));
     return TCM_OK;
+}
+
+long long range_alloc(tcm_batch *b, long long len)
+{
+    for (size_t i = 0; i < b->free_ranges.size(); ++i) {
+        Range &r = b->free_ranges[i];
+        if (r.len >= len) {
+            const long long base = r.base;
+            r.base += len;
+            r.len -= len;
+            if (r.len == 0) b->free_ranges.erase(b->free_ranges.begin() + (long)i);
+            return base;
+        }
+    }
+    return -1;
+}
+
+void range_free(tcm_batch *b, long long base, long long len)
+{
+    b->free_ranges.push_back({base, len});
+    std::sort(b->free_ranges.begin(), b->free_ranges.end(),
+              [](const Range &x, const Range &y) { return x.base < y.base; });
+    std::vector<Range> merged;
+    for (const Range &r : b->free_ranges) {
+        if (!merged.empty() && merged.back().base + merged.back().len == r.base) merged.back().len += r.len;
+        else merged.push_back(r);
+    }
+    b->free_ranges.swap(merged);
 }
 
 float model_c_max(const tcm_domain *d, const tcm_velocity_model *v, bool *bad)
@@ -261,44 +258,18 @@ float model_c_max(const tcm_domain *d, const tcm_velocity_model *v, bool *bad)
     return cmax;
 }
 
-}  // namespace
-
-bool tcm_internal_view(const tcm_sim *s, SimView *v)
+// Argument checks shared by tcm_create and tcm_batch_add, before any GPU work.
+tcm_status check_sim_args(const tcm_domain *domain, const tcm_velocity_model *velocity, double dx, double dt,
+                          double threshold, tcm_brick brick, int storage, int threshold_mode, int decay_steps)
 {
-    if (!s || !v) return false;
-    v->E = &s->E;
-    v->device = s->device;
-    v->stream = s->stream;
-    v->started = s->started;
-    v->step = s->step;
-    v->list_parity = s->list_parity;
-    return true;
-}
-
-extern "C" {
-
-tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out)
-{
-    if (!out || brick.bx != BX || brick.by != BY || brick.bz != BZ || storage != TCM_STORAGE_F32)
-        return TCM_EINVAL;
-    *out = (size_t)2 * BVOL * sizeof(float);
-    return TCM_OK;
-}
-
-tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *velocity, double dx, double dt,
-                      double threshold, tcm_brick brick, const tcm_options *options, tcm_sim **out)
-{
-    if (!out) return TCM_EINVAL;
-    *out = nullptr;
-    if (!domain || !velocity || !options) return TCM_EINVAL;
+    if (!domain || !velocity) return TCM_EINVAL;
     if (domain->nx < 1 || domain->ny < 1 || domain->nz < 1) return TCM_EINVAL;
     if (domain->nx > (1LL << 30) || domain->ny > (1LL << 30) || domain->nz > (1LL << 30)) return TCM_EINVAL;
     if (!(dx > 0) || !(dt > 0) || !(threshold >= 0) || std::isinf(threshold)) return TCM_EINVAL;
     size_t slot_bytes = 0;
-    if (tcm_slot_bytes(brick, options->storage, &slot_bytes) != TCM_OK) return TCM_EINVAL;
-    if (options->threshold_mode != TCM_THR_ABSOLUTE && options->threshold_mode != TCM_THR_RELATIVE)
-        return TCM_EINVAL;
-    if (options->decay_steps < 0 || options->decay_steps > (int)SD_MASK) return TCM_EINVAL;
+    if (tcm_slot_bytes(brick, storage, &slot_bytes) != TCM_OK) return TCM_EINVAL;
+    if (threshold_mode != TCM_THR_ABSOLUTE && threshold_mode != TCM_THR_RELATIVE) return TCM_EINVAL;
+    if (decay_steps < 0 || decay_steps > (int)SD_MASK) return TCM_EINVAL;
     if (velocity->kind == TCM_MEDIA_DENSE) {
         if (!velocity->c) return TCM_EINVAL;
     } else if (velocity->kind == TCM_MEDIA_RULES) {
@@ -310,105 +281,110 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     }
     const long long mx = (domain->nx + BX - 1) / BX, my = (domain->ny + BY - 1) / BY,
                     mz = (domain->nz + BZ - 1) / BZ;
-    const long long n_bricks = mx * my * mz;
-    if (n_bricks > (1LL << 31) - 64) return TCM_EINVAL;
+    if (mx * my * mz > (1LL << 31) - 64) return TCM_EINVAL;
     // Eq. 4 with the largest velocity of the model.
     bool bad = false;
     const float cmax = model_c_max(domain, velocity, &bad);
     if (bad) return TCM_EINVAL;
     if ((double)cmax * dt / dx > INV_SQRT3) return TCM_ECFL;
-    if (options->dense && options->pool_ptr == nullptr && options->pool_bytes == 0) {
-        // default pool for the dense comparator: one box per brick
-    }
-    const size_t pool_bytes = options->pool_bytes ? options->pool_bytes
-                                                  : (options->dense ? (size_t)n_bricks * slot_bytes : 0);
-    const long long n_slots_ll = (long long)(pool_bytes / slot_bytes);
-    if (n_slots_ll < 1) return TCM_EINVAL;
-    const int n_slots = (int)std::min<long long>(n_slots_ll, (1LL << 31) - 64);
-    if (options->dense && n_slots < n_bricks) return TCM_ENOMEM;
+    return TCM_OK;
+}
 
+tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t pool_bytes, long long max_bricks,
+                     int max_sims, tcm_batch **out)
+{
+    *out = nullptr;
+    size_t slot_bytes = 2 * BVOL * sizeof(float);
+    const long long n_slots_ll = (long long)(pool_bytes / slot_bytes);
+    if (n_slots_ll < 1 || max_bricks < 1 || max_sims < 1 || max_sims > 65535) return TCM_EINVAL;
+    if (pool_ptr && reinterpret_cast<uintptr_t>(pool_ptr) % 16 != 0) return TCM_EINVAL;
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || options->device < 0 || options->device >= ndev) {
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
         return TCM_EDEVICE;
     }
-    DeviceGuard guard(options->device);
-    tcm_sim *s = new (std::nothrow) tcm_sim();
-    if (!s) return TCM_ENOMEM;
-    s->device = options->device;
-    s->stream = (cudaStream_t)options->stream;
-    s->nx = domain->nx;
-    s->ny = domain->ny;
-    s->nz = domain->nz;
-    s->mx = (int)mx;
-    s->my = (int)my;
-    s->mz = (int)mz;
-    s->n_bricks = n_bricks;
-    s->n_words = (n_bricks + 31) / 32;
-    s->n_slots = n_slots;
-    s->grid = step_grid_size(s->device);
-    tcm_status st = TCM_OK;
+    DeviceGuard guard(device);
+    tcm_batch *b = new (std::nothrow) tcm_batch();
+    if (!b) return TCM_ENOMEM;
     auto fail = [&](tcm_status e) {
-        tcm_destroy(s);
+        tcm_batch_destroy(b);
         return e;
     };
-    if (s->grid <= 0) return fail(TCM_EDEVICE);
-    if (cudaMallocHost(&s->h_err, sizeof(unsigned)) != cudaSuccess) return fail(TCM_EDEVICE);
-
-    // pool
-    if (options->pool_ptr) {
-        if (reinterpret_cast<uintptr_t>(options->pool_ptr) % 16 != 0) return fail(TCM_EINVAL);
-        s->pool = options->pool_ptr;
+    b->device = device;
+    b->stream = stream;
+    b->n_slots = (int)std::min<long long>(n_slots_ll, (1LL << 31) - 64);
+    b->cap_bricks = (max_bricks + 31) / 32 * 32;
+    b->n_words = b->cap_bricks / 32;
+    b->max_sims = max_sims;
+    b->grid = step_grid_size(device);
+    if (b->grid <= 0) return fail(TCM_EDEVICE);
+    if (cudaMallocHost(&b->h_err, sizeof(unsigned)) != cudaSuccess) return fail(TCM_EDEVICE);
+    if (pool_ptr) {
+        b->pool = pool_ptr;
     } else {
-        if (cudaMalloc(&s->pool, (size_t)n_slots * slot_bytes) != cudaSuccess) {
+        if (cudaMalloc(&b->pool, (size_t)b->n_slots * slot_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(TCM_ENOMEM);
         }
-        s->own_pool = true;
+        b->own_pool = true;
     }
-    Engine &E = s->E;
-    E.phi = static_cast<float *>(s->pool);
-    E.n_slots = n_slots;
-    E.n_words = s->n_words;
-    E.words_per_block = (int)((s->n_words + s->grid - 1) / s->grid);
-    if (E.words_per_block < 1) E.words_per_block = 1;
-    const long long nb_pad = s->n_words * 32;
+    Engine &E = b->E;
+    E.phi = static_cast<float *>(b->pool);
+    E.n_slots = b->n_slots;
+    E.n_words = b->n_words;
+    E.words_per_block = (int)std::max<long long>(1, (b->n_words + b->grid - 1) / b->grid);
+    tcm_status st;
     float *kscal = nullptr;
     int *kslab_of_brick = nullptr;
-    if ((st = dalloc(s, &E.slot_of_brick, nb_pad)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &kscal, nb_pad)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &kslab_of_brick, nb_pad)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.slot_of_brick, b->cap_bricks)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &kscal, b->cap_bricks)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &kslab_of_brick, b->cap_bricks)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.sd_of_brick, b->cap_bricks)) != TCM_OK) return fail(st);
     E.kscal = kscal;
     E.kslab_of_brick = kslab_of_brick;
-    if ((st = dalloc(s, &E.sd_of_brick, nb_pad)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.bitmap, s->n_words)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.blocktot, s->grid)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.meta, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.rec, (size_t)n_slots * 8)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.items0, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.items1, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.listids, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.free_stack, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.retired, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.newslots, n_slots)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.sims, 1)) != TCM_OK) return fail(st);
-    if ((st = dalloc(s, &E.st, 1)) != TCM_OK) return fail(st);
-    E.n_sims = 1;
-    cudaStream_t q = s->stream;
-    if (cudaMemsetAsync(E.slot_of_brick, 0xff, nb_pad * sizeof(int), q) != cudaSuccess ||
-        cudaMemsetAsync(E.bitmap, 0, s->n_words * sizeof(unsigned), q) != cudaSuccess ||
-        cudaMemsetAsync(E.sd_of_brick, 0, nb_pad * sizeof(unsigned short), q) != cudaSuccess ||
-        cudaMemsetAsync(E.blocktot, 0, s->grid * sizeof(int), q) != cudaSuccess ||
-        cudaMemsetAsync(E.st, 0, sizeof(EngineState), q) != cudaSuccess)
+    if ((st = dalloc(b, &E.bitmap, b->n_words)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.sim_of_word, b->n_words)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.blocktot, b->grid)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.meta, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.rec, (size_t)b->n_slots * 8)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.items0, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.items1, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.listids, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.free_stack, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.retired, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.newslots, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.sims, max_sims)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.st, 1)) != TCM_OK) return fail(st);
+    E.n_sims = max_sims;
+    b->sims.resize(max_sims);
+    b->handles.assign(max_sims, nullptr);
+    b->free_ranges.push_back({0, b->cap_bricks});
+    cudaStream_t q = b->stream;
+    EngineState es{};
+    es.free_top = b->n_slots;
+    if (cudaMemsetAsync(E.slot_of_brick, 0xff, b->cap_bricks * sizeof(int), q) != cudaSuccess ||
+        cudaMemsetAsync(E.sd_of_brick, 0, b->cap_bricks * sizeof(unsigned short), q) != cudaSuccess ||
+        cudaMemsetAsync(E.bitmap, 0, b->n_words * sizeof(unsigned), q) != cudaSuccess ||
+        cudaMemsetAsync(E.sim_of_word, 0, b->n_words * sizeof(unsigned short), q) != cudaSuccess ||
+        cudaMemsetAsync(E.blocktot, 0, b->grid * sizeof(int), q) != cudaSuccess ||
+        cudaMemsetAsync(E.sims, 0, max_sims * sizeof(SimDev), q) != cudaSuccess ||
+        cudaMemcpyAsync(E.st, &es, sizeof(es), cudaMemcpyHostToDevice, q) != cudaSuccess ||
+        launch_iota_desc(E.free_stack, b->n_slots, b->n_slots - 1, q) != cudaSuccess ||
+        cudaStreamSynchronize(q) != cudaSuccess)
         return fail(TCM_EDEVICE);
+    // an empty source table, so kernels always see valid pointers
+    if ((st = upload_sources(b)) != TCM_OK) return fail(st);
+    if (cudaStreamSynchronize(q) != cudaSuccess) return fail(TCM_EDEVICE);
+    *out = b;
+    return TCM_OK;
+}
 
-    // Heterogenic Bulking, once (Media).
+// Heterogenic Bulking of one simulation into its brick range (Media).
+tcm_status bulk_sim(tcm_batch *b, HostSim &h, const tcm_velocity_model *velocity, double dx, double dt)
+{
+    cudaStream_t q = b->stream;
     MediaDev md{};
     md.kind = velocity->kind == TCM_MEDIA_DENSE ? MEDIA_DENSE : MEDIA_RULES;
-    float *d_c = nullptr;
-    double *d_lz = nullptr, *d_sph = nullptr;
-    float *d_lc = nullptr, *d_sc = nullptr;
-    int *d_cnt = nullptr;
     std::vector<void *> tmp;
     auto tmp_alloc = [&](void **p, size_t bytes) -> bool {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
@@ -418,17 +394,24 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
         tmp.push_back(*p);
         return true;
     };
-    auto free_tmp = [&]() {
-        for (void *p : tmp) cudaFree(p);
-        tmp.clear();
-    };
-    const size_t n_nodes = (size_t)(domain->nx * domain->ny * domain->nz);
+    struct Cleanup {
+        std::vector<void *> &t;
+        ~Cleanup()
+        {
+            for (void *p : t) cudaFree(p);
+        }
+    } cleanup{tmp};
+    int *d_cnt = nullptr;
     bool ok = tmp_alloc((void **)&d_cnt, sizeof(int));
+    const size_t n_nodes = (size_t)(h.nx * h.ny * h.nz);
     if (ok && md.kind == MEDIA_DENSE) {
+        float *d_c = nullptr;
         ok = tmp_alloc((void **)&d_c, n_nodes * sizeof(float)) &&
              cudaMemcpyAsync(d_c, velocity->c, n_nodes * sizeof(float), cudaMemcpyHostToDevice, q) == cudaSuccess;
         md.c = d_c;
     } else if (ok) {
+        double *d_lz = nullptr, *d_sph = nullptr;
+        float *d_lc = nullptr, *d_sc = nullptr;
         md.c_bg = velocity->c_background;
         md.n_layers = velocity->n_layers;
         md.n_spheres = velocity->n_spheres;
@@ -451,112 +434,371 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
         md.sph = d_sph;
         md.sph_c = d_sc;
     }
-    if (!ok) {
-        free_tmp();
-        return fail(TCM_ENOMEM);
-    }
+    if (!ok) return TCM_ENOMEM;
+    float *kscal = const_cast<float *>(b->E.kscal);
+    int *kslab_of_brick = const_cast<int *>(b->E.kslab_of_brick);
+    TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int), q));
+    TRY(launch_bulk_classify(md, (int)h.nx, (int)h.ny, (int)h.nz, h.mx, h.my, h.mz, dt, dx, h.brick_base, kscal,
+                             kslab_of_brick, d_cnt, q));
     int n_kslabs = 0;
-    if (cudaMemsetAsync(d_cnt, 0, sizeof(int), q) != cudaSuccess ||
-        launch_bulk_classify(md, (int)s->nx, (int)s->ny, (int)s->nz, s->mx, s->my, s->mz, dt, dx, kscal,
-                             kslab_of_brick, d_cnt, q) != cudaSuccess ||
-        cudaMemcpyAsync(s->h_err, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, q) != cudaSuccess ||
-        cudaStreamSynchronize(q) != cudaSuccess) {
-        free_tmp();
-        return fail(TCM_EDEVICE);
-    }
-    std::memcpy(&n_kslabs, s->h_err, sizeof(int));
-    s->n_kslabs = n_kslabs;
-    float *kslabs = nullptr;
-    if ((st = dalloc(s, &kslabs, (size_t)n_kslabs * BVOL)) != TCM_OK) {
-        free_tmp();
-        return fail(st);
-    }
-    E.kslabs = kslabs;
-    if (n_kslabs > 0 &&
-        (launch_bulk_fill(md, (int)s->nx, (int)s->ny, (int)s->nz, s->mx, s->my, s->mz, dt, dx, kslab_of_brick,
-                          kslabs, q) != cudaSuccess ||
-         cudaStreamSynchronize(q) != cudaSuccess)) {
-        free_tmp();
-        return fail(TCM_EDEVICE);
-    }
-    cudaStreamSynchronize(q);
-    free_tmp();
+    TRY(cudaMemcpyAsync(b->h_err, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, q));
+    TRY(cudaStreamSynchronize(q));
+    std::memcpy(&n_kslabs, b->h_err, sizeof(int));
+    h.n_kslabs = n_kslabs;
+    TRY(cudaMalloc(&h.kslabs, std::max<size_t>((size_t)n_kslabs * BVOL, 1) * sizeof(float)));
+    if (n_kslabs > 0)
+        TRY(launch_bulk_fill(md, (int)h.nx, (int)h.ny, (int)h.nz, h.mx, h.my, h.mz, dt, dx, h.brick_base,
+                             kslab_of_brick, h.kslabs, q));
+    TRY(cudaStreamSynchronize(q));
+    return TCM_OK;
+}
 
-    SimDev &S = s->simh;
-    S.nx = (int)s->nx;
-    S.ny = (int)s->ny;
-    S.nz = (int)s->nz;
-    S.mx = s->mx;
-    S.my = s->my;
-    S.mz = s->mz;
-    S.brick_base = 0;
-    S.n_bricks = n_bricks;
-    S.thr_mode = options->threshold_mode;
-    S.dense = options->dense ? 1 : 0;
+tcm_status sim_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_model *velocity, double dx, double dt,
+                   double threshold, int thr_mode, float alpha, int decay_steps, int dense, long long n_steps,
+                   int *out_id)
+{
+    int id = -1;
+    for (int i = 0; i < b->max_sims; ++i)
+        if (!b->sims[i].used) {
+            id = i;
+            break;
+        }
+    if (id < 0) return TCM_ENOMEM;
+    HostSim h;
+    h.nx = domain->nx;
+    h.ny = domain->ny;
+    h.nz = domain->nz;
+    h.mx = (int)((h.nx + BX - 1) / BX);
+    h.my = (int)((h.ny + BY - 1) / BY);
+    h.mz = (int)((h.nz + BZ - 1) / BZ);
+    h.n_bricks = (long long)h.mx * h.my * h.mz;
+    h.range_len = (h.n_bricks + 31) / 32 * 32;
+    h.dense = dense;
+    h.target = n_steps > 0 ? n_steps : -1;
+    if (dense && h.n_bricks > b->n_slots) return TCM_ENOMEM;
+    h.brick_base = range_alloc(b, h.range_len);
+    if (h.brick_base < 0) return TCM_ENOMEM;
+    tcm_status st = bulk_sim(b, h, velocity, dx, dt);
+    if (st != TCM_OK) {
+        if (h.kslabs) cudaFree(h.kslabs);
+        range_free(b, h.brick_base, h.range_len);
+        return st;
+    }
+    SimDev &S = h.dev;
+    S = SimDev{};
+    S.nx = (int)h.nx;
+    S.ny = (int)h.ny;
+    S.nz = (int)h.nz;
+    S.mx = h.mx;
+    S.my = h.my;
+    S.mz = h.mz;
+    S.brick_base = h.brick_base;
+    S.n_bricks = h.n_bricks;
+    S.thr_mode = thr_mode;
+    S.dense = dense;
     S.tau = threshold;
-    S.alpha = options->decay_alpha;
-    S.decay_steps = options->decay_steps;
-    S.step = 0;
-    if (cudaMemcpyAsync(E.sims, &S, sizeof(SimDev), cudaMemcpyHostToDevice, q) != cudaSuccess ||
-        cudaStreamSynchronize(q) != cudaSuccess)
-        return fail(TCM_EDEVICE);
+    S.alpha = alpha;
+    S.decay_steps = decay_steps;
+    S.kslabs = h.kslabs;
+    S.live = 0;
+    h.used = true;
+    // the brick range's words now belong to this sim
+    {
+        std::vector<unsigned short> owner((size_t)(h.range_len / 32), (unsigned short)id);
+        cudaError_t e = cudaMemcpyAsync(b->E.sim_of_word + h.brick_base / 32, owner.data(),
+                                        owner.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h.kslabs);
+            range_free(b, h.brick_base, h.range_len);
+            return TCM_EDEVICE;
+        }
+    }
+    b->sims[id] = std::move(h);
+    // full upload: counters start at zero
+    TRY(cudaMemcpyAsync(b->E.sims + id, &b->sims[id].dev, sizeof(SimDev), cudaMemcpyHostToDevice, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
+    *out_id = id;
+    return TCM_OK;
+}
+
+// Box a simulation's initial bricks (source bricks, bricks with initial
+// values, or every brick of a dense simulation) and start it stepping.
+tcm_status sim_prime(tcm_batch *b, int id)
+{
+    HostSim &h = b->sims[id];
+    if (h.primed) return TCM_OK;
+    cudaStream_t q = b->stream;
+    TRYS(upload_sources(b));
+    for (const auto &src : h.sources) {
+        const unsigned short bit = (unsigned short)FLAG_HAS_SRC;
+        TRY(cudaMemcpyAsync(b->E.sd_of_brick + h.brick_base + src.brick, &bit, sizeof(bit), cudaMemcpyHostToDevice,
+                            q));
+        TRY(cudaStreamSynchronize(q));
+    }
+    std::vector<long long> init;
+    long long n_init = 0;
+    if (h.dense) {
+        n_init = h.n_bricks;
+    } else {
+        std::vector<char> mark((size_t)h.n_bricks, 0);
+        for (const auto &src : h.sources)
+            if (!src.w.empty()) mark[(size_t)src.brick] = 1;
+        if (h.have_field) {
+            for (long long z = 0; z < h.nz; ++z)
+                for (long long y = 0; y < h.ny; ++y)
+                    for (long long x = 0; x < h.nx; ++x) {
+                        const size_t i = (size_t)((z * h.ny + y) * h.nx + x);
+                        if (h.init_now[i] != 0.f || h.init_prev[i] != 0.f)
+                            mark[(size_t)(((z / BZ) * h.my + (y / BY)) * h.mx + (x / BX))] = 1;
+                    }
+        }
+        for (long long i = 0; i < h.n_bricks; ++i)
+            if (mark[(size_t)i]) init.push_back(i);
+        n_init = (long long)init.size();
+    }
+    long long *d_init = nullptr;
+    if (!h.dense && n_init > 0) {
+        TRY(cudaMalloc(&d_init, n_init * sizeof(long long)));
+        TRY(cudaMemcpyAsync(d_init, init.data(), n_init * sizeof(long long), cudaMemcpyHostToDevice, q));
+    }
+    tcm_status st = dev_err(launch_settle(b->E, q));
+    if (st == TCM_OK) st = dev_err(launch_admit(b->E, id, d_init, n_init, q));
+    if (st == TCM_OK && h.have_field && n_init > 0) {
+        const long long bvol = BVOL;
+        std::vector<float> packed((size_t)(n_init * 2 * bvol), 0.f);
+        std::vector<long long> gids((size_t)n_init);
+        for (long long i = 0; i < n_init; ++i) {
+            const long long brick = h.dense ? i : init[(size_t)i];
+            gids[(size_t)i] = h.brick_base + brick;
+            const long long cx = brick % h.mx, cy = (brick / h.mx) % h.my, cz = brick / ((long long)h.mx * h.my);
+            for (int e = 0; e < BVOL; ++e) {
+                const long long x = cx * BX + e % BX, y = cy * BY + (e / BX) % BY, z = cz * BZ + e / (BX * BY);
+                if (x >= h.nx || y >= h.ny || z >= h.nz) continue;
+                const size_t i0 = (size_t)((z * h.ny + y) * h.nx + x);
+                packed[(size_t)(i * 2 * bvol + e)] = h.init_now[i0];
+                packed[(size_t)(i * 2 * bvol + bvol + e)] = h.init_prev[i0];
+            }
+        }
+        float *d_packed = nullptr;
+        long long *d_gids = nullptr;
+        st = dev_err(cudaMalloc(&d_packed, packed.size() * sizeof(float)));
+        if (st == TCM_OK) st = dev_err(cudaMalloc(&d_gids, gids.size() * sizeof(long long)));
+        if (st == TCM_OK)
+            st = dev_err(cudaMemcpyAsync(d_packed, packed.data(), packed.size() * sizeof(float),
+                                         cudaMemcpyHostToDevice, q));
+        if (st == TCM_OK)
+            st = dev_err(cudaMemcpyAsync(d_gids, gids.data(), gids.size() * sizeof(long long),
+                                         cudaMemcpyHostToDevice, q));
+        if (st == TCM_OK) st = dev_err(launch_scatter_field(b->E, d_packed, d_gids, n_init, (int)(h.step & 1), q));
+        if (st == TCM_OK) st = dev_err(cudaStreamSynchronize(q));
+        if (d_packed) cudaFree(d_packed);
+        if (d_gids) cudaFree(d_gids);
+    }
+    if (st == TCM_OK) st = dev_err(cudaStreamSynchronize(q));
+    if (d_init) cudaFree(d_init);
+    if (st != TCM_OK) return poison(b, st);
+    std::vector<float>().swap(h.init_now);
+    std::vector<float>().swap(h.init_prev);
+    h.primed = true;
+    h.live = h.target != 0;
+    h.dev.live = h.live ? 1 : 0;
+    TRYS(upload_sim_header(b, id));
+    b->dirty_list = true;
+    // a pool too small for the initial bricks
+    return sync_status(b);
+}
+
+tcm_status prime_all(tcm_batch *b)
+{
+    for (int id = 0; id < b->max_sims; ++id)
+        if (b->sims[id].used && !b->sims[id].primed) TRYS(sim_prime(b, id));
+    return TCM_OK;
+}
+
+tcm_status ensure_list(tcm_batch *b)
+{
+    if (!b->dirty_list) return TCM_OK;
+    TRY(launch_compact(b->E, b->grid, b->list_parity, b->stream));
+    b->dirty_list = false;
+    return TCM_OK;
+}
+
+tcm_status freeze_sim(tcm_batch *b, int id)
+{
+    HostSim &h = b->sims[id];
+    TRY(launch_freeze(b->E, id, h.brick_base / 32, h.range_len / 32, b->stream));
+    h.live = false;
+    h.dev.live = 0;
+    b->dirty_list = true;
+    return TCM_OK;
+}
+
+tcm_status batch_step_async(tcm_batch *b, long long n)
+{
+    if (b->poisoned) return TCM_ESTATE;
+    DeviceGuard g(b->device);
+    TRYS(prime_all(b));
+    for (long long i = 0; i < n; ++i) {
+        TRYS(ensure_list(b));
+        cudaError_t e = launch_step(b->E, b->grid, b->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return poison(b, TCM_EDEVICE);
+        }
+        b->launches += 1;
+        b->list_parity ^= 1;
+        for (int id = 0; id < b->max_sims; ++id) {
+            HostSim &h = b->sims[id];
+            if (!h.used || !h.live) continue;
+            h.step += 1;
+            if (h.target > 0 && h.step >= h.target) TRYS(freeze_sim(b, id));
+        }
+    }
+    return TCM_OK;
+}
+
+tcm_status sim_release(tcm_batch *b, int id)
+{
+    DeviceGuard g(b->device);
+    HostSim &h = b->sims[id];
+    if (!h.used) return TCM_EINVAL;
+    if (h.primed) {
+        TRY(launch_settle(b->E, b->stream));
+        TRY(launch_release(b->E, id, h.brick_base, h.n_bricks, b->stream));
+    }
+    TRY(cudaStreamSynchronize(b->stream));
+    if (h.kslabs) cudaFree(h.kslabs);
+    range_free(b, h.brick_base, h.range_len);
+    // the released entry stops stepping; clear it on the device
+    SimDev zero{};
+    TRY(cudaMemcpyAsync(b->E.sims + id, &zero, sizeof(SimDev), cudaMemcpyHostToDevice, b->stream));
+    b->sims[id] = HostSim{};
+    TRYS(upload_sources(b));
+    TRY(cudaStreamSynchronize(b->stream));
+    b->dirty_list = true;
+    return TCM_OK;
+}
+
+HostSim *sim_of(const tcm_sim *s)
+{
+    if (!s || !s->b || s->id < 0 || s->id >= s->b->max_sims || !s->b->sims[s->id].used) return nullptr;
+    return &s->b->sims[s->id];
+}
+
+// Make sure the simulation's initial state is on the device and the active
+// list matches the current state (reads and diagnostics).
+tcm_status ready_for_read(tcm_batch *b, int id)
+{
+    if (!b->sims[id].primed) TRYS(sim_prime(b, id));
+    TRYS(ensure_list(b));
+    return TCM_OK;
+}
+
+}  // namespace
+
+bool tcm_internal_view(const tcm_sim *s, SimView *v)
+{
+    HostSim *h = sim_of(s);
+    if (!h || !v) return false;
+    v->E = &s->b->E;
+    v->device = s->b->device;
+    v->stream = s->b->stream;
+    v->started = h->primed && !s->b->dirty_list;
+    v->step = h->step;
+    v->list_parity = s->b->list_parity;
+    v->sim = s->id;
+    return true;
+}
+
+extern "C" {
+
+tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out)
+{
+    if (!out || brick.bx != BX || brick.by != BY || brick.bz != BZ || storage != TCM_STORAGE_F32)
+        return TCM_EINVAL;
+    *out = (size_t)2 * BVOL * sizeof(float);
+    return TCM_OK;
+}
+
+tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *velocity, double dx, double dt,
+                      double threshold, tcm_brick brick, const tcm_options *options, tcm_sim **out)
+{
+    if (!out) return TCM_EINVAL;
+    *out = nullptr;
+    if (!options) return TCM_EINVAL;
+    TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, options->storage, options->threshold_mode,
+                        options->decay_steps));
+    const long long n_bricks = ((domain->nx + BX - 1) / BX) * ((domain->ny + BY - 1) / BY) *
+                               ((domain->nz + BZ - 1) / BZ);
+    size_t slot_bytes = 0;
+    tcm_slot_bytes(brick, options->storage, &slot_bytes);
+    const size_t pool_bytes = options->pool_bytes ? options->pool_bytes
+                                                  : (options->dense ? (size_t)n_bricks * slot_bytes : 0);
+    if (pool_bytes / slot_bytes < 1) return TCM_EINVAL;
+    if (options->dense && (long long)(pool_bytes / slot_bytes) < n_bricks) return TCM_ENOMEM;
+    tcm_batch *b = nullptr;
+    TRYS(batch_new(options->device, (cudaStream_t)options->stream, options->pool_ptr, pool_bytes, n_bricks, 1, &b));
+    DeviceGuard g(b->device);
+    int id = -1;
+    tcm_status st = sim_add(b, domain, velocity, dx, dt, threshold, options->threshold_mode, options->decay_alpha,
+                            options->decay_steps, options->dense ? 1 : 0, -1, &id);
+    if (st != TCM_OK) {
+        tcm_batch_destroy(b);
+        return st;
+    }
+    tcm_sim *s = new (std::nothrow) tcm_sim();
+    if (!s) {
+        tcm_batch_destroy(b);
+        return TCM_ENOMEM;
+    }
+    s->b = b;
+    s->id = id;
+    s->owns_batch = true;
+    b->handles[id] = s;
     *out = s;
     return TCM_OK;
 }
 
 tcm_status tcm_add_source(tcm_sim *s, int64_t x, int64_t y, int64_t z, const float *wavelet, int64_t n)
 {
-    if (!s || n < 0 || (n > 0 && !wavelet)) return TCM_EINVAL;
-    if (x < 0 || y < 0 || z < 0 || x >= s->nx || y >= s->ny || z >= s->nz) return TCM_EINVAL;
-    if (s->started) return TCM_ESTATE;
-    tcm_sim::Source q;
-    q.brick = (int)(((z / BZ) * s->my + (y / BY)) * s->mx + (x / BX));
+    HostSim *h = sim_of(s);
+    if (!h || n < 0 || (n > 0 && !wavelet)) return TCM_EINVAL;
+    if (x < 0 || y < 0 || z < 0 || x >= h->nx || y >= h->ny || z >= h->nz) return TCM_EINVAL;
+    if (h->primed) return TCM_ESTATE;
+    HostSrc q;
+    q.brick = (int)(((z / BZ) * h->my + (y / BY)) * h->mx + (x / BX));
     q.local = (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX));
-    q.start = s->step;
+    q.start = h->step;
     q.w.assign(wavelet, wavelet + n);
-    s->sources.push_back(std::move(q));
+    h->sources.push_back(std::move(q));
     return TCM_OK;
 }
 
 tcm_status tcm_set_field(tcm_sim *s, const float *now, const float *prev)
 {
-    if (!s || !now || !prev) return TCM_EINVAL;
-    if (s->started) return TCM_ESTATE;
-    const size_t n = (size_t)(s->nx * s->ny * s->nz);
-    s->init_now.assign(now, now + n);
-    s->init_prev.assign(prev, prev + n);
-    s->have_field = true;
+    HostSim *h = sim_of(s);
+    if (!h || !now || !prev) return TCM_EINVAL;
+    if (h->primed) return TCM_ESTATE;
+    const size_t n = (size_t)(h->nx * h->ny * h->nz);
+    h->init_now.assign(now, now + n);
+    h->init_prev.assign(prev, prev + n);
+    h->have_field = true;
     return TCM_OK;
 }
 
 tcm_status tcm_step_async(tcm_sim *s, int64_t n)
 {
-    if (!s || n < 0) return TCM_EINVAL;
-    if (s->poisoned) return TCM_ESTATE;
-    DeviceGuard g(s->device);
-    tcm_status st = start(s);
-    if (st != TCM_OK) return st;
-    for (int64_t i = 0; i < n; ++i) {
-        cudaError_t e = launch_step(s->E, s->grid, s->stream);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            s->poisoned = true;
-            s->sticky = TCM_EDEVICE;
-            return TCM_EDEVICE;
-        }
-        s->step += 1;
-        s->launches += 1;
-        s->list_parity ^= 1;
-    }
-    return TCM_OK;
+    if (!sim_of(s) || n < 0) return TCM_EINVAL;
+    if (!s->owns_batch) return TCM_ESTATE;
+    return batch_step_async(s->b, n);
 }
 
 tcm_status tcm_sync(tcm_sim *s)
 {
-    if (!s) return TCM_EINVAL;
-    DeviceGuard g(s->device);
-    if (s->poisoned && s->sticky != TCM_OK) return s->sticky;
-    return sync_status(s);
+    if (!sim_of(s)) return TCM_EINVAL;
+    return tcm_batch_sync(s->b);
 }
 
 tcm_status tcm_step(tcm_sim *s, int64_t n)
@@ -569,35 +811,36 @@ tcm_status tcm_step(tcm_sim *s, int64_t n)
 tcm_status tcm_read_field_device(const tcm_sim *cs, int which, int64_t x0, int64_t y0, int64_t z0, int64_t wx,
                                  int64_t wy, int64_t wz, float *device_out)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s || (which != 0 && which != 1) || wx < 0 || wy < 0 || wz < 0 || (!device_out && wx * wy * wz > 0))
+    HostSim *h = sim_of(cs);
+    if (!h || (which != 0 && which != 1) || wx < 0 || wy < 0 || wz < 0 || (!device_out && wx * wy * wz > 0))
         return TCM_EINVAL;
-    DeviceGuard g(s->device);
-    tcm_status st = start(s);
-    if (st != TCM_OK) return st;
-    const int half = which == 0 ? (int)(s->step & 1) : (int)((s->step + 1) & 1);
-    TRY(launch_read_window(s->E, 0, half, x0, y0, z0, wx, wy, wz, device_out, s->stream));
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
+    TRYS(ready_for_read(b, cs->id));
+    const int half = which == 0 ? (int)(h->step & 1) : (int)((h->step + 1) & 1);
+    TRY(launch_read_window(b->E, cs->id, half, x0, y0, z0, wx, wy, wz, device_out, b->stream));
     return TCM_OK;
 }
 
 tcm_status tcm_read_field(const tcm_sim *cs, int which, int64_t x0, int64_t y0, int64_t z0, int64_t wx,
                           int64_t wy, int64_t wz, float *host_out)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s || (which != 0 && which != 1) || wx < 0 || wy < 0 || wz < 0 || (!host_out && wx * wy * wz > 0))
+    HostSim *h = sim_of(cs);
+    if (!h || (which != 0 && which != 1) || wx < 0 || wy < 0 || wz < 0 || (!host_out && wx * wy * wz > 0))
         return TCM_EINVAL;
     const long long n = wx * wy * wz;
     if (n == 0) return TCM_OK;
-    DeviceGuard g(s->device);
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
     float *d = nullptr;
     if (cudaMalloc(&d, n * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return TCM_ENOMEM;
     }
-    tcm_status st = tcm_read_field_device(s, which, x0, y0, z0, wx, wy, wz, d);
+    tcm_status st = tcm_read_field_device(cs, which, x0, y0, z0, wx, wy, wz, d);
     if (st == TCM_OK) {
-        cudaError_t e = cudaMemcpyAsync(host_out, d, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        cudaError_t e = cudaMemcpyAsync(host_out, d, n * sizeof(float), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         st = dev_err(e);
     }
     cudaFree(d);
@@ -606,99 +849,99 @@ tcm_status tcm_read_field(const tcm_sim *cs, int which, int64_t x0, int64_t y0, 
 
 tcm_status tcm_active_count(const tcm_sim *cs, int64_t *bricks, int64_t *cells)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s) return TCM_EINVAL;
-    DeviceGuard g(s->device);
-    tcm_status st = start(s);
-    if (st != TCM_OK) return st;
+    HostSim *h = sim_of(cs);
+    if (!h) return TCM_EINVAL;
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
+    TRYS(ready_for_read(b, cs->id));
     unsigned long long *d = nullptr;
     TRY(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
-    EngineState es{};
-    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), s->stream);
-    if (e == cudaSuccess) e = launch_active_bricks(s->E, s->list_parity, nullptr, d, s->stream);
-    unsigned long long hc = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d, sizeof(hc), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&es, s->E.st, sizeof(es), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    unsigned long long hc[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), b->stream);
+    if (e == cudaSuccess) e = launch_active_bricks(b->E, cs->id, b->list_parity, nullptr, d, d + 1, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, d, sizeof(hc), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     cudaFree(d);
     TRY(e);
-    if (bricks) *bricks = es.n_active[s->list_parity];
-    if (cells) *cells = (int64_t)hc;
+    if (bricks) *bricks = (int64_t)hc[0];
+    if (cells) *cells = (int64_t)hc[1];
     return TCM_OK;
 }
 
 tcm_status tcm_active_bricks(const tcm_sim *cs, int64_t *ids, int64_t cap, int64_t *n)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s || cap < 0 || (cap > 0 && !ids)) return TCM_EINVAL;
-    DeviceGuard g(s->device);
-    tcm_status st = start(s);
-    if (st != TCM_OK) return st;
-    EngineState es{};
-    TRY(cudaMemcpyAsync(&es, s->E.st, sizeof(es), cudaMemcpyDeviceToHost, s->stream));
-    TRY(cudaStreamSynchronize(s->stream));
-    const long long na = es.n_active[s->list_parity];
-    if (n) *n = na;
-    if (na == 0 || cap == 0) return TCM_OK;
+    HostSim *h = sim_of(cs);
+    if (!h || cap < 0 || (cap > 0 && !ids)) return TCM_EINVAL;
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
+    TRYS(ready_for_read(b, cs->id));
+    const long long upper = h->n_bricks;
     long long *d = nullptr;
-    TRY(cudaMalloc(&d, na * sizeof(long long)));
-    std::vector<long long> h((size_t)na);
-    cudaError_t e = launch_active_bricks(s->E, s->list_parity, d, nullptr, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, na * sizeof(long long), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    unsigned long long *dn = nullptr;
+    TRY(cudaMalloc(&d, std::max<long long>(upper, 1) * sizeof(long long)));
+    cudaError_t e = cudaMalloc(&dn, sizeof(unsigned long long));
+    unsigned long long hn = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(dn, 0, sizeof(unsigned long long), b->stream);
+    if (e == cudaSuccess) e = launch_active_bricks(b->E, cs->id, b->list_parity, d, dn, nullptr, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hn, dn, sizeof(hn), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    std::vector<long long> hv((size_t)hn);
+    if (e == cudaSuccess && hn > 0)
+        e = cudaMemcpy(hv.data(), d, hn * sizeof(long long), cudaMemcpyDeviceToHost);
     cudaFree(d);
+    if (dn) cudaFree(dn);
     TRY(e);
-    std::sort(h.begin(), h.end());
-    for (long long i = 0; i < na && i < cap; ++i) ids[i] = h[(size_t)i];
+    std::sort(hv.begin(), hv.end());
+    if (n) *n = (int64_t)hn;
+    for (long long i = 0; i < (long long)hn && i < cap; ++i) ids[i] = hv[(size_t)i];
     return TCM_OK;
 }
 
 tcm_status tcm_updates(const tcm_sim *cs, int64_t *cell_updates)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s || !cell_updates) return TCM_EINVAL;
-    DeviceGuard g(s->device);
-    if (!s->started) {
-        *cell_updates = 0;
-        return TCM_OK;
-    }
-    EngineState es{};
-    TRY(cudaMemcpyAsync(&es, s->E.st, sizeof(es), cudaMemcpyDeviceToHost, s->stream));
-    TRY(cudaStreamSynchronize(s->stream));
-    *cell_updates = (int64_t)es.updates;
+    HostSim *h = sim_of(cs);
+    if (!h || !cell_updates) return TCM_EINVAL;
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
+    unsigned long long u = 0;
+    TRY(cudaMemcpyAsync(&u, &b->E.sims[cs->id].updates, sizeof(u), cudaMemcpyDeviceToHost, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
+    *cell_updates = (int64_t)u;
     return TCM_OK;
 }
 
 tcm_status tcm_energy(const tcm_sim *cs, double *e_out)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s || !e_out) return TCM_EINVAL;
-    DeviceGuard g(s->device);
-    tcm_status st = start(s);
-    if (st != TCM_OK) return st;
+    HostSim *h = sim_of(cs);
+    if (!h || !e_out) return TCM_EINVAL;
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
+    TRYS(ready_for_read(b, cs->id));
     double *d = nullptr;
     TRY(cudaMalloc(&d, sizeof(double)));
-    double h = 0.0;
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double), s->stream);
-    if (e == cudaSuccess) e = launch_energy(s->E, 0, (int)(s->step & 1), s->list_parity, d, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    double hv = 0.0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double), b->stream);
+    if (e == cudaSuccess) e = launch_energy(b->E, cs->id, (int)(h->step & 1), b->list_parity, d, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hv, d, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     cudaFree(d);
     TRY(e);
-    *e_out = h;
+    *e_out = hv;
     return TCM_OK;
 }
 
-tcm_status tcm_brick_media(const tcm_sim *cs, int64_t b, int *kind, float *k)
+tcm_status tcm_brick_media(const tcm_sim *cs, int64_t bi, int *kind, float *k)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s || b < 0 || b >= s->n_bricks || !kind) return TCM_EINVAL;
-    DeviceGuard g(s->device);
+    HostSim *h = sim_of(cs);
+    if (!h || bi < 0 || bi >= h->n_bricks || !kind) return TCM_EINVAL;
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
     int ks = 0;
     float kv = 0.f;
-    TRY(cudaMemcpyAsync(&ks, s->E.kslab_of_brick + b, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    TRY(cudaMemcpyAsync(&kv, s->E.kscal + b, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    TRY(cudaStreamSynchronize(s->stream));
+    TRY(cudaMemcpyAsync(&ks, b->E.kslab_of_brick + h->brick_base + bi, sizeof(int), cudaMemcpyDeviceToHost,
+                        b->stream));
+    TRY(cudaMemcpyAsync(&kv, b->E.kscal + h->brick_base + bi, sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
     *kind = ks >= 0 ? 2 : 1;
     if (k) *k = ks >= 0 ? 0.f : kv;
     return TCM_OK;
@@ -706,43 +949,31 @@ tcm_status tcm_brick_media(const tcm_sim *cs, int64_t b, int *kind, float *k)
 
 tcm_status tcm_pool_info(const tcm_sim *cs, int64_t *slots, int64_t *free_slots)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s) return TCM_EINVAL;
-    DeviceGuard g(s->device);
-    if (slots) *slots = s->n_slots;
-    if (!free_slots) return TCM_OK;
-    if (!s->started) {
-        *free_slots = s->n_slots;
-        return TCM_OK;
-    }
-    EngineState es{};
-    TRY(cudaMemcpyAsync(&es, s->E.st, sizeof(es), cudaMemcpyDeviceToHost, s->stream));
-    TRY(cudaStreamSynchronize(s->stream));
-    *free_slots = std::max(es.free_top, 0) + es.n_retired;
-    return TCM_OK;
+    if (!sim_of(cs)) return TCM_EINVAL;
+    return tcm_batch_info(cs->b, slots, free_slots, nullptr);
 }
 
 tcm_status tcm_phase_ns(const tcm_sim *cs, int64_t *stepping, int64_t *update, int64_t *compaction)
 {
-    tcm_sim *s = const_cast<tcm_sim *>(cs);
-    if (!s) return TCM_EINVAL;
-    int64_t v[3] = {0, 0, 0};
-    if (s->started) {
-        DeviceGuard g(s->device);
-        EngineState es{};
-        TRY(cudaMemcpyAsync(&es, s->E.st, sizeof(es), cudaMemcpyDeviceToHost, s->stream));
-        TRY(cudaStreamSynchronize(s->stream));
-        for (int i = 0; i < 3; ++i) v[i] = (int64_t)es.phase_ns[i];
-    }
-    if (stepping) *stepping = v[0];
-    if (update) *update = v[1];
-    if (compaction) *compaction = v[2];
+    if (!sim_of(cs)) return TCM_EINVAL;
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
+    EngineState es{};
+    TRY(cudaMemcpyAsync(&es, b->E.st, sizeof(es), cudaMemcpyDeviceToHost, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
+    if (stepping) *stepping = (int64_t)es.phase_ns[0];
+    if (update) *update = (int64_t)es.phase_ns[1];
+    if (compaction) *compaction = (int64_t)es.phase_ns[2];
     return TCM_OK;
 }
 
-int64_t tcm_launch_count(const tcm_sim *s) { return s ? s->launches : -1; }
+int64_t tcm_launch_count(const tcm_sim *s) { return sim_of(s) ? s->b->launches : -1; }
 
-int64_t tcm_step_index(const tcm_sim *s) { return s ? s->step : -1; }
+int64_t tcm_step_index(const tcm_sim *s)
+{
+    HostSim *h = sim_of(s);
+    return h ? h->step : -1;
+}
 
 const char *tcm_status_string(tcm_status st)
 {
@@ -761,12 +992,122 @@ const char *tcm_status_string(tcm_status st)
 void tcm_destroy(tcm_sim *s)
 {
     if (!s) return;
-    DeviceGuard g(s->device);
-    if (s->stream || true) cudaStreamSynchronize(s->stream);
-    for (void *p : s->allocs) cudaFree(p);
-    if (s->own_pool && s->pool) cudaFree(s->pool);
-    if (s->h_err) cudaFreeHost(s->h_err);
-    delete s;
+    if (s->owns_batch) {
+        tcm_batch_destroy(s->b);   // also deletes s
+        return;
+    }
+    tcm_batch_remove(s->b, s);
+}
+
+// ---- batches --------------------------------------------------------------
+
+tcm_status tcm_batch_create(const tcm_batch_options *o, tcm_batch **out)
+{
+    if (!out) return TCM_EINVAL;
+    *out = nullptr;
+    if (!o || o->storage != TCM_STORAGE_F32) return TCM_EINVAL;
+    return batch_new(o->device, (cudaStream_t)o->stream, o->pool_ptr, o->pool_bytes, o->max_bricks, o->max_sims,
+                     out);
+}
+
+tcm_status tcm_batch_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_model *velocity, double dx,
+                         double dt, double threshold, tcm_brick brick, int threshold_mode, float decay_alpha,
+                         int decay_steps, int dense, int64_t n_steps, tcm_sim **out)
+{
+    if (!b || !out) return TCM_EINVAL;
+    *out = nullptr;
+    TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, TCM_STORAGE_F32, threshold_mode, decay_steps));
+    if (b->poisoned) return TCM_ESTATE;
+    DeviceGuard g(b->device);
+    int id = -1;
+    TRYS(sim_add(b, domain, velocity, dx, dt, threshold, threshold_mode, decay_alpha, decay_steps, dense ? 1 : 0,
+                 n_steps, &id));
+    tcm_sim *s = new (std::nothrow) tcm_sim();
+    if (!s) {
+        sim_release(b, id);
+        return TCM_ENOMEM;
+    }
+    s->b = b;
+    s->id = id;
+    s->owns_batch = false;
+    b->handles[id] = s;
+    *out = s;
+    return TCM_OK;
+}
+
+tcm_status tcm_batch_step_async(tcm_batch *b, int64_t n)
+{
+    if (!b || n < 0) return TCM_EINVAL;
+    return batch_step_async(b, n);
+}
+
+tcm_status tcm_batch_sync(tcm_batch *b)
+{
+    if (!b) return TCM_EINVAL;
+    DeviceGuard g(b->device);
+    if (b->poisoned && b->sticky != TCM_OK) return b->sticky;
+    return sync_status(b);
+}
+
+tcm_status tcm_batch_step(tcm_batch *b, int64_t n)
+{
+    tcm_status st = tcm_batch_step_async(b, n);
+    if (st != TCM_OK) return st;
+    return tcm_batch_sync(b);
+}
+
+tcm_status tcm_sim_done(const tcm_sim *s, int *done)
+{
+    HostSim *h = sim_of(s);
+    if (!h || !done) return TCM_EINVAL;
+    *done = (h->target > 0 && h->step >= h->target) ? 1 : 0;
+    return TCM_OK;
+}
+
+tcm_status tcm_batch_remove(tcm_batch *b, tcm_sim *s)
+{
+    if (!b || !s || s->b != b || !sim_of(s)) return TCM_EINVAL;
+    const int id = s->id;
+    tcm_status st = sim_release(b, id);
+    b->handles[id] = nullptr;
+    if (!s->owns_batch) delete s;
+    return st;
+}
+
+tcm_status tcm_batch_info(const tcm_batch *cb, int64_t *slots, int64_t *free_slots, int *sims)
+{
+    tcm_batch *b = const_cast<tcm_batch *>(cb);
+    if (!b) return TCM_EINVAL;
+    DeviceGuard g(b->device);
+    if (slots) *slots = b->n_slots;
+    if (sims) {
+        int n = 0;
+        for (const auto &h : b->sims) n += h.used ? 1 : 0;
+        *sims = n;
+    }
+    if (free_slots) {
+        EngineState es{};
+        TRY(cudaMemcpyAsync(&es, b->E.st, sizeof(es), cudaMemcpyDeviceToHost, b->stream));
+        TRY(cudaStreamSynchronize(b->stream));
+        *free_slots = std::max(es.free_top, 0) + es.n_retired;
+    }
+    return TCM_OK;
+}
+
+void tcm_batch_destroy(tcm_batch *b)
+{
+    if (!b) return;
+    DeviceGuard g(b->device);
+    cudaStreamSynchronize(b->stream);
+    for (auto &h : b->sims)
+        if (h.kslabs) cudaFree(h.kslabs);
+    for (tcm_sim *s : b->handles) delete s;
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->d_src) cudaFree(b->d_src);
+    if (b->d_wave) cudaFree(b->d_wave);
+    if (b->own_pool && b->pool) cudaFree(b->pool);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    delete b;
 }
 
 }  // extern "C"

@@ -10,6 +10,7 @@
 //             sd_of_brick[g]    uint16   Shutdown_log: shut-down steps left (bits 0-14) and
 //                                        "holds a source" (bit 15)
 //             bitmap[g/32]      bit      active for the next step (drives the compaction)
+//             sim_of_word[g/32] uint16   simulation owning those 32 bricks
 //   per box   meta[slot]        16 B     Box2cell brick id, bulk index, scalar k, sim/sd flags
 //             rec[slot][8]      float    6 face maxima, cell maximum, max |phi^{n+1}|
 //   lists     items[2][n_slots] 48 B     active bricks in brick order (double-buffered): box,
@@ -74,11 +75,15 @@ struct SimDev {
     float alpha;
     int decay_steps;
     int src_begin, src_end;
+    const float *kslabs;   // this sim's bulked coefficient bricks
+    int live;              // 1 while the sim steps (0: frozen or released)
+    int pad1;
     // mutable (device-owned)
     long long step;        // n of phi^n
     unsigned gmax[2];      // max |phi^{n+1}| of step n in gmax[n & 1] (float bits)
     unsigned poisoned;
     unsigned pad;
+    unsigned long long updates;   // cumulative node updates of this sim
 };
 
 struct SrcDev {
@@ -113,9 +118,9 @@ struct Engine {
     int *slot_of_brick;
     const float *kscal;
     const int *kslab_of_brick;
-    const float *kslabs;
     unsigned short *sd_of_brick;
     unsigned *bitmap;
+    unsigned short *sim_of_word;   // owning sim of each 32-brick bitmap word
     long long n_words;
     int *blocktot;
     int words_per_block;
@@ -146,19 +151,26 @@ struct MediaDev {
 
 // ---- launchers (tcm_kernels.cu) -------------------------------------------
 // Every launcher returns the cudaError_t of its launch.
+// Bulking of one sim whose bricks start at global index bb.
 cudaError_t launch_bulk_classify(const MediaDev &m, int nx, int ny, int nz, int mx, int my, int mz,
-                                 double dt, double dx, float *kscal, int *kslab_of_brick,
+                                 double dt, double dx, long long bb, float *kscal, int *kslab_of_brick,
                                  int *n_kslabs, cudaStream_t s);
 cudaError_t launch_bulk_fill(const MediaDev &m, int nx, int ny, int nz, int mx, int my, int mz,
-                             double dt, double dx, const int *kslab_of_brick, float *kslabs,
+                             double dt, double dx, long long bb, const int *kslab_of_brick, float *kslabs,
                              cudaStream_t s);
 cudaError_t launch_iota_desc(int *a, int n, int first, cudaStream_t s);
-cudaError_t launch_prime(const Engine &e, int sim, const long long *bricks, long long n,
-                         int slot0, cudaStream_t s);
+// Between steps: fold the boxes released by the last step into the free stack.
+cudaError_t launch_settle(const Engine &e, cudaStream_t s);
+// Box bricks[0..n) (local ids; all n bricks when bricks == nullptr) of sim,
+// zeroed, popped from the free stack.
+cudaError_t launch_admit(const Engine &e, int sim, const long long *bricks, long long n, cudaStream_t s);
+// Take every brick of sim out of the active set (boxes stay) / release its boxes.
+cudaError_t launch_freeze(const Engine &e, int sim, long long words_begin, long long n_words, cudaStream_t s);
+cudaError_t launch_release(const Engine &e, int sim, long long bb, long long n, cudaStream_t s);
 // Rebuild the active list `list_parity` from the bitmap (same grid as the step).
 cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStream_t s);
-cudaError_t launch_zero_slots(const Engine &e, int slot0, long long n, cudaStream_t s);
-cudaError_t launch_scatter_field(const Engine &e, const float *packed, long long n, int slot0,
+// packed[i] = {phi^n, phi^{n-1}} of global brick gids[i] (boxed), into its box.
+cudaError_t launch_scatter_field(const Engine &e, const float *packed, const long long *gids, long long n,
                                  int now_half, cudaStream_t s);
 cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s);
 int step_grid_size(int device);
@@ -167,8 +179,9 @@ cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0,
                                cudaStream_t s);
 cudaError_t launch_energy(const Engine &e, int sim, int now_half, int list_parity, double *out,
                           cudaStream_t s);
-cudaError_t launch_active_bricks(const Engine &e, int list_parity, long long *ids_out,
-                                 unsigned long long *cells_out, cudaStream_t s);
+// Active bricks of sim in the list: local ids (unsorted, count in *n_out) and in-domain nodes.
+cudaError_t launch_active_bricks(const Engine &e, int sim, int list_parity, long long *ids_out,
+                                 unsigned long long *n_out, unsigned long long *cells_out, cudaStream_t s);
 
 // Read-only view of a simulation for entry points defined outside tcm_api.cu.
 struct SimView {
@@ -178,6 +191,7 @@ struct SimView {
     bool started;
     long long step;
     int list_parity;
+    int sim;
 };
 
 }  // namespace tcm

@@ -187,6 +187,13 @@ __device__ __forceinline__ void flush_gmax(const Engine &E, float gacc, int gsim
     if (gsim >= 0 && gacc > 0.f) atomicMax(&E.sims[gsim].gmax[nh], __float_as_uint(gacc));
 }
 
+// Add a lane's node-update count to its sim's counter.
+__device__ __forceinline__ void flush_updates(const Engine &E, unsigned long long &n, int gsim)
+{
+    if (gsim >= 0 && n) atomicAdd(&E.sims[gsim].updates, n);
+    n = 0;
+}
+
 // ---------------------------------------------------------------------------
 // P1: Eq. 3 on one brick per TPB-lane segment, straight from global memory.
 // Each lane owns one float4 column (x4, y) of all BZ planes: it issues every
@@ -199,8 +206,8 @@ __device__ __forceinline__ void flush_gmax(const Engine &E, float gacc, int gsim
 // this (valid = false on a missing brick) so shuffles see full warps.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
-                                         bool share_xm, bool share_xp, unsigned long long &cells, float &gacc,
-                                         int &gsim, int &gnh)
+                                         bool share_xm, bool share_xp, unsigned long long &cells,
+                                         unsigned long long &scells, float &gacc, int &gsim, int &gnh)
 {
     const int x4 = t % XQ;
     const int y = t / XQ;
@@ -227,7 +234,9 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 #pragma unroll
         for (int z = 0; z < BZ; ++z) M[z] = __ldcs(prv4 + z * TPB + t);
         if (w.kslab >= 0) {
-            const float4 *k4 = reinterpret_cast<const float4 *>(E.kslabs + (size_t)w.kslab * BVOL);
+            const float *kbase = reinterpret_cast<const float *>(
+                __ldg(reinterpret_cast<const unsigned long long *>(&S->kslabs)));
+            const float4 *k4 = reinterpret_cast<const float4 *>(kbase + (size_t)w.kslab * BVOL);
 #pragma unroll
             for (int z = 0; z < BZ; ++z) K[z] = __ldg(k4 + z * TPB + t);
         } else {
@@ -352,6 +361,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         // (or its step parity) changes
         if (sim != gsim || nh != gnh) {
             flush_gmax(E, gacc, gsim, gnh);
+            flush_updates(E, scells, gsim);
             gsim = sim;
             gnh = nh;
             gacc = 0.f;
@@ -359,6 +369,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         gacc = fmaxf(gacc, qm);
         const int ex = min(BX, nx - cx * BX), ey = min(BY, ny - cy * BY), ez = min(BZ, nz - cz * BZ);
         cells += (unsigned long long)(ex * ey * ez);
+        scells += (unsigned long long)(ex * ey * ez);
     }
 }
 
@@ -503,19 +514,18 @@ __device__ long long block_sum(long long v)
 __device__ __forceinline__ void build_item(const Engine &E, long long g, WorkItem *out, int step_ahead,
                                            int &c_sim, long long &c_step)
 {
-    int si = 0;
-    for (int s = 1; s < E.n_sims; ++s)
-        if (g >= __ldg(&E.sims[s].brick_base)) si = s;
+    const int si = __ldg(E.sim_of_word + (g >> 5));
     const SimDev *S = E.sims + si;
     if (si != c_sim) {
         c_sim = si;
         c_step = __ldcg(&S->step);
     }
-    const int mx = __ldg(&S->mx), my = __ldg(&S->my), mz = __ldg(&S->mz);
+    const int mx = max(__ldg(&S->mx), 1), my = max(__ldg(&S->my), 1), mz = __ldg(&S->mz);
     const long long bb = __ldg(&S->brick_base);
     const int b = (int)(g - bb);
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
-    const int slot = __ldcg(E.slot_of_brick + g);
+    // a brick outside its sim's grid (never listed) gets no box
+    const int slot = (b >= 0 && cz < mz) ? __ldcg(E.slot_of_brick + g) : -1;
     const int kslab = __ldg(E.kslab_of_brick + g);
     const float kscal = __ldg(E.kscal + g);
     const unsigned sd = __ldcg(E.sd_of_brick + g);
@@ -716,7 +726,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
 
     // ---- P1: time stepping of every active brick -------------------------
     {
-        unsigned long long cells = 0;
+        unsigned long long cells = 0, scells = 0;
         float gacc = 0.f;
         int gsim = -1;
         int gnh = 0;
@@ -727,23 +737,26 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
         int i = pr * BRICKS_PER_WARP + seg;
         bool v = pr < npairs && i < nact;
         WorkItem w = load_item(L, v ? i : 0);
+        v = v && w.slot >= 0;
         while (pr < npairs) {
             // the next pair's item, loaded while this pair is stepped
             const int pn = pr + nwarps;
             const int in = pn * BRICKS_PER_WARP + seg;
-            const bool vn = pn < npairs && in < nact;
+            bool vn = pn < npairs && in < nact;
             const WorkItem wn = load_item(L, vn ? in : 0);
+            vn = vn && wn.slot >= 0;
             // is the second brick of the pair the x+ neighbour of the first?
             const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
             const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
             const bool pair_x = seg == 0 ? (other_v && w.nb[1] >= 0 && w.nb[1] == other_slot)
                                          : (v && w.nb[0] >= 0 && w.nb[0] == other_slot);
-            p1_brick(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, cells, gacc, gsim, gnh);
+            p1_brick(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, cells, scells, gacc, gsim, gnh);
             pr = pn;
             w = wn;
             v = vn;
         }
         flush_gmax(E, gacc, gsim, gnh);
+        flush_updates(E, scells, gsim);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(FULL, cells, o);
         if (lane == 0 && cells) atomicAdd(&st->updates, cells);
@@ -768,13 +781,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const float4 *r = reinterpret_cast<const float4 *>(E.rec + (size_t)w[u].slot * 8);
+                const float4 *r = reinterpret_cast<const float4 *>(E.rec + (size_t)max(w[u].slot, 0) * 8);
                 r0[u] = __ldcg(r);
                 r1[u] = __ldcg(r + 1);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (base + u * nthr < nact) p2_item(E, w[u], r0[u], r1[u], sc);
+                if (base + u * nthr < nact && w[u].slot >= 0) p2_item(E, w[u], r0[u], r1[u], sc);
         }
         // Manual activation of source bricks still being fed at step n+1.
         if (blockIdx.x == 0) {
@@ -814,6 +827,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
                 __threadfence();
                 for (int s = 0; s < E.n_sims; ++s) {
                     SimDev *S = E.sims + s;
+                    if (!__ldcg(&S->live)) continue;
                     const long long n = __ldcg(&S->step);
                     S->gmax[(n + 1) & 1] = 0u;
                     S->step = n + 1;
@@ -895,7 +909,7 @@ __device__ bool rules_uniform(const MediaDev &M, long long x0, long long x1, lon
 }
 
 __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
-                                double dx, float *kscal, int *kslab_of_brick, int *n_kslabs)
+                                double dx, long long bb, float *kscal, int *kslab_of_brick, int *n_kslabs)
 {
     const long long nb = (long long)mx * my * mz;
     const int lane = threadIdx.x & 31;
@@ -919,24 +933,24 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
         }
         if (lane == 0) {
             if (diff) {
-                kslab_of_brick[g] = atomicAdd(n_kslabs, 1);
-                kscal[g] = 0.f;
+                kslab_of_brick[bb + g] = atomicAdd(n_kslabs, 1);
+                kscal[bb + g] = 0.f;
             } else {
-                kslab_of_brick[g] = -1;
-                kscal[g] = k0;
+                kslab_of_brick[bb + g] = -1;
+                kscal[bb + g] = k0;
             }
         }
     }
 }
 
 __global__ void k_bulk_fill(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
-                            double dx, const int *kslab_of_brick, float *kslabs)
+                            double dx, long long bb, const int *kslab_of_brick, float *kslabs)
 {
     const long long nb = (long long)mx * my * mz;
     const int lane = threadIdx.x & 31;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nb; g += nw) {
-        const int ks = kslab_of_brick[g];
+        const int ks = kslab_of_brick[bb + g];
         if (ks < 0) continue;
         const long long cx = g % mx, cy = (g / mx) % my, cz = g / ((long long)mx * my);
         for (int e = lane; e < BVOL; e += 32) {
@@ -957,45 +971,98 @@ __global__ void k_iota_desc(int *a, int n, int first)
         a[i] = first - (int)i;
 }
 
-// Box the initial bricks: bricks[i] (or brick i when bricks == nullptr) gets
-// box slot0 + i; the active list is then built from the bitmap (k_compact).
-__global__ void k_prime(Engine E, int sim, const long long *bricks, long long n, int slot0)
+// Fold the boxes released by the last step into the free stack (the step
+// kernel does the same at its start); leaves the counters consistent for
+// admissions and releases between steps.
+__global__ void k_settle(Engine E)
+{
+    EngineState *st = E.st;
+    st->free_top = max(st->free_top, 0) + st->n_retired;
+    st->n_retired = 0;
+    st->n_new = 0;
+}
+
+// Box bricks[i] (or brick i) of sim: one warp per brick pops a vacant box,
+// writes Cell2box / Box2cell and the active bit, and zeroes the box.
+__global__ void k_admit(Engine E, int sim, const long long *bricks, long long n)
 {
     SimDev *S = E.sims + sim;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const int b = bricks ? (int)bricks[i] : (int)i;
-        const int slot = slot0 + (int)i;
         const long long g = S->brick_base + b;
-        E.slot_of_brick[g] = slot;
-        SlotMeta m;
-        m.brick = b;
-        m.kslab = E.kslab_of_brick[g];
-        m.kscal = E.kscal[g];
-        m.flags = ((unsigned)sim << 16) | (brick_has_src(E, S, b) ? FLAG_HAS_SRC : 0u);
-        store_meta(E.meta + slot, m);
-        atomicOr(E.bitmap + (g >> 5), 1u << (unsigned)(g & 31));
-        atomicAdd(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
+        int slot = -1;
+        if (lane == 0) {
+            const int idx = atomicSub(&E.st->free_top, 1) - 1;
+            if (idx < 0) {
+                atomicAdd(&E.st->free_top, 1);
+                atomicOr(&E.st->err, ERR_NOMEM);
+                atomicOr(&S->poisoned, 1u);
+            } else {
+                slot = E.free_stack[idx];
+                E.slot_of_brick[g] = slot;
+                SlotMeta m;
+                m.brick = b;
+                m.kslab = E.kslab_of_brick[g];
+                m.kscal = E.kscal[g];
+                m.flags = ((unsigned)sim << 16) | (brick_has_src(E, S, b) ? FLAG_HAS_SRC : 0u);
+                store_meta(E.meta + slot, m);
+                E.sd_of_brick[g] &= (unsigned short)FLAG_HAS_SRC;
+                atomicOr(E.bitmap + (g >> 5), 1u << (unsigned)(g & 31));
+                atomicAdd(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
+            }
+        }
+        slot = __shfl_sync(FULL, slot, 0);
+        if (slot < 0) continue;
+        float4 *p = reinterpret_cast<float4 *>(E.phi + (size_t)slot * 2 * BVOL);
+        for (int e = lane; e < 2 * BVOL / 4; e += 32) p[e] = f4zero();
     }
 }
 
-__global__ void k_zero_slots(float *phi, int slot0, long long n)
+// Take sim's bricks out of the active set; their boxes (and fields) stay.
+__global__ void k_freeze(Engine E, int sim, long long w0, long long n_words)
 {
-    float4 *p = reinterpret_cast<float4 *>(phi + (size_t)slot0 * 2 * BVOL);
-    const long long total = n * 2 * BVOL / 4;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-        p[i] = f4zero();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_words; i += (long long)gridDim.x * blockDim.x) {
+        const long long w = w0 + i;
+        const int c = __popc(E.bitmap[w]);
+        if (c) {
+            E.bitmap[w] = 0u;
+            atomicSub(E.blocktot + (int)(w / E.words_per_block), c);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) E.sims[sim].live = 0;
 }
 
-// packed[i] = {now brick (BVOL), prev brick (BVOL)} for box slot0 + i.
-__global__ void k_scatter_field(float *phi, const float *packed, long long n, int slot0, int now_half)
+// Release every box of sim's bricks [bb, bb + n) back to the free stack.
+__global__ void k_release(Engine E, int sim, long long bb, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long g = bb + i;
+        const int slot = E.slot_of_brick[g];
+        if (slot < 0) continue;
+        const int idx = atomicAdd(&E.st->free_top, 1);
+        E.free_stack[idx] = slot;
+        E.slot_of_brick[g] = -1;
+        E.sd_of_brick[g] = 0;
+        const unsigned bit = 1u << (unsigned)(g & 31);
+        if (atomicAnd(E.bitmap + (g >> 5), ~bit) & bit)
+            atomicSub(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) E.sims[sim].live = 0;
+}
+
+// packed[i] = {phi^n, phi^{n-1}} of boxed global brick gids[i].
+__global__ void k_scatter_field(Engine E, const float *packed, const long long *gids, long long n, int now_half)
 {
     const long long total = n * 2 * BVOL;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long brick = i / (2 * BVOL);
+        const long long bi = i / (2 * BVOL);
         const int r = (int)(i % (2 * BVOL));
         const int which = r / BVOL, e = r % BVOL;
         const int half = which == 0 ? now_half : (now_half ^ 1);
-        phi[((size_t)(slot0 + brick) * 2 + half) * BVOL + e] = packed[i];
+        const int slot = E.slot_of_brick[gids[bi]];
+        if (slot >= 0) E.phi[((size_t)slot * 2 + half) * BVOL + e] = packed[i];
     }
 }
 
@@ -1052,7 +1119,7 @@ __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *ou
         const double nb = prev_at(E, S, ph, x - 1, y, z) + prev_at(E, S, ph, x + 1, y, z) +
                           prev_at(E, S, ph, x, y - 1, z) + prev_at(E, S, ph, x, y + 1, z) +
                           prev_at(E, S, ph, x, y, z - 1) + prev_at(E, S, ph, x, y, z + 1);
-        const double k = m.kslab >= 0 ? (double)E.kslabs[(size_t)m.kslab * BVOL + e] : (double)m.kscal;
+        const double k = m.kslab >= 0 ? (double)S->kslabs[(size_t)m.kslab * BVOL + e] : (double)m.kscal;
         const double d = a - bb;
         acc += d * d / k + a * (6.0 * bb - nb);
     }
@@ -1061,16 +1128,18 @@ __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *ou
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
-__global__ void k_active_bricks(Engine E, int parity, long long *ids, unsigned long long *cells)
+// Boxed bricks of sim (its active set; a frozen sim keeps the set it ended
+// with): local ids (unsorted, count in *count) and in-domain nodes.
+__global__ void k_active_bricks(Engine E, int sim, long long *ids, unsigned long long *count,
+                                unsigned long long *cells)
 {
-    const WorkItem *L = parity ? E.items1 : E.items0;
-    const int n = E.st->n_active[parity];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const SlotMeta m = load_meta(E.meta + L[i].slot);
-        const SimDev *S = E.sims + (m.flags >> 16);
-        const int b = m.brick;
-        if (ids) ids[i] = b;
-        const int cx = b % S->mx, cy = (b / S->mx) % S->my, cz = b / (S->mx * S->my);
+    const SimDev *S = E.sims + sim;
+    const long long bb = S->brick_base, nb = S->n_bricks;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        if (E.slot_of_brick[bb + b] < 0) continue;
+        const unsigned long long k = atomicAdd(count, 1ull);
+        if (ids) ids[k] = b;
+        const int cx = (int)(b % S->mx), cy = (int)((b / S->mx) % S->my), cz = (int)(b / ((long long)S->mx * S->my));
         const int ex = min(BX, S->nx - cx * BX), ey = min(BY, S->ny - cy * BY), ez = min(BZ, S->nz - cz * BZ);
         if (cells) atomicAdd(cells, (unsigned long long)(ex * ey * ez));
     }
@@ -1090,21 +1159,21 @@ int grid_for(long long work, int block)
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_bulk_classify(const MediaDev &m, int nx, int ny, int nz, int mx, int my, int mz,
-                                 double dt, double dx, float *kscal, int *kslab_of_brick,
+                                 double dt, double dx, long long bb, float *kscal, int *kslab_of_brick,
                                  int *n_kslabs, cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_classify<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, kscal,
+    k_bulk_classify<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, bb, kscal,
                                                            kslab_of_brick, n_kslabs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bulk_fill(const MediaDev &m, int nx, int ny, int nz, int mx, int my, int mz,
-                             double dt, double dx, const int *kslab_of_brick, float *kslabs,
+                             double dt, double dx, long long bb, const int *kslab_of_brick, float *kslabs,
                              cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_fill<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx,
+    k_bulk_fill<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, bb,
                                                        kslab_of_brick, kslabs);
     return cudaGetLastError();
 }
@@ -1116,11 +1185,28 @@ cudaError_t launch_iota_desc(int *a, int n, int first, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_prime(const Engine &e, int sim, const long long *bricks, long long n, int slot0,
-                         cudaStream_t s)
+cudaError_t launch_settle(const Engine &e, cudaStream_t s)
+{
+    k_settle<<<1, 1, 0, s>>>(e);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_admit(const Engine &e, int sim, const long long *bricks, long long n, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_prime<<<grid_for(n, 256), 256, 0, s>>>(e, sim, bricks, n, slot0);
+    k_admit<<<grid_for(n * 32, 256), 256, 0, s>>>(e, sim, bricks, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_freeze(const Engine &e, int sim, long long words_begin, long long n_words, cudaStream_t s)
+{
+    k_freeze<<<grid_for(n_words, 256), 256, 0, s>>>(e, sim, words_begin, n_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_release(const Engine &e, int sim, long long bb, long long n, cudaStream_t s)
+{
+    k_release<<<grid_for(n, 256), 256, 0, s>>>(e, sim, bb, n);
     return cudaGetLastError();
 }
 
@@ -1130,18 +1216,11 @@ cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_slots(const Engine &e, int slot0, long long n, cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    k_zero_slots<<<grid_for(n * 2 * BVOL / 4, 256), 256, 0, s>>>(e.phi, slot0, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scatter_field(const Engine &e, const float *packed, long long n, int slot0,
+cudaError_t launch_scatter_field(const Engine &e, const float *packed, const long long *gids, long long n,
                                  int now_half, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_scatter_field<<<grid_for(n * 2 * BVOL, 256), 256, 0, s>>>(e.phi, packed, n, slot0, now_half);
+    k_scatter_field<<<grid_for(n * 2 * BVOL, 256), 256, 0, s>>>(e, packed, gids, n, now_half);
     return cudaGetLastError();
 }
 
@@ -1177,10 +1256,11 @@ cudaError_t launch_energy(const Engine &e, int sim, int now_half, int list_parit
     return cudaGetLastError();
 }
 
-cudaError_t launch_active_bricks(const Engine &e, int list_parity, long long *ids_out,
-                                 unsigned long long *cells_out, cudaStream_t s)
+cudaError_t launch_active_bricks(const Engine &e, int sim, int list_parity, long long *ids_out,
+                                 unsigned long long *n_out, unsigned long long *cells_out, cudaStream_t s)
 {
-    k_active_bricks<<<256, 256, 0, s>>>(e, list_parity, ids_out, cells_out);
+    (void)list_parity;
+    k_active_bricks<<<1024, 256, 0, s>>>(e, sim, ids_out, n_out, cells_out);
     return cudaGetLastError();
 }
 

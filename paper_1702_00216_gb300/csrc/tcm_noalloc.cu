@@ -42,7 +42,7 @@ __device__ __forceinline__ double prev_node(const tcm::Engine &E, const tcm::Sim
 
 // One warp per active brick: its energy contribution, reduced in a fixed
 // order so the result does not depend on scheduling.
-__global__ void k_energy_partials(tcm::Engine E, int now_half, int parity, int n, double *part)
+__global__ void k_energy_partials(tcm::Engine E, int sim, int now_half, int parity, int n, double *part)
 {
     using namespace tcm;
     const int lane = threadIdx.x & 31;
@@ -55,6 +55,10 @@ __global__ void k_energy_partials(tcm::Engine E, int now_half, int parity, int n
         const int b = mv.x, kslab = mv.y;
         const double kscal = (double)__int_as_float(mv.z);
         const SimDev *S = E.sims + ((unsigned)mv.w >> 16);
+        if ((int)((unsigned)mv.w >> 16) != sim) {
+            if (lane == 0) part[i] = 0.0;
+            continue;
+        }
         const long long bx0 = (long long)(b % S->mx) * BX, by0 = (long long)((b / S->mx) % S->my) * BY,
                         bz0 = (long long)(b / (S->mx * S->my)) * BZ;
         double acc = 0.0;
@@ -66,7 +70,7 @@ __global__ void k_energy_partials(tcm::Engine E, int now_half, int parity, int n
             const double nb = prev_node(E, S, ph, x - 1, y, z) + prev_node(E, S, ph, x + 1, y, z) +
                               prev_node(E, S, ph, x, y - 1, z) + prev_node(E, S, ph, x, y + 1, z) +
                               prev_node(E, S, ph, x, y, z - 1) + prev_node(E, S, ph, x, y, z + 1);
-            const double k = kslab >= 0 ? (double)E.kslabs[(size_t)kslab * BVOL + e] : kscal;
+            const double k = kslab >= 0 ? (double)S->kslabs[(size_t)kslab * BVOL + e] : kscal;
             const double d = a - bb;
             acc += d * d / k + a * (6.0 * bb - nb);
         }
@@ -129,7 +133,7 @@ extern "C" tcm_status tcm_energy_noalloc(const tcm_sim *sim, double *device_out)
         double *part = g_partials_addr[v.device];
         if (n > 0) {
             const int blocks = (n + 7) / 8;
-            k_energy_partials<<<blocks, 256, 0, v.stream>>>(*v.E, (int)(v.step & 1), v.list_parity, n, part);
+            k_energy_partials<<<blocks, 256, 0, v.stream>>>(*v.E, v.sim, (int)(v.step & 1), v.list_parity, n, part);
         }
         k_energy_total<<<1, FINAL_THREADS, 0, v.stream>>>(part, n, device_out);
         if (cudaGetLastError() != cudaSuccess) st = TCM_EDEVICE;

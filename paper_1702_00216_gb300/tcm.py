@@ -26,7 +26,9 @@ EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "t
            "tcm_active_count", "tcm_active_bricks", "tcm_updates", "tcm_energy",
            "tcm_energy_noalloc",
            "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_step_index",
-           "tcm_status_string", "tcm_destroy"]
+           "tcm_status_string", "tcm_destroy", "tcm_batch_create", "tcm_batch_add",
+           "tcm_batch_step", "tcm_batch_step_async", "tcm_batch_sync", "tcm_sim_done",
+           "tcm_batch_remove", "tcm_batch_info", "tcm_batch_destroy"]
 
 
 class tcm_domain(C.Structure):
@@ -47,6 +49,12 @@ class tcm_options(C.Structure):
     _fields_ = [("threshold_mode", C.c_int), ("decay_alpha", C.c_float), ("decay_steps", C.c_int),
                 ("pool_ptr", C.c_void_p), ("pool_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("storage", C.c_int), ("dense", C.c_int), ("device", C.c_int)]
+
+
+class tcm_batch_options(C.Structure):
+    _fields_ = [("pool_ptr", C.c_void_p), ("pool_bytes", C.c_size_t), ("stream", C.c_void_p),
+                ("device", C.c_int), ("storage", C.c_int), ("max_bricks", C.c_int64),
+                ("max_sims", C.c_int)]
 
 
 class TCMError(RuntimeError):
@@ -89,6 +97,16 @@ def lib():
             "tcm_step_index": ([_vp], _i64),
             "tcm_status_string": ([C.c_int], C.c_char_p),
             "tcm_destroy": ([_vp], None),
+            "tcm_batch_create": ([_vp, _vp], C.c_int),
+            "tcm_batch_add": ([_vp, _vp, _vp, C.c_double, C.c_double, C.c_double, tcm_brick, C.c_int,
+                               C.c_float, C.c_int, C.c_int, _i64, _vp], C.c_int),
+            "tcm_batch_step": ([_vp, _i64], C.c_int),
+            "tcm_batch_step_async": ([_vp, _i64], C.c_int),
+            "tcm_batch_sync": ([_vp], C.c_int),
+            "tcm_sim_done": ([_vp, _vp], C.c_int),
+            "tcm_batch_remove": ([_vp, _vp], C.c_int),
+            "tcm_batch_info": ([_vp, _vp, _vp, _vp], C.c_int),
+            "tcm_batch_destroy": ([_vp], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -256,6 +274,58 @@ def tcm_destroy(h):
     lib().tcm_destroy(h)
 
 
+def tcm_batch_create(options) -> int:
+    out = _vp()
+    _chk(lib().tcm_batch_create(C.byref(options), C.byref(out)), "tcm_batch_create")
+    return out.value
+
+
+def tcm_batch_add(b, shape, media, dx, dt, threshold, brick, thr_mode, decay_alpha, decay_steps,
+                  dense=False, n_steps=0) -> int:
+    nz, ny, nx = shape
+    dom = tcm_domain(nx, ny, nz)
+    vm, keep = velocity_model(media)
+    out = _vp()
+    rc = lib().tcm_batch_add(b, C.byref(dom), C.byref(vm), float(dx), float(dt), float(threshold),
+                             tcm_brick(*brick), int(thr_mode), float(decay_alpha), int(decay_steps),
+                             int(bool(dense)), int(n_steps), C.byref(out))
+    del keep
+    _chk(rc, "tcm_batch_add")
+    return out.value
+
+
+def tcm_batch_step(b, n=1):
+    _chk(lib().tcm_batch_step(b, int(n)), "tcm_batch_step")
+
+
+def tcm_batch_step_async(b, n=1):
+    _chk(lib().tcm_batch_step_async(b, int(n)), "tcm_batch_step_async")
+
+
+def tcm_batch_sync(b):
+    _chk(lib().tcm_batch_sync(b), "tcm_batch_sync")
+
+
+def tcm_sim_done(h) -> bool:
+    d = C.c_int(0)
+    _chk(lib().tcm_sim_done(h, C.byref(d)), "tcm_sim_done")
+    return bool(d.value)
+
+
+def tcm_batch_remove(b, h):
+    _chk(lib().tcm_batch_remove(b, h), "tcm_batch_remove")
+
+
+def tcm_batch_info(b):
+    s, f, n = C.c_int64(0), C.c_int64(0), C.c_int(0)
+    _chk(lib().tcm_batch_info(b, C.byref(s), C.byref(f), C.byref(n)), "tcm_batch_info")
+    return s.value, f.value, n.value
+
+
+def tcm_batch_destroy(b):
+    lib().tcm_batch_destroy(b)
+
+
 # ---- convenience wrapper ----------------------------------------------------
 def _torch():
     try:
@@ -301,6 +371,19 @@ class Sim:
         opts.stream = stream or None
         self._h = None
         self._h = tcm_create(self.shape, media, dx, dt, threshold, brick, opts)
+
+    @classmethod
+    def _wrap(cls, handle, shape, brick):
+        s = cls.__new__(cls)
+        s.shape = tuple(int(v) for v in shape)
+        nz, ny, nx = s.shape
+        bx, by, bz = brick
+        s.brick = (bx, by, bz)
+        s.mx, s.my, s.mz = -(-nx // bx), -(-ny // by), -(-nz // bz)
+        s._pool = None
+        s._h = handle
+        s._borrowed = True
+        return s
 
     @classmethod
     def from_workload(cls, wl, dense=False, **kw):
@@ -366,10 +449,13 @@ class Sim:
     def step_index(self):
         return tcm_step_index(self._h)
 
+    def done(self):
+        return tcm_sim_done(self._h)
+
     def close(self):
-        if self._h:
+        if self._h and not getattr(self, "_borrowed", False):
             tcm_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -382,3 +468,76 @@ class Sim:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Many simulations stepped together by one launch per step (tcm_batch_*)."""
+
+    def __init__(self, pool_bytes, max_bricks, max_sims=64, device=0, stream=None,
+                 pool_tensor=None):
+        torch = _torch()
+        o = tcm_batch_options()
+        o.pool_bytes = int(pool_bytes)
+        o.device = int(device)
+        o.storage = TCM_STORAGE_F32
+        o.max_bricks = int(max_bricks)
+        o.max_sims = int(max_sims)
+        self._pool = None
+        if pool_tensor is not None:
+            self._pool = pool_tensor
+        elif torch is not None and torch.cuda.is_available():
+            self._pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+        if self._pool is not None:
+            o.pool_ptr = int(self._pool.data_ptr())
+            o.pool_bytes = int(self._pool.numel() * self._pool.element_size())
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream(device).cuda_stream
+        o.stream = stream or None
+        self._h = None
+        self._h = tcm_batch_create(o)
+        self._sims = []
+
+    def add(self, wl, n_steps=0, dense=False):
+        """Add a workloads.Workload (with its sources); returns a Sim bound to the batch."""
+        h = tcm_batch_add(self._h, wl.shape, wl.media, wl.dx, wl.dt, wl.tau, wl.brick, wl.thr_mode,
+                          wl.decay_alpha, wl.decay_steps, dense=dense, n_steps=n_steps)
+        sim = Sim._wrap(h, wl.shape, wl.brick)
+        for x, y, z, w in wl.sources:
+            sim.add_source(x, y, z, np.asarray(w, dtype=np.float32))
+        self._sims.append(sim)
+        return sim
+
+    def step(self, n=1):
+        tcm_batch_step(self._h, n)
+
+    def step_async(self, n=1):
+        tcm_batch_step_async(self._h, n)
+
+    def sync(self):
+        tcm_batch_sync(self._h)
+
+    def remove(self, sim):
+        tcm_batch_remove(self._h, sim._h)
+        sim._h = None
+        self._sims = [s for s in self._sims if s is not sim]
+
+    def info(self):
+        """(boxes in the pool, free boxes, simulations alive)."""
+        return tcm_batch_info(self._h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            for s in self._sims:
+                s._h = None
+            tcm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
