@@ -206,6 +206,8 @@ def run_ours(args, rank, world, local_rank):
         extra = time_to_solution(torch, tcm, W, wl, dev, local_rank)
     e2e = end_to_end(torch, tcm, W, wl, local_rank) if not args.quick else None
     cpu = cpu_baseline(W, args, wl=wl) if (rank == 0 and world == 1 and not args.quick) else None
+    serving = serving_leg(torch, W, args, local_rank) if (not args.quick and args.serving > 0) else None
+    precision = precision_leg(torch, tcm, W, dev, local_rank) if (rank == 0 and not args.quick) else None
 
     if rank != 0:
         return
@@ -244,6 +246,10 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
     }
     line.update(extra)
+    if serving is not None:
+        line["serving"] = serving
+    if precision is not None:
+        line["precision"] = precision
     print(json.dumps(line), flush=True)
 
 
@@ -280,6 +286,87 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
         "dense_cell_updates": out["dense"]["cell_updates"],
         "max_abs_diff_tcm_vs_dense": out["max_abs_diff_tcm_vs_dense"],
         "max_abs_field": out["max_abs_field"]}}
+
+
+def precision_leg(torch, tcm, W, dev, local_rank):
+    """Field storage FP32 / BF16 / FP16 on the 256^3 layered, perturbed medium
+    (relative threshold 1e-6, 20-step decay), 800 steps each: device time of
+    the steps, node updates/s, HBM GB/s at the storage's algorithmic bytes per
+    update, max and RMS error of phi^800 against the FP32 run (which is within
+    ~1e-6 of the FP64 dense grid), and the drift of the leapfrog energy from
+    step len(wavelet)+50 to step 800 (FP64 reduction on the device)."""
+    wl = W.precision(256, 800)
+    n_src = len(wl.sources[0][3])
+    out = {"workload": f"{wl.name}, 800 steps, relative threshold 1e-6, 20-step decay"}
+    ref = None
+    for st in ("f32", "bf16", "f16"):
+        s = tcm.Sim.from_workload(wl, device=local_rank, storage=st)
+        s.step(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        u0 = s.updates
+        e0.record()
+        s.step_async(n_src + 49)
+        e1.record()
+        s.sync()
+        ms = e0.elapsed_time(e1)
+        en_a = s.energy()
+        u1 = s.updates
+        e0.record()
+        s.step_async(800 - n_src - 50)
+        e1.record()
+        s.sync()
+        ms += e0.elapsed_time(e1)
+        en_b = s.energy()
+        upd = s.updates - u0
+        buf = torch.empty(wl.shape, dtype=torch.float32, device=dev)
+        tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
+        torch.cuda.synchronize()
+        bpu = 16 if st == "f32" else 10
+        r = {"updates_per_s": upd / (ms / 1e3), "ms": ms, "bytes_per_update": bpu,
+             "hbm_gbs": upd * bpu / (ms / 1e3) / 1e9,
+             "energy_drift": abs(en_b - en_a) / abs(en_a) if en_a else None}
+        if ref is None:
+            ref = buf
+            gmax = float(ref.abs().max().item())
+            grms = float(ref.double().pow(2).mean().sqrt().item())
+        else:
+            d = (buf - ref).double()
+            r["max_rel_err_vs_f32"] = float(d.abs().max().item()) / gmax
+            r["rms_rel_err_vs_f32"] = float(d.pow(2).mean().sqrt().item()) / grms
+            del buf
+        out[st] = r
+        s.close()
+    del ref
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_leg(torch, W, args, local_rank):
+    """Continuous batching on the serving stream: the first N requests (grid edge
+    log-uniform 64..512, 2-6 layers, Ricker at a random node, 200..3000 steps,
+    relative threshold 1e-6, 20-step decay), Poisson arrivals at the given rate;
+    p50/p99 time to result (arrival -> result read back) and aggregate node
+    updates per second over the whole run."""
+    from paper_1702_00216_gb300 import serve
+    reqs = W.serving_stream(n_requests=args.serving, seed=216, rate_hz=args.serving_rate)
+    for r in reqs:
+        r.workload.thr_mode, r.workload.tau = 1, 1e-6
+        r.workload.decay_alpha, r.workload.decay_steps = 0.8, 20
+    srv = serve.Server(pool_bytes=48 * 1024 ** 3, max_bricks=24 * 1024 ** 2, max_sims=512,
+                       steps_per_tick=16, device=local_rank, storages=("f32", "bf16"))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = srv.run(reqs, time_scale=1.0)
+    wall = time.perf_counter() - t
+    srv.close()
+    out = serve.summarize(res, wall)
+    out.update({"stream": f"first {args.serving} requests of the serving stream (seed 216), "
+                          f"Poisson {args.serving_rate}/s, FP32/BF16 mix (one batch each, "
+                          f"half the pool each)",
+                "steps_per_tick": 16})
+    return out
 
 
 def end_to_end(torch, tcm, W, wl, local_rank):
@@ -386,7 +473,10 @@ def main():
     ap.add_argument("--trace", default=None,
                     help="write per-launch node updates of the untimed steps (JSON lines)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--quick", action="store_true", help="skip time-to-solution, e2e, CPU baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip time-to-solution, e2e, CPU baseline and serving")
+    ap.add_argument("--serving", type=int, default=120, help="requests in the serving leg (0: skip)")
+    ap.add_argument("--serving-rate", type=float, default=8.0, help="serving arrivals per second")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -54,7 +54,12 @@ typedef enum {
 
 enum { TCM_MEDIA_DENSE = 0, TCM_MEDIA_RULES = 1 };
 enum { TCM_THR_ABSOLUTE = 0, TCM_THR_RELATIVE = 1 };
-enum { TCM_STORAGE_F32 = 0 };
+/* Field storage in the pool.  F32: binary32.  BF16 / F16: bfloat16 or IEEE
+ * binary16 holding phi / s, with s a power of two per simulation (1 for BF16;
+ * for F16 chosen when the simulation starts so that its largest source sample
+ * or initial value is stored in [128, 256)).  Every storage computes Eq. 3 in
+ * binary32 with binary32 k; values are rounded to nearest-even on store. */
+enum { TCM_STORAGE_F32 = 0, TCM_STORAGE_BF16 = 1, TCM_STORAGE_F16 = 2 };
 
 typedef struct {
     int64_t nx, ny, nz; /* nodes */
@@ -90,7 +95,7 @@ typedef struct {
     void *pool_ptr;     /* device memory for the boxes, or NULL: library allocates */
     size_t pool_bytes;  /* size of the pool (caps the number of boxes) */
     void *stream;       /* cudaStream_t */
-    int storage;        /* TCM_STORAGE_F32 */
+    int storage;        /* TCM_STORAGE_F32 / _BF16 / _F16 */
     int dense;          /* 1: box every brick and never release (dense comparator) */
     int device;         /* CUDA device ordinal */
 } tcm_options;
@@ -217,7 +222,7 @@ typedef struct {
     size_t pool_bytes;  /* pool size (number of boxes = pool_bytes / tcm_slot_bytes) */
     void *stream;       /* cudaStream_t */
     int device;         /* CUDA device ordinal */
-    int storage;        /* TCM_STORAGE_F32 */
+    int storage;        /* TCM_STORAGE_F32 / _BF16 / _F16 */
     int64_t max_bricks; /* brick-table capacity summed over simulations (12 B per brick) */
     int max_sims;       /* simulation-table capacity */
 } tcm_batch_options;

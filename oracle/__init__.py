@@ -32,6 +32,8 @@ from . import build as _build
 _LIB = None
 
 ORC_MEDIA_DENSE, ORC_MEDIA_RULES = 0, 1
+STORAGE_F32, STORAGE_BF16, STORAGE_F16 = 0, 1, 2
+_STORAGE_NAMES = {"f32": STORAGE_F32, "bf16": STORAGE_BF16, "f16": STORAGE_F16}
 THR_ABSOLUTE, THR_RELATIVE = 0, 1
 
 _i64 = C.c_int64
@@ -71,6 +73,9 @@ def lib():
                 getattr(L, f"orc_tcm_{name}_{sfx}").argtypes = [_vp]
                 getattr(L, f"orc_tcm_{name}_{sfx}").restype = _i64
             getattr(L, f"orc_tcm_status_{sfx}").argtypes = [_vp]
+            getattr(L, f"orc_tcm_set_storage_{sfx}").argtypes = [_vp, C.c_int]
+            getattr(L, f"orc_tcm_storage_scale_{sfx}").argtypes = [_vp]
+            getattr(L, f"orc_tcm_storage_scale_{sfx}").restype = _d
             getattr(L, f"orc_tcm_brick_media_{sfx}").argtypes = [_vp, _i64, _vp]
             getattr(L, f"orc_tcm_destroy_{sfx}").argtypes = [_vp]
             getattr(L, f"orc_tcm_destroy_{sfx}").restype = None
@@ -78,6 +83,9 @@ def lib():
                                   _vp, _vp]
         L.orc_rules_c.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
+        for name in ("orc_round_bf16", "orc_round_f16"):
+            getattr(L, name).argtypes = [C.c_float]
+            getattr(L, name).restype = C.c_float
         _LIB = L
     return _LIB
 
@@ -158,6 +166,14 @@ def dense_run(k: np.ndarray, now: np.ndarray, prev: np.ndarray, steps: int, sour
     return now, prev
 
 
+def round_storage(v, storage) -> np.ndarray:
+    """Round binary32 values to bfloat16 ("bf16") or binary16 ("f16"), nearest
+    even, returned as binary32 (the oracle's element-wise C routine)."""
+    fn = getattr(lib(), "orc_round_" + storage)
+    a = np.asarray(v, dtype=np.float32)
+    return np.array([fn(float(x)) for x in a.ravel()], dtype=np.float32).reshape(a.shape)
+
+
 def energy(k: np.ndarray, a: np.ndarray, b: np.ndarray) -> float:
     """Leapfrog discrete energy between phi^{n+1} = a and phi^n = b (FP64 sum)."""
     sfx = _sfx(k.dtype)
@@ -174,7 +190,7 @@ class OracleTCM:
     def __init__(self, shape, media, dx: float, dt: float, brick=(8, 8, 8),
                  thr_mode: int = THR_ABSOLUTE, tau: float = 0.0, decay_alpha: float = 1.0,
                  decay_steps: int = 0, max_slots: int = 0, dense: bool = False,
-                 dtype=np.float32):
+                 dtype=np.float32, storage="f32"):
         self.dtype = np.dtype(dtype)
         self._s = _sfx(dtype)
         self.shape = tuple(int(v) for v in shape)
@@ -201,6 +217,10 @@ class OracleTCM:
         if not h:
             raise ValueError("orc_tcm_create rejected its arguments")
         self._h = h
+        st = _STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+        if st != STORAGE_F32 and self._f("set_storage")(h, st) != 0:
+            self.close()
+            raise ValueError("storage not supported by this program")
         self.mx = -(-nx // bx)
         self.my = -(-ny // by)
         self.mz = -(-nz // bz)
@@ -266,6 +286,10 @@ class OracleTCM:
     @property
     def step_index(self) -> int:
         return int(self._f("step_index")(self._h))
+
+    @property
+    def storage_scale(self) -> float:
+        return float(self._f("storage_scale")(self._h))
 
     @property
     def status(self) -> int:

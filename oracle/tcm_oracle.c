@@ -113,6 +113,32 @@ double orc_energy_f32(int64_t nx, int64_t ny, int64_t nz, const float *k,
     ENERGY_BODY(float, float)
 }
 
+/* ---- 16-bit storage formats ------------------------------------------------ */
+/* Round v to nearest-even with `bits` significant bits, the quantum never
+ * below 2^min_exp (gradual underflow), overflowing to inf at 2^max_exp.
+ * In binary64 every step is exact: v has 24 bits, v / quantum is an integer
+ * plus a fraction of at most 24 bits, and rint() rounds ties to even. */
+static float round_to_format(float v, int bits, int min_exp, int max_exp)
+{
+    if (v == 0.0f || isnan(v) || isinf(v)) return v;
+    int e;
+    frexp((double)v, &e);   /* |v| in [2^(e-1), 2^e) */
+    int qe = (e - 1) - (bits - 1);
+    if (qe < min_exp) qe = min_exp;
+    const double quantum = ldexp(1.0, qe);
+    const double r = rint((double)v / quantum) * quantum;
+    if (fabs(r) >= ldexp(1.0, max_exp)) return v < 0 ? -INFINITY : INFINITY;
+    return (float)r;
+}
+
+/* bfloat16: 1+7 bits significand, exponent field as binary32 (bias 127):
+ * smallest subnormal 2^-126 * 2^-7 = 2^-133, finite values below 2^128. */
+float orc_round_bf16(float v) { return round_to_format(v, 8, -133, 128); }
+
+/* binary16: 1+10 bits significand, bias 15: smallest subnormal 2^-24, largest
+ * finite (2 - 2^-10) * 2^15 = 65504, everything rounding to 2^16 overflows. */
+float orc_round_f16(float v) { return round_to_format(v, 11, -24, 16); }
+
 /* ---- type-generic programs ---------------------------------------------- */
 #define REAL float
 #define SFX(name) name##_f32

@@ -87,6 +87,19 @@ double orc_energy_f64(int64_t nx, int64_t ny, int64_t nz, const double *k,
 double orc_energy_f32(int64_t nx, int64_t ny, int64_t nz, const float *k,
                       const float *a, const float *b);
 
+/* ---- 16-bit storage formats -------------------------------------------- */
+/* Round a binary32 value to nearest (ties to even) in a narrower format and
+ * return it as binary32 (exactly representable):
+ *   bfloat16: 8 significant bits, binary32's exponent range (normal down to
+ *             2^-126, subnormals in steps of 2^-133), overflow to +-inf;
+ *   binary16: 11 significant bits, normal down to 2^-14, subnormals in steps
+ *             of 2^-24, largest finite 65504, overflow to +-inf.
+ * Written from the formats' definitions; zeros, infinities and NaN pass. */
+float orc_round_bf16(float v);
+float orc_round_f16(float v);
+
+enum { ORC_STORAGE_F32 = 0, ORC_STORAGE_BF16 = 1, ORC_STORAGE_F16 = 2 };
+
 /* ---- Triggered Cells Method ---------------------------------------------- */
 typedef struct orc_tcm orc_tcm;
 
@@ -120,6 +133,21 @@ int orc_tcm_add_source_f64(orc_tcm *t, int64_t x, int64_t y, int64_t z,
 /* Initial fields (dense nx*ny*nz arrays); only before the first step. */
 int orc_tcm_set_field_f32(orc_tcm *t, const float *now, const float *prev);
 int orc_tcm_set_field_f64(orc_tcm *t, const double *now, const double *prev);
+/* Field storage precision (before the first step; default ORC_STORAGE_F32).
+ * With BF16 or F16 every phi^{n+1} is rounded to the format when it is
+ * written -- after Eq. 3, the source samples and the shut-down factor, all in
+ * the program's type -- and the maxima, the trigger decisions and the domain
+ * maximum are taken on the rounded value.  Initial fields are rounded the
+ * same way at the first step.  F16 holds phi / s with s = 2^(e-8), where
+ * 2^(e-1) <= m < 2^e and m is the largest |value| among the source samples
+ * and initial fields at the first step (s = 1 when m = 0; e - 8 clamped to
+ * [-100, 100]); BF16 and F32 use s = 1.  Only the _f32 program takes a
+ * 16-bit storage (the _f64 one would round twice); it returns ORC_EINVAL. */
+int orc_tcm_set_storage_f32(orc_tcm *t, int storage);
+int orc_tcm_set_storage_f64(orc_tcm *t, int storage);
+/* The scale s in use (1 before the first step). */
+double orc_tcm_storage_scale_f32(const orc_tcm *t);
+double orc_tcm_storage_scale_f64(const orc_tcm *t);
 int orc_tcm_step_f32(orc_tcm *t, int64_t n);
 int orc_tcm_step_f64(orc_tcm *t, int64_t n);
 /* which = 0: phi^n, 1: phi^{n-1}; zeros where no box is allocated. */

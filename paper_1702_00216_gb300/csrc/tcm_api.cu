@@ -290,11 +290,12 @@ tcm_status check_sim_args(const tcm_domain *domain, const tcm_velocity_model *ve
     return TCM_OK;
 }
 
-tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t pool_bytes, long long max_bricks,
-                     int max_sims, tcm_batch **out)
+tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t pool_bytes, int storage,
+                     long long max_bricks, int max_sims, tcm_batch **out)
 {
     *out = nullptr;
-    size_t slot_bytes = 2 * BVOL * sizeof(float);
+    if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16) return TCM_EINVAL;
+    const size_t slot_bytes = (size_t)2 * BVOL * storage_bytes(storage);
     const long long n_slots_ll = (long long)(pool_bytes / slot_bytes);
     if (n_slots_ll < 1 || max_bricks < 1 || max_sims < 1 || max_sims > 65535) return TCM_EINVAL;
     if (pool_ptr && reinterpret_cast<uintptr_t>(pool_ptr) % 16 != 0) return TCM_EINVAL;
@@ -329,7 +330,8 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
         b->own_pool = true;
     }
     Engine &E = b->E;
-    E.phi = static_cast<float *>(b->pool);
+    E.phi = b->pool;
+    E.storage = storage;
     E.n_slots = b->n_slots;
     E.n_words = b->n_words;
     E.words_per_block = (int)std::max<long long>(1, (b->n_words + b->grid - 1) / b->grid);
@@ -501,6 +503,8 @@ tcm_status sim_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_mo
     S.decay_steps = decay_steps;
     S.kslabs = h.kslabs;
     S.live = 0;
+    S.scale = 1.f;
+    S.inv_scale = 1.f;
     h.used = true;
     // the brick range's words now belong to this sim
     {
@@ -530,6 +534,24 @@ tcm_status sim_prime(tcm_batch *b, int id)
     HostSim &h = b->sims[id];
     if (h.primed) return TCM_OK;
     cudaStream_t q = b->stream;
+    if (b->E.storage == ST_F16) {
+        // binary16 holds phi / scale: the largest initial value or source
+        // sample maps to [128, 256), leaving 2^8 of headroom below 65504.
+        float peak = 0.f;
+        for (const auto &src : h.sources)
+            for (float v : src.w) peak = std::max(peak, std::fabs(v));
+        for (float v : h.init_now) peak = std::max(peak, std::fabs(v));
+        for (float v : h.init_prev) peak = std::max(peak, std::fabs(v));
+        int e = 0;
+        if (peak > 0.f && std::isfinite(peak)) {
+            std::frexp(peak, &e);   // peak = f * 2^e, f in [0.5, 1)
+            e -= 8;
+        }
+        e = std::max(-100, std::min(100, e));
+        h.dev.scale = std::ldexp(1.f, e);
+        h.dev.inv_scale = std::ldexp(1.f, -e);
+    }
+    TRYS(upload_sim_header(b, id));
     TRYS(upload_sources(b));
     for (const auto &src : h.sources) {
         const unsigned short bit = (unsigned short)FLAG_HAS_SRC;
@@ -716,9 +738,9 @@ extern "C" {
 
 tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out)
 {
-    if (!out || brick.bx != BX || brick.by != BY || brick.bz != BZ || storage != TCM_STORAGE_F32)
-        return TCM_EINVAL;
-    *out = (size_t)2 * BVOL * sizeof(float);
+    if (!out || brick.bx != BX || brick.by != BY || brick.bz != BZ) return TCM_EINVAL;
+    if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16) return TCM_EINVAL;
+    *out = (size_t)2 * BVOL * storage_bytes(storage);
     return TCM_OK;
 }
 
@@ -739,7 +761,8 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     if (pool_bytes / slot_bytes < 1) return TCM_EINVAL;
     if (options->dense && (long long)(pool_bytes / slot_bytes) < n_bricks) return TCM_ENOMEM;
     tcm_batch *b = nullptr;
-    TRYS(batch_new(options->device, (cudaStream_t)options->stream, options->pool_ptr, pool_bytes, n_bricks, 1, &b));
+    TRYS(batch_new(options->device, (cudaStream_t)options->stream, options->pool_ptr, pool_bytes, options->storage,
+                   n_bricks, 1, &b));
     DeviceGuard g(b->device);
     int id = -1;
     tcm_status st = sim_add(b, domain, velocity, dx, dt, threshold, options->threshold_mode, options->decay_alpha,
@@ -1005,9 +1028,9 @@ tcm_status tcm_batch_create(const tcm_batch_options *o, tcm_batch **out)
 {
     if (!out) return TCM_EINVAL;
     *out = nullptr;
-    if (!o || o->storage != TCM_STORAGE_F32) return TCM_EINVAL;
-    return batch_new(o->device, (cudaStream_t)o->stream, o->pool_ptr, o->pool_bytes, o->max_bricks, o->max_sims,
-                     out);
+    if (!o) return TCM_EINVAL;
+    return batch_new(o->device, (cudaStream_t)o->stream, o->pool_ptr, o->pool_bytes, o->storage, o->max_bricks,
+                     o->max_sims, out);
 }
 
 tcm_status tcm_batch_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_model *velocity, double dx,
@@ -1016,7 +1039,7 @@ tcm_status tcm_batch_add(tcm_batch *b, const tcm_domain *domain, const tcm_veloc
 {
     if (!b || !out) return TCM_EINVAL;
     *out = nullptr;
-    TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, TCM_STORAGE_F32, threshold_mode, decay_steps));
+    TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, b->E.storage, threshold_mode, decay_steps));
     if (b->poisoned) return TCM_ESTATE;
     DeviceGuard g(b->device);
     int id = -1;

@@ -21,6 +21,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace tcm {
@@ -43,6 +45,10 @@ constexpr unsigned FLAG_HAS_SRC = 1u << 15;
 constexpr unsigned SD_MASK = 0x7fffu;
 
 enum { MEDIA_DENSE = 0, MEDIA_RULES = 1 };
+// Field storage of the boxes: binary32, or bfloat16 / binary16 holding
+// phi / scale (scale a power of two per simulation; compute is binary32).
+enum { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
+__host__ __device__ constexpr int storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
 
 struct __align__(16) SlotMeta {
     int brick;       // local brick id within its sim (Box2cell)
@@ -77,6 +83,8 @@ struct SimDev {
     int src_begin, src_end;
     const float *kslabs;   // this sim's bulked coefficient bricks
     int live;              // 1 while the sim steps (0: frozen or released)
+    float scale;           // stored field value = phi / scale (power of two)
+    float inv_scale;
     int pad1;
     // mutable (device-owned)
     long long step;        // n of phi^n
@@ -113,7 +121,8 @@ struct EngineState {
 };
 
 struct Engine {
-    float *phi;
+    void *phi;             // pool: 2 * BVOL elements of `storage` per box
+    int storage;
     int n_slots;
     int *slot_of_brick;
     const float *kscal;
@@ -148,6 +157,26 @@ struct MediaDev {
     const double *sph;
     const float *sph_c;
 };
+
+// Element e of box half (slot, half), as a physical value (x scale).
+__device__ __forceinline__ float load_phys(const Engine &E, int slot, int half, int e, float scale)
+{
+    const size_t i = ((size_t)slot * 2 + half) * BVOL + e;
+    if (E.storage == ST_F32) return static_cast<const float *>(E.phi)[i] * scale;
+    const unsigned short bits = static_cast<const unsigned short *>(E.phi)[i];
+    if (E.storage == ST_BF16) return __uint_as_float((unsigned)bits << 16) * scale;
+    return __half2float(__ushort_as_half(bits)) * scale;
+}
+
+// Store a physical value v into element e of box half (slot, half).
+__device__ __forceinline__ void store_phys(const Engine &E, int slot, int half, int e, float v, float inv_scale)
+{
+    const size_t i = ((size_t)slot * 2 + half) * BVOL + e;
+    const float s = v * inv_scale;
+    if (E.storage == ST_F32) static_cast<float *>(E.phi)[i] = s;
+    else if (E.storage == ST_BF16) static_cast<__nv_bfloat16 *>(E.phi)[i] = __float2bfloat16_rn(s);
+    else static_cast<__half *>(E.phi)[i] = __float2half_rn(s);
+}
 
 // ---- launchers (tcm_kernels.cu) -------------------------------------------
 // Every launcher returns the cudaError_t of its launch.

@@ -175,9 +175,115 @@ __device__ __forceinline__ WorkItem load_item(const WorkItem *L, int i)
     return w;
 }
 
-__device__ __forceinline__ const float *half_ptr(const Engine &E, int slot, int half)
+// Vector access to 4 consecutive field elements (x fastest) in the storage
+// format ST, as physical binary32 values.  Scaling by a power of two is exact.
+template <int ST>
+struct Fld;
+
+template <>
+struct Fld<ST_F32> {
+    using T = float;
+    static __device__ __forceinline__ float4 ld(const T *p, float) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    static __device__ __forceinline__ float4 ld_stream(const T *p, float)
+    {
+        return __ldcs(reinterpret_cast<const float4 *>(p));
+    }
+    static __device__ __forceinline__ float ld1(const T *p, float) { return __ldg(p); }
+    // Round q to the storage format: returns the stored value (physical) and
+    // its bit pattern for st().
+    using V = float4;
+    static __device__ __forceinline__ float4 rnd(float4 q, float, float, V &v)
+    {
+        v = q;
+        return q;
+    }
+    static __device__ __forceinline__ void st(T *p, V v) { __stcg(reinterpret_cast<float4 *>(p), v); }
+};
+
+__device__ __forceinline__ float4 scale4(float4 v, float s)
 {
-    return E.phi + ((size_t)slot * 2 + half) * BVOL;
+    return make_float4(v.x * s, v.y * s, v.z * s, v.w * s);
+}
+
+template <>
+struct Fld<ST_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float4 cvt(uint2 u, float s)
+    {
+        return scale4(make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                  __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u)),
+                      s);
+    }
+    static __device__ __forceinline__ float4 ld(const T *p, float s)
+    {
+        return cvt(__ldg(reinterpret_cast<const uint2 *>(p)), s);
+    }
+    static __device__ __forceinline__ float4 ld_stream(const T *p, float s)
+    {
+        return cvt(__ldcs(reinterpret_cast<const uint2 *>(p)), s);
+    }
+    static __device__ __forceinline__ float ld1(const T *p, float s)
+    {
+        return __uint_as_float((unsigned)__ldg(reinterpret_cast<const unsigned short *>(p)) << 16) * s;
+    }
+    using V = uint2;
+    static __device__ __forceinline__ float4 rnd(float4 q, float s, float inv_s, V &v)
+    {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(q.x * inv_s, q.y * inv_s);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(q.z * inv_s, q.w * inv_s);
+        v.x = *reinterpret_cast<const unsigned *>(&a);
+        v.y = *reinterpret_cast<const unsigned *>(&b);
+        return cvt(v, s);
+    }
+    static __device__ __forceinline__ void st(T *p, V v) { __stcg(reinterpret_cast<uint2 *>(p), v); }
+};
+
+template <>
+struct Fld<ST_F16> {
+    using T = __half;
+    static __device__ __forceinline__ float4 cvt(uint2 u, float s)
+    {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return scale4(make_float4(a.x, a.y, b.x, b.y), s);
+    }
+    static __device__ __forceinline__ float4 ld(const T *p, float s)
+    {
+        return cvt(__ldg(reinterpret_cast<const uint2 *>(p)), s);
+    }
+    static __device__ __forceinline__ float4 ld_stream(const T *p, float s)
+    {
+        return cvt(__ldcs(reinterpret_cast<const uint2 *>(p)), s);
+    }
+    static __device__ __forceinline__ float ld1(const T *p, float s)
+    {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p)))) * s;
+    }
+    using V = uint2;
+    static __device__ __forceinline__ float4 rnd(float4 q, float s, float inv_s, V &v)
+    {
+        const __half2 a = __floats2half2_rn(q.x * inv_s, q.y * inv_s);
+        const __half2 b = __floats2half2_rn(q.z * inv_s, q.w * inv_s);
+        v.x = *reinterpret_cast<const unsigned *>(&a);
+        v.y = *reinterpret_cast<const unsigned *>(&b);
+        return cvt(v, s);
+    }
+    static __device__ __forceinline__ void st(T *p, V v) { __stcg(reinterpret_cast<uint2 *>(p), v); }
+};
+
+template <int ST>
+__device__ __forceinline__ typename Fld<ST>::T *half_ptr(const Engine &E, int slot, int half)
+{
+    return static_cast<typename Fld<ST>::T *>(E.phi) + ((size_t)slot * 2 + half) * BVOL;
+}
+
+// Zero one box (both halves) with the lanes of a warp.
+__device__ __forceinline__ void zero_box(const Engine &E, int slot, int lane)
+{
+    const int n16 = 2 * BVOL * storage_bytes(E.storage) / 16;
+    float4 *p = reinterpret_cast<float4 *>(static_cast<unsigned char *>(E.phi) +
+                                           (size_t)slot * 2 * BVOL * storage_bytes(E.storage));
+    for (int e = lane; e < n16; e += 32) p[e] = f4zero();
 }
 
 // Merge a lane's running max |phi^{n+1}| into its sim's domain maximum.  The
@@ -205,6 +311,7 @@ __device__ __forceinline__ void flush_updates(const Engine &E, unsigned long lon
 // lanes (lane ^ 17) instead of being loaded.  Every lane of the warp calls
 // this (valid = false on a missing brick) so shuffles see full warps.
 // ---------------------------------------------------------------------------
+template <int ST>
 __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
                                          bool share_xm, bool share_xp, unsigned long long &cells,
                                          unsigned long long &scells, float &gacc, int &gsim, int &gnh)
@@ -218,6 +325,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const int nh = w.nh;
     const int b = w.brick;
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
+    using F = Fld<ST>;
+    const float sc = __ldg(&S->scale), isc = __ldg(&S->inv_scale);
 
     float4 P[BZ], M[BZ], K[BZ], YH[BZ];
     float XH[BZ];
@@ -227,12 +336,12 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const int ys = !valid ? -1 : (y == 0 ? w.nb[2] : (y == BY - 1 ? w.nb[3] : -1));
     const int xs = !valid ? -1 : (x4 == 0 ? (share_xm ? -1 : w.nb[0]) : (x4 == XQ - 1 ? (share_xp ? -1 : w.nb[1]) : -1));
     if (valid) {
-        const float4 *now4 = reinterpret_cast<const float4 *>(half_ptr(E, w.slot, nh));
-        const float4 *prv4 = reinterpret_cast<const float4 *>(half_ptr(E, w.slot, nh ^ 1));
+        const typename F::T *now = half_ptr<ST>(E, w.slot, nh);
+        const typename F::T *prv = half_ptr<ST>(E, w.slot, nh ^ 1);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) P[z] = __ldg(now4 + z * TPB + t);
+        for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), sc);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) M[z] = __ldcs(prv4 + z * TPB + t);
+        for (int z = 0; z < BZ; ++z) M[z] = F::ld_stream(prv + 4 * (z * TPB + t), sc);
         if (w.kslab >= 0) {
             const float *kbase = reinterpret_cast<const float *>(
                 __ldg(reinterpret_cast<const unsigned long long *>(&S->kslabs)));
@@ -243,8 +352,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 #pragma unroll
             for (int z = 0; z < BZ; ++z) K[z] = make_float4(w.kscal, w.kscal, w.kscal, w.kscal);
         }
-        if (w.nb[4] >= 0) Zm = __ldg(reinterpret_cast<const float4 *>(half_ptr(E, w.nb[4], nh)) + (BZ - 1) * TPB + t);
-        if (w.nb[5] >= 0) Zp = __ldg(reinterpret_cast<const float4 *>(half_ptr(E, w.nb[5], nh)) + t);
+        if (w.nb[4] >= 0) Zm = F::ld(half_ptr<ST>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), sc);
+        if (w.nb[5] >= 0) Zp = F::ld(half_ptr<ST>(E, w.nb[5], nh) + 4 * t, sc);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) {
@@ -254,17 +363,17 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         }
     }
     if (ys >= 0) {
-        const float4 *yb = reinterpret_cast<const float4 *>(half_ptr(E, ys, nh)) + (y == 0 ? BY - 1 : 0) * XQ + x4;
+        const typename F::T *yb = half_ptr<ST>(E, ys, nh) + 4 * ((y == 0 ? BY - 1 : 0) * XQ + x4);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) YH[z] = __ldg(yb + z * TPB);
+        for (int z = 0; z < BZ; ++z) YH[z] = F::ld(yb + 4 * z * TPB, sc);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) YH[z] = f4zero();
     }
     if (xs >= 0) {
-        const float *xb = half_ptr(E, xs, nh) + y * BX + (x4 == 0 ? BX - 1 : 0);
+        const typename F::T *xb = half_ptr<ST>(E, xs, nh) + y * BX + (x4 == 0 ? BX - 1 : 0);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) XH[z] = __ldg(xb + z * BY * BX);
+        for (int z = 0; z < BZ; ++z) XH[z] = F::ld1(xb + z * BY * BX, sc);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) XH[z] = 0.f;
@@ -274,7 +383,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const bool decay = (w.flags & SD_MASK) != 0u;
     const bool ragged = (cx + 1) * BX > nx || (cy + 1) * BY > ny || (cz + 1) * BZ > nz;
     const int gx0 = cx * BX + 4 * x4, gy = cy * BY + y, gz0 = cz * BZ;
-    float4 *out = reinterpret_cast<float4 *>(E.phi + ((size_t)w.slot * 2 + (nh ^ 1)) * BVOL);
+    typename F::T *out = half_ptr<ST>(E, w.slot, nh ^ 1);
     const bool src = valid && (w.flags & FLAG_HAS_SRC);
     const long long step = src ? __ldcg(&S->step) : 0;
     const bool xrecv = (x4 == 0 && share_xm) || (x4 == XQ - 1 && share_xp);
@@ -334,7 +443,11 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
             if (!rowin || gx0 + 2 >= nx) q.z = 0.f;
             if (!rowin || gx0 + 3 >= nx) q.w = 0.f;
         }
-        if (valid) __stcg(out + z * TPB + t, q);
+        // phi^{n+1} is what the storage holds: maxima and thresholds see the
+        // stored (rounded) value.
+        typename F::V qs;
+        q = F::rnd(q, sc, isc, qs);
+        if (valid) F::st(out + 4 * (z * TPB + t), qs);
         const float mq = max4abs(q);
         qm = fmaxf(qm, mq);
         mc = fmaxf(mc, fmaxf(mq, max4abs(p)));
@@ -704,6 +817,7 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
 // ---------------------------------------------------------------------------
 // The step kernel.
 // ---------------------------------------------------------------------------
+template <int ST>
 __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
 {
     EngineState *st = E.st;
@@ -750,7 +864,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
             const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
             const bool pair_x = seg == 0 ? (other_v && w.nb[1] >= 0 && w.nb[1] == other_slot)
                                          : (v && w.nb[0] >= 0 && w.nb[0] == other_slot);
-            p1_brick(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, cells, scells, gacc, gsim, gnh);
+            p1_brick<ST>(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, cells, scells, gacc, gsim,
+                         gnh);
             pr = pn;
             w = wn;
             v = vn;
@@ -811,8 +926,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
         for (int i = gwarp; i < n_new; i += nwarps) {
             const int ns = __ldcg(E.newslots + i);
             if (ns < 0) continue;   // a claim that found no vacant box
-            float4 *p = reinterpret_cast<float4 *>(E.phi + (size_t)ns * 2 * BVOL);
-            for (int e = lane; e < 2 * BVOL / 4; e += 32) p[e] = f4zero();
+            zero_box(E, ns, lane);
         }
         const int n_ret = __ldcg(&st->n_retired);
         const int base = max(__ldcg(&st->free_top), 0);
@@ -1015,8 +1129,7 @@ __global__ void k_admit(Engine E, int sim, const long long *bricks, long long n)
         }
         slot = __shfl_sync(FULL, slot, 0);
         if (slot < 0) continue;
-        float4 *p = reinterpret_cast<float4 *>(E.phi + (size_t)slot * 2 * BVOL);
-        for (int e = lane; e < 2 * BVOL / 4; e += 32) p[e] = f4zero();
+        zero_box(E, slot, lane);
     }
 }
 
@@ -1061,8 +1174,9 @@ __global__ void k_scatter_field(Engine E, const float *packed, const long long *
         const int r = (int)(i % (2 * BVOL));
         const int which = r / BVOL, e = r % BVOL;
         const int half = which == 0 ? now_half : (now_half ^ 1);
-        const int slot = E.slot_of_brick[gids[bi]];
-        if (slot >= 0) E.phi[((size_t)slot * 2 + half) * BVOL + e] = packed[i];
+        const long long g = gids[bi];
+        const int slot = E.slot_of_brick[g];
+        if (slot >= 0) store_phys(E, slot, half, e, packed[i], E.sims[E.sim_of_word[g >> 5]].inv_scale);
     }
 }
 
@@ -1079,7 +1193,7 @@ __global__ void k_read_window(Engine E, int sim, int half, long long x0, long lo
             const int slot = E.slot_of_brick[S->brick_base + b];
             if (slot >= 0) {
                 const int e = (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX));
-                v = E.phi[((size_t)slot * 2 + half) * BVOL + e];
+                v = load_phys(E, slot, half, e, S->scale);
             }
         }
         out[i] = v;
@@ -1094,7 +1208,7 @@ __device__ __forceinline__ double prev_at(const Engine &E, const SimDev *S, int 
     const long long b = ((z / BZ) * S->my + (y / BY)) * S->mx + (x / BX);
     const int slot = E.slot_of_brick[S->brick_base + b];
     if (slot < 0) return 0.0;
-    return (double)E.phi[((size_t)slot * 2 + prev_half) * BVOL + ((z % BZ) * BY + (y % BY)) * BX + (x % BX)];
+    return (double)load_phys(E, slot, prev_half, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
 }
 
 __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *out)
@@ -1114,8 +1228,8 @@ __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *ou
         const long long y = (long long)((b / S->mx) % S->my) * BY + (e / BX) % BY;
         const long long z = (long long)(b / (S->mx * S->my)) * BZ + e / (BX * BY);
         if (x >= S->nx || y >= S->ny || z >= S->nz) continue;
-        const double a = (double)E.phi[((size_t)slot * 2 + now_half) * BVOL + e];
-        const double bb = (double)E.phi[((size_t)slot * 2 + ph) * BVOL + e];
+        const double a = (double)load_phys(E, slot, now_half, e, S->scale);
+        const double bb = (double)load_phys(E, slot, ph, e, S->scale);
         const double nb = prev_at(E, S, ph, x - 1, y, z) + prev_at(E, S, ph, x + 1, y, z) +
                           prev_at(E, S, ph, x, y - 1, z) + prev_at(E, S, ph, x, y + 1, z) +
                           prev_at(E, S, ph, x, y, z - 1) + prev_at(E, S, ph, x, y, z + 1);
@@ -1228,7 +1342,11 @@ int step_grid_size(int device)
 {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, BLOCK, 0) != cudaSuccess) return 0;
+    int a = 0, b = 0, c = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<ST_F32>, BLOCK, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<ST_BF16>, BLOCK, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_step<ST_F16>, BLOCK, 0) != cudaSuccess) return 0;
+    per_sm = min(a, min(b, c));
     return sms * per_sm;
 }
 
@@ -1236,7 +1354,10 @@ cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s)
 {
     Engine copy = e;
     void *args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void *)k_step, dim3(grid), dim3(BLOCK), args, 0, s);
+    const void *fn = e.storage == ST_BF16 ? (const void *)k_step<ST_BF16>
+                     : e.storage == ST_F16 ? (const void *)k_step<ST_F16>
+                                           : (const void *)k_step<ST_F32>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, 0, s);
 }
 
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,

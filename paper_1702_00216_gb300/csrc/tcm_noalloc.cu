@@ -37,7 +37,7 @@ __device__ __forceinline__ double prev_node(const tcm::Engine &E, const tcm::Sim
     const long long b = ((z / BZ) * S->my + (y / BY)) * S->mx + (x / BX);
     const int slot = E.slot_of_brick[S->brick_base + b];
     if (slot < 0) return 0.0;
-    return (double)E.phi[((size_t)slot * 2 + ph) * BVOL + ((z % BZ) * BY + (y % BY)) * BX + (x % BX)];
+    return (double)load_phys(E, slot, ph, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
 }
 
 // One warp per active brick: its energy contribution, reduced in a fixed
@@ -65,8 +65,8 @@ __global__ void k_energy_partials(tcm::Engine E, int sim, int now_half, int pari
         for (int e = lane; e < BVOL; e += 32) {
             const long long x = bx0 + e % BX, y = by0 + (e / BX) % BY, z = bz0 + e / (BX * BY);
             if (x >= S->nx || y >= S->ny || z >= S->nz) continue;
-            const double a = (double)E.phi[((size_t)slot * 2 + now_half) * BVOL + e];
-            const double bb = (double)E.phi[((size_t)slot * 2 + ph) * BVOL + e];
+            const double a = (double)load_phys(E, slot, now_half, e, S->scale);
+            const double bb = (double)load_phys(E, slot, ph, e, S->scale);
             const double nb = prev_node(E, S, ph, x - 1, y, z) + prev_node(E, S, ph, x + 1, y, z) +
                               prev_node(E, S, ph, x, y - 1, z) + prev_node(E, S, ph, x, y + 1, z) +
                               prev_node(E, S, ph, x, y, z - 1) + prev_node(E, S, ph, x, y, z + 1);

@@ -19,7 +19,13 @@ LIB_PATH = os.path.join(HERE, "libtcm.so")
 TCM_OK, TCM_EINVAL, TCM_ECFL, TCM_ENOMEM, TCM_EDEVICE, TCM_ETIMEOUT, TCM_ESTATE = range(7)
 TCM_MEDIA_DENSE, TCM_MEDIA_RULES = 0, 1
 TCM_THR_ABSOLUTE, TCM_THR_RELATIVE = 0, 1
-TCM_STORAGE_F32 = 0
+TCM_STORAGE_F32, TCM_STORAGE_BF16, TCM_STORAGE_F16 = 0, 1, 2
+STORAGES = {"f32": TCM_STORAGE_F32, "bf16": TCM_STORAGE_BF16, "f16": TCM_STORAGE_F16}
+
+
+def storage_code(storage) -> int:
+    """TCM_STORAGE_* from a code or a name ('f32', 'bf16', 'f16')."""
+    return STORAGES[storage] if isinstance(storage, str) else int(storage)
 
 EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "tcm_step",
            "tcm_step_async", "tcm_sync", "tcm_read_field", "tcm_read_field_device",
@@ -340,13 +346,14 @@ class Sim:
 
     def __init__(self, shape, media, dx, dt, threshold=0.0, brick=(8, 8, 8),
                  thr_mode=TCM_THR_ABSOLUTE, decay_alpha=1.0, decay_steps=0, pool_bytes=None,
-                 dense=False, device=0, stream=None, pool_tensor=None):
+                 dense=False, device=0, stream=None, pool_tensor=None, storage=TCM_STORAGE_F32):
         self.shape = tuple(int(v) for v in shape)
+        self.storage = storage_code(storage)
         nz, ny, nx = self.shape
         bx, by, bz = brick
         self.brick = (bx, by, bz)
         self.mx, self.my, self.mz = -(-nx // bx), -(-ny // by), -(-nz // bz)
-        slot = tcm_slot_bytes(brick)
+        slot = tcm_slot_bytes(brick, self.storage)
         if pool_bytes is None:
             pool_bytes = self.mx * self.my * self.mz * slot
         torch = _torch()
@@ -356,7 +363,7 @@ class Sim:
         opts.decay_alpha = float(decay_alpha)
         opts.decay_steps = int(decay_steps)
         opts.pool_bytes = int(pool_bytes)
-        opts.storage = TCM_STORAGE_F32
+        opts.storage = self.storage
         opts.dense = int(bool(dense))
         opts.device = int(device)
         if pool_tensor is not None:
@@ -474,12 +481,13 @@ class Batch:
     """Many simulations stepped together by one launch per step (tcm_batch_*)."""
 
     def __init__(self, pool_bytes, max_bricks, max_sims=64, device=0, stream=None,
-                 pool_tensor=None):
+                 pool_tensor=None, storage=TCM_STORAGE_F32):
         torch = _torch()
+        self.storage = storage_code(storage)
         o = tcm_batch_options()
         o.pool_bytes = int(pool_bytes)
         o.device = int(device)
-        o.storage = TCM_STORAGE_F32
+        o.storage = self.storage
         o.max_bricks = int(max_bricks)
         o.max_sims = int(max_sims)
         self._pool = None

@@ -219,8 +219,10 @@ def virtual(n: int = 4096, steps: int = 2500, pool_bytes: int = 120 * 2**30) -> 
 
 
 def precision(n: int = 256, steps: int = 800) -> Workload:
-    w = small(n, steps)
-    w.name = f"precision-{n}^3-homogeneous-ricker"
+    """The layered, perturbed medium and settings of layered() on a 256^3 grid
+    (the storage-precision comparison)."""
+    w = layered(n, steps)
+    w.name = f"precision-{n}^3-layered-perturbed-ricker"
     return w
 
 

@@ -1,0 +1,167 @@
+"""16-bit field storage (bfloat16 / binary16 holding phi / scale, binary32
+arithmetic): the GPU equals, bit for bit, the oracle's storage form (fields
+and active sets), TCM at threshold 0 equals the dense grid, and the error
+against the binary64 dense grid stays within the stated bounds."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00216_gb300 import tcm
+from paper_1702_00216_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+F32 = np.float32
+STORAGES = ["bf16", "f16"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def het_workload():
+    """Ragged heterogeneous grid, relative threshold with shut-down decay,
+    two sources (one of them large, so the F16 scale is well above 1)."""
+    shape = (45, 38, 53)
+    m = W.random_dense_media(shape, 11, 1.0, 2.2)
+    dt = 0.5 / m.c_max()
+    return W.Workload("het", shape, m, 1.0, dt,
+                      [(7, 30, 9, W.ricker(1 / 9, dt) * 300.0),
+                       (40, 5, 33, W.ricker(1 / 6, dt)[:40])], 0,
+                      thr_mode=1, tau=1e-4, decay_alpha=0.8, decay_steps=5)
+
+
+def oracle_of(wl, storage, dense=False):
+    o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, thr_mode=wl.thr_mode, tau=wl.tau,
+                         decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps, dense=dense,
+                         storage=storage)
+    for x, y, z, w in wl.sources:
+        o.add_source(x, y, z, np.asarray(w, F32))
+    return o
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("dense", [False, True])
+def test_16bit_equals_oracle_storage_form(storage, dense):
+    wl = het_workload()
+    s = tcm.Sim.from_workload(wl, dense=dense, storage=storage)
+    o = oracle_of(wl, storage, dense)
+    for _ in range(4):
+        s.step(30)
+        o.step(30)
+        assert np.array_equal(s.read_field(0), o.read_field(0))
+        assert np.array_equal(s.read_field(1), o.read_field(1))
+        assert np.array_equal(s.active_bricks(), o.active_bricks())
+    assert s.updates == o.updates
+    s.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_16bit_threshold0_equals_dense(storage):
+    wl = W.small(n=40, steps=0)
+    runs = []
+    for dense in (False, True):
+        s = tcm.Sim.from_workload(wl, dense=dense, storage=storage)
+        s.step(70)
+        runs.append((s.read_field(0), s.read_field(1)))
+        s.close()
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("storage,bound", [("bf16", 6e-2), ("f16", 1e-2)])
+def test_16bit_error_against_fp64(storage, bound):
+    # Layered 48^3, 200 steps.  The rounding of phi^{n+1} to 8 (bf16) or 11
+    # (f16) significant bits each step leaves max|error| / max|phi| of about
+    # 3.3e-2 and 4.9e-3 (the storage form of the oracle gives the same
+    # numbers); the bounds allow 2x.
+    n, steps = 48, 200
+    m = W.Media(kind="rules", c_background=1.0, layers=[(n * 0.5, 1.6)])
+    dt = 0.5 / m.c_max()
+    w = W.ricker(1 / 10, dt)
+    ref = oracle.OracleTCM((n, n, n), m, 1.0, dt, dense=True, dtype=np.float64)
+    ref.add_source(n // 3, n // 2, n // 4, w)
+    ref.step(steps)
+    r = ref.read_field(0)
+    s = tcm.Sim((n, n, n), m, 1.0, dt, dense=True, storage=storage)
+    s.add_source(n // 3, n // 2, n // 4, w.astype(F32))
+    s.step(steps)
+    d = s.read_field(0).astype(np.float64) - r
+    rel = np.abs(d).max() / np.abs(r).max()
+    assert rel < bound
+    s.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_16bit_initial_field_and_energy(storage):
+    # eigenmode initial fields of amplitude 5000 (F16 scale 2^5)
+    shape = (24, 20, 28)
+    m = W.homogeneous(1.0)
+    dt = 0.5
+    now = (5000.0 * W.eigenmode(shape, (2, 1, 3))).astype(F32)
+    prev = (now * F32(0.98)).astype(F32)
+    s = tcm.Sim(shape, m, 1.0, dt, storage=storage)
+    s.set_field(now.astype(F32), prev.astype(F32))
+    o = oracle.OracleTCM(shape, m, 1.0, dt, storage=storage)
+    o.set_field(now.astype(F32), prev.astype(F32))
+    s.step(25)
+    o.step(25)
+    a, b = o.read_field(0), o.read_field(1)
+    assert np.array_equal(s.read_field(0), a) and np.array_equal(s.read_field(1), b)
+    k = oracle.k_from_c(np.ones(shape, F32), dt, 1.0, F32)
+    e_ref = oracle.energy(k, a, b)
+    assert s.energy() == pytest.approx(e_ref, rel=1e-12)
+    s.close()
+
+
+def test_16bit_batch_equals_solo():
+    wl = het_workload()
+    b = tcm.Batch(pool_bytes=4000 * tcm.tcm_slot_bytes(storage=tcm.TCM_STORAGE_BF16),
+                  max_bricks=20000, max_sims=4, storage="bf16")
+    a1 = b.add(wl)
+    a2 = b.add(W.small(n=32, steps=0))
+    b.step(50)
+    for sim, w in ((a1, wl), (a2, W.small(n=32, steps=0))):
+        s = tcm.Sim.from_workload(w, storage="bf16")
+        s.step(50)
+        assert np.array_equal(sim.read_field(0), s.read_field(0))
+        s.close()
+    b.close()
+
+
+def test_precision_workload_error_against_fp64_dense(capsys):
+    """256^3 layered, perturbed medium, 800 steps, relative threshold 1e-6 with
+    20-step decay: the TCM solution in each storage against the binary64 dense
+    grid (the oracle's plain definition).  Prints max and RMS errors relative
+    to max|phi| and RMS(phi)."""
+    wl = W.precision(256, 800)
+    (x, y, z, w), = wl.sources
+    k = oracle.k_from_c(wl.media.c, wl.dt, wl.dx, np.float64)
+    now = np.zeros(wl.shape)
+    prev = np.zeros(wl.shape)
+    oracle.set_threads(os.cpu_count() or 1)
+    now, prev = oracle.dense_run(k, now, prev, 800, sources=[(x, y, z, np.asarray(w, np.float64))])
+    del k
+    gmax = np.abs(now).max()
+    grms = np.sqrt((now ** 2).mean())
+    errs = {}
+    for st in ("f32", "bf16", "f16"):
+        s = tcm.Sim.from_workload(wl, storage=st)
+        s.step(800)
+        d = s.read_field(0).astype(np.float64) - now
+        errs[st] = (np.abs(d).max() / gmax, np.sqrt((d ** 2).mean()) / grms)
+        s.close()
+    with capsys.disabled():
+        print("\nprecision 256^3 x 800 vs FP64 dense (max rel, rms rel):",
+              {k_: tuple(float(f"{v:.3e}") for v in e) for k_, e in errs.items()})
+    # measured: f32 6.5e-6, f16 1.4e-2, bf16 0.45 (max rel).  The leapfrog
+    # recursion turns each rounding of phi^{n+1} into a velocity kick, so the
+    # error of a 16-bit store grows with the steps per period (~50 here).
+    assert errs["f32"][0] < 1e-4
+    assert errs["f16"][0] < 3e-2 and errs["bf16"][0] < 0.9
+    assert errs["f16"][0] < errs["bf16"][0] / 8

@@ -72,3 +72,23 @@ def test_summary_percentiles():
     s = serve.summarize(res, wall)
     assert s["requests"] == 6 and 0 < s["p50_s"] <= s["p99_s"] <= wall + 1e-6
     assert s["cell_updates"] > 0
+
+
+def test_mixed_storage_lanes_equal_solo_runs():
+    """FP32 and BF16 requests served side by side, one lane (batch) per
+    storage: each result equals its solo run in the same storage, bit for bit."""
+    reqs = small_stream(n=8, seed=77)
+    assert {r.storage for r in reqs} == {"f32", "bf16"}
+    srv = serve.Server(pool_bytes=900 * tcm.tcm_slot_bytes(), max_bricks=8000, max_sims=6,
+                       steps_per_tick=9, keep_fields=True, storages=("f32", "bf16"))
+    res = srv.run(reqs, time_scale=1.0, virtual=True)
+    srv.close()
+    assert len(res) == len(reqs)
+    for r in res:
+        q = reqs[r.rid]
+        assert r.storage == q.storage
+        s = tcm.Sim.from_workload(q.workload, storage=q.storage)
+        s.step(q.workload.steps)
+        assert np.array_equal(r.field, s.read_field(0)), q.rid
+        assert r.cell_updates == s.updates
+        s.close()

@@ -25,8 +25,13 @@ class FakeSim:
 
 
 class FakeBatch:
-    def __init__(self, pool_bytes, max_bricks, max_sims, device=0):
-        self.slots = pool_bytes // 4096
+    made = []
+
+    def __init__(self, pool_bytes, max_bricks, max_sims, device=0, storage="f32"):
+        self.slots = pool_bytes // (4096 if storage == "f32" else 2048)
+        self.storage = storage
+        self.max_sims = max_sims
+        FakeBatch.made.append(self)
         self.sims = []
         self.peak = 0
         self.events = []
@@ -47,6 +52,12 @@ class FakeBatch:
                 k = min(n, s.wl.steps - s.step_index)
                 s.step_index += k
                 s.updates += k * 512
+
+    def step_async(self, n):
+        self.step(n)
+
+    def sync(self):
+        pass
 
     def remove(self, sim):
         self.sims.remove(sim)
@@ -80,3 +91,41 @@ def test_summarize():
     s = serve.summarize(rs, 10.0)
     assert s["requests"] == 100 and abs(s["p50_s"] - 50.5) < 1e-9 and s["p99_s"] > 99
     assert s["cell_updates_per_s"] == 1000.0
+
+
+def test_lanes_route_by_storage():
+    FakeBatch.made = []
+    import pytest
+    mp = pytest.MonkeyPatch()
+    mp.setattr(serve.tcm, "Batch", FakeBatch)
+    try:
+        reqs = W.serving_stream(n_requests=30, seed=8, edge_lo=16, edge_hi=48, steps_lo=10,
+                                steps_hi=40, rate_hz=3.0)
+        assert {r.storage for r in reqs} == {"f32", "bf16"}
+        srv = serve.Server(pool_bytes=2000 * 4096, max_bricks=8192, max_sims=6, steps_per_tick=4,
+                           storages=("f32", "bf16"), pool_shares=(0.5, 0.5))
+        res = srv.run(reqs, virtual=True)
+        assert sorted(r.rid for r in res) == [r.rid for r in reqs]
+        lanes = {b.storage: b for b in FakeBatch.made}
+        assert set(lanes) == {"f32", "bf16"}
+        # the BF16 lane holds twice the boxes of the FP32 one for the same bytes
+        assert lanes["bf16"].slots == 2 * lanes["f32"].slots
+        for r in res:
+            assert r.storage == reqs[r.rid].storage
+        for st, b in lanes.items():
+            adds = [e[1] for e in b.events if e[0] == "add"]
+            want = [q.workload.name for q in sorted(reqs, key=lambda q: q.arrival) if q.storage == st]
+            assert adds == want and b.peak <= 3
+        s = serve.summarize(res, 1.0)
+        assert sum(s["by_storage"].values()) == 30
+    finally:
+        mp.undo()
+
+
+def test_request_that_never_fits_is_refused(monkeypatch):
+    monkeypatch.setattr(serve.tcm, "Batch", FakeBatch)
+    reqs = W.serving_stream(n_requests=3, seed=1, edge_lo=64, edge_hi=65, steps_lo=5, steps_hi=6)
+    srv = serve.Server(pool_bytes=100 * 4096, max_bricks=4096, max_sims=2)
+    import pytest
+    with pytest.raises(RuntimeError):
+        srv.run(reqs, virtual=True)
