@@ -254,28 +254,33 @@ def run_ours(args, rank, world, local_rank):
 
 
 def time_to_solution(torch, tcm, W, wl, dev, local_rank):
-    """Full 1500-step runs from create to the final field on the device: TCM vs
-    the same kernel over every brick (dense)."""
+    """Full 1500-step runs from create to the final field on the device: TCM
+    (update procedure every step, face neighbours), TCM on the Eq. 5 schedule
+    (update every 8 steps, 26 neighbours), and the same kernel over every
+    brick (dense, no update procedure)."""
+    import dataclasses
+    runs = [("dense", wl, True), ("tcm", wl, False),
+            ("tcm_eq5_26", dataclasses.replace(wl, interval=0, neighbours=26), False)]
     out = {}
-    for dense in (False, True):
+    ref = None
+    for name, w, dense in runs:
         torch.cuda.synchronize()
         t = time.perf_counter()
-        s = tcm.Sim.from_workload(wl, dense=dense, device=local_rank,
-                                  pool_bytes=None)
+        s = tcm.Sim.from_workload(w, dense=dense, device=local_rank, pool_bytes=None)
         s.step(TOTAL_STEPS)
-        buf = torch.empty(wl.shape, dtype=torch.float32, device=dev)
-        tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
+        buf = torch.empty(w.shape, dtype=torch.float32, device=dev)
+        tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), w.shape[::-1], buf.data_ptr())
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
-        out["dense" if dense else "tcm"] = {"seconds": dt, "cell_updates": s.updates}
-        if not dense:
+        r = {"seconds": dt, "cell_updates": s.updates, "schedule": list(s.schedule())}
+        if ref is None:
             ref = buf
+            r["max_abs_field"] = float(buf.abs().max().item())
         else:
-            diff = float((buf - ref).abs().max().item())
-            out["max_abs_diff_tcm_vs_dense"] = diff
-            out["max_abs_field"] = float(buf.abs().max().item())
+            r["max_abs_diff_vs_dense"] = float((buf - ref).abs().max().item())
+            del buf
+        out[name] = r
         s.close()
-        del buf
     del ref
     torch.cuda.empty_cache()
     return {"time_to_solution": {
@@ -284,8 +289,9 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
         "speedup": out["dense"]["seconds"] / out["tcm"]["seconds"],
         "tcm_cell_updates": out["tcm"]["cell_updates"],
         "dense_cell_updates": out["dense"]["cell_updates"],
-        "max_abs_diff_tcm_vs_dense": out["max_abs_diff_tcm_vs_dense"],
-        "max_abs_field": out["max_abs_field"]}}
+        "max_abs_diff_tcm_vs_dense": out["tcm"]["max_abs_diff_vs_dense"],
+        "max_abs_field": out["dense"]["max_abs_field"],
+        "eq5_interval_26_neighbours": out["tcm_eq5_26"]}}
 
 
 def precision_leg(torch, tcm, W, dev, local_rank):

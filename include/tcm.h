@@ -121,8 +121,31 @@ tcm_status tcm_add_source(tcm_sim *sim, int64_t x, int64_t y, int64_t z, const f
                           int64_t n_samples);
 
 /* Initial fields phi^0 and phi^{-1} (host arrays, nx*ny*nz).  Bricks holding a
- * non-zero value in either become active.  Only before the first tcm_step. */
+ * non-zero value in either become active, and the update procedure runs once
+ * on this state before the first step (bricks across a face whose max |phi^0|
+ * is above the level become active too; with the 26-neighbour set, all
+ * neighbours of a brick above the level).  Only before the first tcm_step. */
 tcm_status tcm_set_field(tcm_sim *sim, const float *phi_now, const float *phi_prev);
+
+/* Schedule of the update procedure ("Updating active cells", Eq. 5, Fig. 3).
+ * interval >= 1: the procedure runs after every interval-th step of this
+ * simulation (after step n when (n+1) % interval == 0); launches in between
+ * only step the active bricks.  interval = 0: Eq. 5, n = dx * 8 / (2 c_max
+ * dt) rounded down (at least 1), 8 = the brick edge in nodes.  A run covers
+ * the steps up to the next one: a source brick fed in any of them is kept or
+ * boxed, and a shut-down count (in time steps) drops by interval.
+ * neighbours = 6 (default): a brick stays if its maximum or the touching face
+ * of a boxed face neighbour is above the level; each face above the level
+ * boxes the brick across it.  neighbours = 26: a brick is triggered if its
+ * maximum is above the level or a source feeds it; it stays if it or a boxed
+ * one of its 26 neighbours is triggered by its maximum; a triggered brick
+ * boxes all 26 neighbours (the paper's nearest and diagonal cells) -- with
+ * interval <= 8 and threshold 0 this equals the dense grid exactly.
+ * Default interval 1, neighbours 6.  Only before the first step (TCM_ESTATE
+ * after); TCM_EINVAL for interval < 0 or another neighbour count. */
+tcm_status tcm_set_schedule(tcm_sim *sim, int interval, int neighbours);
+/* The schedule in use (interval resolved when 0 was given). */
+tcm_status tcm_schedule(const tcm_sim *sim, int *interval, int *neighbours);
 
 /* Advance n steps; returns when they are done (or failed).  TCM_ENOMEM: the
  * pool ran out, the step completed without the bricks that found no box and

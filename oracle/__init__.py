@@ -74,6 +74,7 @@ def lib():
                 getattr(L, f"orc_tcm_{name}_{sfx}").restype = _i64
             getattr(L, f"orc_tcm_status_{sfx}").argtypes = [_vp]
             getattr(L, f"orc_tcm_set_storage_{sfx}").argtypes = [_vp, C.c_int]
+            getattr(L, f"orc_tcm_set_schedule_{sfx}").argtypes = [_vp, C.c_int, C.c_int]
             getattr(L, f"orc_tcm_storage_scale_{sfx}").argtypes = [_vp]
             getattr(L, f"orc_tcm_storage_scale_{sfx}").restype = _d
             getattr(L, f"orc_tcm_brick_media_{sfx}").argtypes = [_vp, _i64, _vp]
@@ -190,7 +191,7 @@ class OracleTCM:
     def __init__(self, shape, media, dx: float, dt: float, brick=(8, 8, 8),
                  thr_mode: int = THR_ABSOLUTE, tau: float = 0.0, decay_alpha: float = 1.0,
                  decay_steps: int = 0, max_slots: int = 0, dense: bool = False,
-                 dtype=np.float32, storage="f32"):
+                 dtype=np.float32, storage="f32", interval: int = 1, neighbours: int = 6):
         self.dtype = np.dtype(dtype)
         self._s = _sfx(dtype)
         self.shape = tuple(int(v) for v in shape)
@@ -221,6 +222,10 @@ class OracleTCM:
         if st != STORAGE_F32 and self._f("set_storage")(h, st) != 0:
             self.close()
             raise ValueError("storage not supported by this program")
+        if (interval, neighbours) != (1, 6) and self._f("set_schedule")(h, int(interval),
+                                                                         int(neighbours)) != 0:
+            self.close()
+            raise ValueError("invalid update schedule")
         self.mx = -(-nx // bx)
         self.my = -(-ny // by)
         self.mz = -(-nz // bz)

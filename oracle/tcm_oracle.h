@@ -148,6 +148,28 @@ int orc_tcm_set_storage_f64(orc_tcm *t, int storage);
 /* The scale s in use (1 before the first step). */
 double orc_tcm_storage_scale_f32(const orc_tcm *t);
 double orc_tcm_storage_scale_f64(const orc_tcm *t);
+/* Schedule of the update procedure (before the first step; default 1, 6).
+ * interval >= 1: the procedure runs after every interval-th step (after step
+ * n when (n+1) % interval == 0; Eq. 5 gives interval = dx*L/(2 c dt) for
+ * cells of L nodes).  Between runs the active cells, their shut-down counts
+ * and the Eq. 6 factors stay as set.  A run covers steps n+1 .. n+interval:
+ * a source cell fed at any of them is kept / boxed, and a cell in shut-down
+ * has its count (in time steps) reduced by interval, released at <= 0.
+ * neighbours = 6: a cell stays if its maximum or a boxed face neighbour's
+ * touching face is above the level; faces above the level trigger the cell
+ * across them.  neighbours = 26: a cell is triggered when it is boxed with
+ * its maximum above the level, or a source feeds it during the steps the run
+ * covers; a cell stays if it or any of its 26 neighbours is triggered; a
+ * triggered cell boxes all 26 neighbours (steps 4 and 5 of the update,
+ * Fig. 3: nearest and diagonal cells).  Before the first step the procedure
+ * runs once on the initial state (level from max |phi^0|; 6 neighbours: the
+ * cell across each face whose max |phi^0| is above it; 26: all neighbours of
+ * a cell above it in max(|phi^0|,|phi^-1|) or fed by a source in steps
+ * 0 .. interval-1), releasing nothing; with the 26-neighbour set, adding a
+ * source boxes its cell's neighbourhood at once.  Returns ORC_EINVAL for
+ * interval < 1 or another neighbour count, ORC_ESTATE after the first step. */
+int orc_tcm_set_schedule_f32(orc_tcm *t, int interval, int neighbours);
+int orc_tcm_set_schedule_f64(orc_tcm *t, int interval, int neighbours);
 int orc_tcm_step_f32(orc_tcm *t, int64_t n);
 int orc_tcm_step_f64(orc_tcm *t, int64_t n);
 /* which = 0: phi^n, 1: phi^{n-1}; zeros where no box is allocated. */

@@ -43,6 +43,8 @@ struct HostSim {
     bool have_field = false;
     long long step = 0;
     long long target = -1;   // freeze after this many steps (-1: never)
+    double dx = 1, dt = 1;
+    float c_max = 0.f;
     SimDev dev{};
 };
 
@@ -260,7 +262,8 @@ float model_c_max(const tcm_domain *d, const tcm_velocity_model *v, bool *bad)
 
 // Argument checks shared by tcm_create and tcm_batch_add, before any GPU work.
 tcm_status check_sim_args(const tcm_domain *domain, const tcm_velocity_model *velocity, double dx, double dt,
-                          double threshold, tcm_brick brick, int storage, int threshold_mode, int decay_steps)
+                          double threshold, tcm_brick brick, int storage, int threshold_mode, int decay_steps,
+                          float *c_max_out)
 {
     if (!domain || !velocity) return TCM_EINVAL;
     if (domain->nx < 1 || domain->ny < 1 || domain->nz < 1) return TCM_EINVAL;
@@ -287,6 +290,7 @@ tcm_status check_sim_args(const tcm_domain *domain, const tcm_velocity_model *ve
     const float cmax = model_c_max(domain, velocity, &bad);
     if (bad) return TCM_EINVAL;
     if ((double)cmax * dt / dx > INV_SQRT3) return TCM_ECFL;
+    *c_max_out = cmax;
     return TCM_OK;
 }
 
@@ -456,8 +460,8 @@ tcm_status bulk_sim(tcm_batch *b, HostSim &h, const tcm_velocity_model *velocity
 }
 
 tcm_status sim_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_model *velocity, double dx, double dt,
-                   double threshold, int thr_mode, float alpha, int decay_steps, int dense, long long n_steps,
-                   int *out_id)
+                   float c_max, double threshold, int thr_mode, float alpha, int decay_steps, int dense,
+                   long long n_steps, int *out_id)
 {
     int id = -1;
     for (int i = 0; i < b->max_sims; ++i)
@@ -505,6 +509,11 @@ tcm_status sim_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_mo
     S.live = 0;
     S.scale = 1.f;
     S.inv_scale = 1.f;
+    S.interval = 1;
+    S.neighbours = 6;
+    h.c_max = c_max;
+    h.dx = dx;
+    h.dt = dt;
     h.used = true;
     // the brick range's words now belong to this sim
     {
@@ -527,8 +536,76 @@ tcm_status sim_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_mo
     return TCM_OK;
 }
 
+// The update procedure run on the initial state (before step 0), over the
+// initially boxed bricks `mark`: returns the bricks it triggers.  Level from
+// the initial phi^0 (relative: tau x max |phi^0|, FP64).  6-neighbour set:
+// the brick across each face whose max |phi^0| is above the level.
+// 26-neighbour set: all 26 neighbours of a brick whose max(|phi^0|,
+// |phi^-1|) is above the level or that a source feeds in steps
+// 0 .. interval-1.
+std::vector<long long> initial_triggers(const HostSim &h, const std::vector<char> &mark)
+{
+    std::vector<long long> out;
+    const long long nb = h.n_bricks;
+    std::vector<float> mc, fm;
+    double G = 0.0;
+    if (h.have_field) {
+        mc.assign((size_t)nb, 0.f);
+        fm.assign((size_t)nb * 6, 0.f);
+        for (long long z = 0; z < h.nz; ++z)
+            for (long long y = 0; y < h.ny; ++y)
+                for (long long x = 0; x < h.nx; ++x) {
+                    const size_t i = (size_t)((z * h.ny + y) * h.nx + x);
+                    const float a = std::fabs(h.init_now[i]), p = std::fabs(h.init_prev[i]);
+                    if (a == 0.f && p == 0.f) continue;
+                    const size_t b = (size_t)(((z / BZ) * h.my + (y / BY)) * h.mx + (x / BX));
+                    G = std::max(G, (double)a);
+                    mc[b] = std::max(mc[b], std::max(a, p));
+                    const long long lx = x % BX, ly = y % BY, lz = z % BZ;
+                    if (lx == 0) fm[b * 6 + 0] = std::max(fm[b * 6 + 0], a);
+                    if (lx == BX - 1) fm[b * 6 + 1] = std::max(fm[b * 6 + 1], a);
+                    if (ly == 0) fm[b * 6 + 2] = std::max(fm[b * 6 + 2], a);
+                    if (ly == BY - 1) fm[b * 6 + 3] = std::max(fm[b * 6 + 3], a);
+                    if (lz == 0) fm[b * 6 + 4] = std::max(fm[b * 6 + 4], a);
+                    if (lz == BZ - 1) fm[b * 6 + 5] = std::max(fm[b * 6 + 5], a);
+                }
+    }
+    const double thr = h.dev.thr_mode == TCM_THR_RELATIVE ? h.dev.tau * G : h.dev.tau;
+    std::vector<char> src((size_t)nb, 0);
+    for (const auto &q : h.sources)
+        if (!q.w.empty() && q.start <= h.step + h.dev.interval - 1) src[(size_t)q.brick] = 1;
+    for (long long b = 0; b < nb; ++b) {
+        if (!mark[(size_t)b]) continue;
+        const int cx = (int)(b % h.mx), cy = (int)((b / h.mx) % h.my), cz = (int)(b / ((long long)h.mx * h.my));
+        if (h.dev.neighbours == 26) {
+            const bool hot = src[(size_t)b] || (h.have_field && (double)mc[(size_t)b] > thr);
+            if (!hot) continue;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int ax = cx + dx, ay = cy + dy, az = cz + dz;
+                        if ((!dx && !dy && !dz) || ax < 0 || ay < 0 || az < 0 || ax >= h.mx || ay >= h.my ||
+                            az >= h.mz)
+                            continue;
+                        out.push_back(((long long)az * h.my + ay) * h.mx + ax);
+                    }
+        } else if (h.have_field) {
+            for (int f = 0; f < 6; ++f) {
+                if (!((double)fm[(size_t)b * 6 + f] > thr)) continue;
+                const int ax = cx + (f == 0 ? -1 : f == 1 ? 1 : 0);
+                const int ay = cy + (f == 2 ? -1 : f == 3 ? 1 : 0);
+                const int az = cz + (f == 4 ? -1 : f == 5 ? 1 : 0);
+                if (ax < 0 || ay < 0 || az < 0 || ax >= h.mx || ay >= h.my || az >= h.mz) continue;
+                out.push_back(((long long)az * h.my + ay) * h.mx + ax);
+            }
+        }
+    }
+    return out;
+}
+
 // Box a simulation's initial bricks (source bricks, bricks with initial
-// values, or every brick of a dense simulation) and start it stepping.
+// values, or every brick of a dense simulation, plus the bricks the update
+// procedure triggers from that state) and start it stepping.
 tcm_status sim_prime(tcm_batch *b, int id)
 {
     HostSim &h = b->sims[id];
@@ -576,6 +653,11 @@ tcm_status sim_prime(tcm_batch *b, int id)
                             mark[(size_t)(((z / BZ) * h.my + (y / BY)) * h.mx + (x / BX))] = 1;
                     }
         }
+        // The update procedure before the first step: triggers from the
+        // initial fields, and (26-neighbour set) the neighbourhoods of
+        // source bricks.
+        const std::vector<long long> extra = initial_triggers(h, mark);
+        for (long long e : extra) mark[(size_t)e] = 1;
         for (long long i = 0; i < h.n_bricks; ++i)
             if (mark[(size_t)i]) init.push_back(i);
         n_init = (long long)init.size();
@@ -664,13 +746,19 @@ tcm_status batch_step_async(tcm_batch *b, long long n)
     TRYS(prime_all(b));
     for (long long i = 0; i < n; ++i) {
         TRYS(ensure_list(b));
-        cudaError_t e = launch_step(b->E, b->grid, b->stream);
+        // Does any simulation run the update procedure after this step?
+        int manage = 0;
+        for (int id = 0; id < b->max_sims && !manage; ++id) {
+            const HostSim &h = b->sims[id];
+            if (h.used && h.live && !h.dense && (h.step + 1) % h.dev.interval == 0) manage = 1;
+        }
+        cudaError_t e = launch_step(b->E, b->grid, manage, b->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return poison(b, TCM_EDEVICE);
         }
         b->launches += 1;
-        b->list_parity ^= 1;
+        if (manage) b->list_parity ^= 1;
         for (int id = 0; id < b->max_sims; ++id) {
             HostSim &h = b->sims[id];
             if (!h.used || !h.live) continue;
@@ -750,8 +838,9 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     if (!out) return TCM_EINVAL;
     *out = nullptr;
     if (!options) return TCM_EINVAL;
+    float c_max = 0.f;
     TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, options->storage, options->threshold_mode,
-                        options->decay_steps));
+                        options->decay_steps, &c_max));
     const long long n_bricks = ((domain->nx + BX - 1) / BX) * ((domain->ny + BY - 1) / BY) *
                                ((domain->nz + BZ - 1) / BZ);
     size_t slot_bytes = 0;
@@ -765,8 +854,8 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
                    n_bricks, 1, &b));
     DeviceGuard g(b->device);
     int id = -1;
-    tcm_status st = sim_add(b, domain, velocity, dx, dt, threshold, options->threshold_mode, options->decay_alpha,
-                            options->decay_steps, options->dense ? 1 : 0, -1, &id);
+    tcm_status st = sim_add(b, domain, velocity, dx, dt, c_max, threshold, options->threshold_mode,
+                            options->decay_alpha, options->decay_steps, options->dense ? 1 : 0, -1, &id);
     if (st != TCM_OK) {
         tcm_batch_destroy(b);
         return st;
@@ -796,6 +885,30 @@ tcm_status tcm_add_source(tcm_sim *s, int64_t x, int64_t y, int64_t z, const flo
     q.start = h->step;
     q.w.assign(wavelet, wavelet + n);
     h->sources.push_back(std::move(q));
+    return TCM_OK;
+}
+
+tcm_status tcm_set_schedule(tcm_sim *s, int interval, int neighbours)
+{
+    HostSim *h = sim_of(s);
+    if (!h || interval < 0 || (neighbours != 6 && neighbours != 26)) return TCM_EINVAL;
+    if (h->primed) return TCM_ESTATE;
+    if (interval == 0) {
+        // Eq. 5: n = dx * (cell length) / (2 c dt), cell length BX nodes
+        const double n = h->c_max > 0.f ? h->dx * BX / (2.0 * (double)h->c_max * h->dt) : 1.0;
+        interval = (int)std::max(1.0, std::min(std::floor(n), 1e6));
+    }
+    h->dev.interval = interval;
+    h->dev.neighbours = neighbours;
+    return TCM_OK;
+}
+
+tcm_status tcm_schedule(const tcm_sim *s, int *interval, int *neighbours)
+{
+    HostSim *h = sim_of(s);
+    if (!h || !interval || !neighbours) return TCM_EINVAL;
+    *interval = h->dev.interval;
+    *neighbours = h->dev.neighbours;
     return TCM_OK;
 }
 
@@ -1039,12 +1152,14 @@ tcm_status tcm_batch_add(tcm_batch *b, const tcm_domain *domain, const tcm_veloc
 {
     if (!b || !out) return TCM_EINVAL;
     *out = nullptr;
-    TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, b->E.storage, threshold_mode, decay_steps));
+    float c_max = 0.f;
+    TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, b->E.storage, threshold_mode, decay_steps,
+                        &c_max));
     if (b->poisoned) return TCM_ESTATE;
     DeviceGuard g(b->device);
     int id = -1;
-    TRYS(sim_add(b, domain, velocity, dx, dt, threshold, threshold_mode, decay_alpha, decay_steps, dense ? 1 : 0,
-                 n_steps, &id));
+    TRYS(sim_add(b, domain, velocity, dx, dt, c_max, threshold, threshold_mode, decay_alpha, decay_steps,
+                 dense ? 1 : 0, n_steps, &id));
     tcm_sim *s = new (std::nothrow) tcm_sim();
     if (!s) {
         sim_release(b, id);

@@ -85,6 +85,8 @@ struct SimDev {
     int live;              // 1 while the sim steps (0: frozen or released)
     float scale;           // stored field value = phi / scale (power of two)
     float inv_scale;
+    int interval;          // the update procedure runs after every interval-th step
+    int neighbours;        // 6: activation across hot faces; 26: all neighbours of a hot cell
     int pad1;
     // mutable (device-owned)
     long long step;        // n of phi^n
@@ -118,6 +120,8 @@ struct EngineState {
     unsigned long long launches;
     unsigned long long t_start, t_p1, t_p2;   // globaltimer stamps of the current launch
     unsigned long long phase_ns[3];           // cumulative: time stepping, update, compaction
+    int list_age;          // launches since the active list was built (phase of its nh)
+    int pad_age;
 };
 
 struct Engine {
@@ -201,7 +205,9 @@ cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStrea
 // packed[i] = {phi^n, phi^{n-1}} of global brick gids[i] (boxed), into its box.
 cudaError_t launch_scatter_field(const Engine &e, const float *packed, const long long *gids, long long n,
                                  int now_half, cudaStream_t s);
-cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s);
+// manage = 0: no simulation runs the update procedure after this step (time
+// stepping only; the active list is kept).
+cudaError_t launch_step(const Engine &e, int grid, int manage, cudaStream_t s);
 int step_grid_size(int device);
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,

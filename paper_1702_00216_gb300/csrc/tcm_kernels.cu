@@ -313,7 +313,7 @@ __device__ __forceinline__ void flush_updates(const Engine &E, unsigned long lon
 // ---------------------------------------------------------------------------
 template <int ST>
 __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
-                                         bool share_xm, bool share_xp, unsigned long long &cells,
+                                         bool share_xm, bool share_xp, int age_flip, unsigned long long &cells,
                                          unsigned long long &scells, float &gacc, int &gsim, int &gnh)
 {
     const int x4 = t % XQ;
@@ -322,7 +322,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     SimDev *S = E.sims + sim;
     const int mx = __ldg(&S->mx), my = __ldg(&S->my);
     const int nx = __ldg(&S->nx), ny = __ldg(&S->ny), nz = __ldg(&S->nz);
-    const int nh = w.nh;
+    const int nh = w.nh ^ age_flip;   // the list may be older than this step
     const int b = w.brick;
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
     using F = Fld<ST>;
@@ -496,11 +496,12 @@ __device__ __forceinline__ bool brick_has_src(const Engine &E, const SimDev *S, 
     return false;
 }
 
-__device__ __forceinline__ bool forced_at(const Engine &E, const SimDev *S, int b, long long n)
+// A source of this sim feeds brick b at some step of [n0, n1].
+__device__ __forceinline__ bool forced_in(const Engine &E, const SimDev *S, int b, long long n0, long long n1)
 {
     for (int s = S->src_begin; s < S->src_end; ++s) {
         const SrcDev &sd = E.src[s];
-        if (sd.brick == b && n >= sd.start && n < sd.start + sd.len) return true;
+        if (sd.brick == b && n1 >= sd.start && n0 < sd.start + sd.len) return true;
     }
     return false;
 }
@@ -532,22 +533,23 @@ __device__ __forceinline__ int agg_add_n(int *ctr, int n)
 // boxes"): claim each with a CAS on Cell2box (-1 -> -2; another thread may
 // be boxing it), pop one vacant box per claim won, then publish.  The
 // steps are batched so the thread waits for each kind of atomic once.
+template <int N>
 __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_local, int n)
 {
     const long long bb = S->brick_base;
-    bool won[6];
+    bool won[N];
     int nw = 0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) won[i] = i < n && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1;
+    for (int i = 0; i < N; ++i) won[i] = i < n && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) nw += won[i] ? 1 : 0;
+    for (int i = 0; i < N; ++i) nw += won[i] ? 1 : 0;
     if (nw == 0) return;
     // vacant boxes free_stack[top - nw .. top - 1]
     const int top = atomicSub(&E.st->free_top, nw);
     const int nn = agg_add_n(&E.st->n_new, nw);
     int k = 0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < N; ++i) {
         if (!won[i]) continue;
         const long long g = bb + b_local[i];
         const int idx = top - 1 - k;
@@ -735,6 +737,9 @@ __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int st
 struct SimCache {
     int sim = -1;
     bool dense = false;
+    bool manage = false;   // this sim runs the update procedure after this step
+    int interval = 1;
+    int neighbours = 6;
     long long step = 0;
     double thr = 0.0;
 };
@@ -746,8 +751,101 @@ __device__ __forceinline__ void sim_cache(const Engine &E, int sim, SimCache &c)
     c.sim = sim;
     c.dense = __ldg(&S->dense) != 0;
     c.step = __ldcg(&S->step);
+    c.interval = __ldg(&S->interval);
+    c.neighbours = __ldg(&S->neighbours);
+    c.manage = (c.step + 1) % c.interval == 0;
     const double G = (double)__uint_as_float(__ldcg(&S->gmax[c.step & 1]));
     c.thr = __ldg(&S->thr_mode) == 1 ? __ldg(&S->tau) * G : __ldg(&S->tau);
+}
+
+// Record the shut-down count of a kept brick, or release its box.
+__device__ __forceinline__ void keep_or_release(const Engine &E, const WorkItem &w, bool keep, unsigned sd,
+                                                unsigned sd0, long long g, int slot)
+{
+    if (keep) {
+        if (sd != sd0) E.sd_of_brick[g] = (unsigned short)((w.flags & FLAG_HAS_SRC) | sd);
+    } else {
+        if (sd0 != 0) E.sd_of_brick[g] = (unsigned short)(w.flags & FLAG_HAS_SRC);
+        atomicExch(E.slot_of_brick + g, -1);
+        atomicAnd(E.bitmap + (g >> 5), ~(1u << (unsigned)(g & 31)));
+        atomicSub(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
+        E.retired[agg_add(&E.st->n_retired, 1)] = slot;
+    }
+}
+
+// The update procedure with the 26-neighbour set (steps 4-5, Fig. 3): a
+// brick is triggered when its own maximum is above the level or a source
+// feeds it during the steps the update covers; it stays when it or any of
+// its 26 neighbours is triggered; a triggered brick boxes all 26 neighbours.
+__device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool above, double thr, int interval,
+                                       int sim, SimDev *S)
+{
+    const int b = w.brick;
+    const int mx = __ldg(&S->mx), my = __ldg(&S->my), mz = __ldg(&S->mz);
+    const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
+    const long long g0 = __ldg(&S->brick_base);
+    const long long step = __ldcg(&S->step);
+    const bool forced = (w.flags & FLAG_HAS_SRC) && forced_in(E, S, b, step + 1, step + interval);
+    int nslot[26];
+    int nid[26];
+    int k = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (!dx && !dy && !dz) continue;
+                const int ax = cx + dx, ay = cy + dy, az = cz + dz;
+                const bool in = ax >= 0 && ay >= 0 && az >= 0 && ax < mx && ay < my && az < mz;
+                nid[k] = in ? (az * my + ay) * mx + ax : -1;
+                nslot[k] = in ? __ldcg(E.slot_of_brick + g0 + nid[k]) : -3;
+                ++k;
+            }
+    bool hot = above || forced;
+    if (!hot) {
+        // a neighbour a source feeds during the steps this update covers
+        const long long n0 = step + 1, n1 = n0 + interval - 1;
+        for (int s = S->src_begin; s < S->src_end && !hot; ++s) {
+            const SrcDev &sd = E.src[s];
+            const int sx = sd.brick % mx, sy = (sd.brick / mx) % my, sz = sd.brick / (mx * my);
+            if (abs(sx - cx) <= 1 && abs(sy - cy) <= 1 && abs(sz - cz) <= 1 && n1 >= sd.start &&
+                n0 < sd.start + sd.len)
+                hot = true;
+        }
+    }
+    if (!hot) {
+        float nm[26];
+#pragma unroll
+        for (int i = 0; i < 26; ++i) nm[i] = nslot[i] >= 0 ? __ldcg(E.rec + (size_t)nslot[i] * 8 + 6) : 0.f;
+#pragma unroll
+        for (int i = 0; i < 26; ++i)
+            if (nslot[i] >= 0 && (double)nm[i] > thr) hot = true;
+    }
+    unsigned sd = w.flags & SD_MASK;
+    const unsigned sd0 = sd;
+    bool keep;
+    if (hot) {
+        sd = 0;
+        keep = true;
+    } else if (sd > 0) {
+        sd = sd > (unsigned)interval ? sd - (unsigned)interval : 0u;
+        keep = sd > 0;
+    } else if (__ldg(&S->decay_steps) > 0) {
+        sd = (unsigned)__ldg(&S->decay_steps);
+        keep = true;
+    } else {
+        keep = false;
+    }
+    keep_or_release(E, w, keep, sd, sd0, g0 + w.brick, w.slot);
+    if (above || forced) {
+        int nbs[26];
+        int n = 0;
+#pragma unroll
+        for (int i = 0; i < 26; ++i)
+            if (nslot[i] == -1) nbs[n++] = nid[i];
+        if (n > 0) claim_bricks<26>(E, sim, S, nbs, n);
+    }
 }
 
 __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, const float4 &r0, const float4 &r1,
@@ -757,9 +855,14 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
     const int sim = (int)(w.flags >> 16);
     SimDev *S = E.sims + sim;
     sim_cache(E, sim, c);
-    if (c.dense) return;
+    if (c.dense || !c.manage) return;
     const long long step = c.step;
     const double thr = c.thr;
+    const int b = w.brick;
+    if (c.neighbours == 26) {
+        p2_item26(E, w, (double)r1.z > thr, thr, c.interval, sim, S);
+        return;
+    }
     const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
     bool hot = (double)r1.z > thr;
     if (!hot) {
@@ -771,8 +874,8 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
         for (int f = 0; f < 6; ++f)
             if (w.nb[f] >= 0 && (double)nf[f] > thr) hot = true;
     }
-    const int b = w.brick;
-    if (!hot && (w.flags & FLAG_HAS_SRC) && forced_at(E, S, b, step + 1)) hot = true;
+    // a source feeds it during the steps this update covers
+    if (!hot && (w.flags & FLAG_HAS_SRC) && forced_in(E, S, b, step + 1, step + c.interval)) hot = true;
     unsigned sd = w.flags & SD_MASK;
     const unsigned sd0 = sd;
     bool keep;
@@ -780,7 +883,8 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
         sd = 0;
         keep = true;
     } else if (sd > 0) {
-        sd -= 1;
+        // the count is in time steps; `interval` of them passed
+        sd = sd > (unsigned)c.interval ? sd - (unsigned)c.interval : 0u;
         keep = sd > 0;
     } else if (__ldg(&S->decay_steps) > 0) {
         sd = (unsigned)__ldg(&S->decay_steps);
@@ -788,16 +892,7 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
     } else {
         keep = false;
     }
-    const long long g = __ldg(&S->brick_base) + b;
-    if (keep) {
-        if (sd != sd0) E.sd_of_brick[g] = (unsigned short)((w.flags & FLAG_HAS_SRC) | sd);
-    } else {
-        if (sd0 != 0) E.sd_of_brick[g] = (unsigned short)(w.flags & FLAG_HAS_SRC);
-        atomicExch(E.slot_of_brick + g, -1);
-        atomicAnd(E.bitmap + (g >> 5), ~(1u << (unsigned)(g & 31)));
-        atomicSub(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
-        E.retired[agg_add(&E.st->n_retired, 1)] = slot;
-    }
+    keep_or_release(E, w, keep, sd, sd0, __ldg(&S->brick_base) + b, slot);
     const int mx = __ldg(&S->mx), my = __ldg(&S->my);
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
     int nbs[6];
@@ -811,17 +906,30 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
             nbs[n++] = (az * my + ay) * mx + ax;
         }
     }
-    if (n > 0) claim_bricks(E, sim, S, nbs, n);
+    if (n > 0) claim_bricks<6>(E, sim, S, nbs, n);
 }
 
 // ---------------------------------------------------------------------------
 // The step kernel.
 // ---------------------------------------------------------------------------
+// Advance every live sim's step (after all blocks have read it this launch).
+__device__ void advance_steps(const Engine &E)
+{
+    for (int s = 0; s < E.n_sims; ++s) {
+        SimDev *S = E.sims + s;
+        if (!__ldcg(&S->live)) continue;
+        const long long n = __ldcg(&S->step);
+        S->gmax[(n + 1) & 1] = 0u;
+        S->step = n + 1;
+    }
+}
+
 template <int ST>
-__global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
+__global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int manage)
 {
     EngineState *st = E.st;
     const int cur = __ldcg(&st->list_parity);
+    const int age_flip = __ldcg(&st->list_age) & 1;
     const WorkItem *L = cur ? E.items1 : E.items0;
     WorkItem *Lnext = cur ? E.items0 : E.items1;
     const int nact = __ldcg(&st->n_active[cur]);
@@ -864,8 +972,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
             const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
             const bool pair_x = seg == 0 ? (other_v && w.nb[1] >= 0 && w.nb[1] == other_slot)
                                          : (v && w.nb[0] >= 0 && w.nb[0] == other_slot);
-            p1_brick<ST>(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, cells, scells, gacc, gsim,
-                         gnh);
+            p1_brick<ST>(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, age_flip, cells, scells, gacc,
+                         gsim, gnh);
             pr = pn;
             w = wn;
             v = vn;
@@ -875,6 +983,23 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(FULL, cells, o);
         if (lane == 0 && cells) atomicAdd(&st->updates, cells);
+    }
+    if (!manage) {
+        // Time stepping only: the last block to finish advances the step and
+        // the age of the (kept) active list.
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&st->p3_done, 1u) == gridDim.x - 1) {
+                __threadfence();
+                advance_steps(E);
+                st->list_age += 1;
+                st->launches += 1;
+                st->p3_done = 0u;
+                st->phase_ns[0] += globaltimer() - __ldcg(&st->t_start);
+            }
+        }
+        return;
     }
     if (!grid_barrier(st)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t_p1 = globaltimer();
@@ -904,14 +1029,17 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
             for (int u = 0; u < U; ++u)
                 if (base + u * nthr < nact && w[u].slot >= 0) p2_item(E, w[u], r0[u], r1[u], sc);
         }
-        // Manual activation of source bricks still being fed at step n+1.
+        // Manual activation of source bricks still being fed during the
+        // steps this update covers (n+1 .. n+interval).
         if (blockIdx.x == 0) {
             for (int s = threadIdx.x; s < E.n_src; s += BLOCK) {
                 const SrcDev sd = E.src[s];
                 SimDev *S = E.sims + sd.sim;
                 if (S->dense) continue;
                 const long long n1 = __ldcg(&S->step) + 1;
-                if (n1 >= sd.start && n1 < sd.start + sd.len) claim_bricks(E, sd.sim, S, &sd.brick, 1);
+                const int iv = __ldg(&S->interval);
+                if (n1 % iv != 0) continue;   // this sim does not run the update now
+                if (n1 + iv - 1 >= sd.start && n1 < sd.start + sd.len) claim_bricks<1>(E, sd.sim, S, &sd.brick, 1);
             }
         }
     }
@@ -939,14 +1067,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
             __threadfence();
             if (atomicAdd(&st->p3_done, 1u) == gridDim.x - 1) {
                 __threadfence();
-                for (int s = 0; s < E.n_sims; ++s) {
-                    SimDev *S = E.sims + s;
-                    if (!__ldcg(&S->live)) continue;
-                    const long long n = __ldcg(&S->step);
-                    S->gmax[(n + 1) & 1] = 0u;
-                    S->step = n + 1;
-                }
+                advance_steps(E);
                 st->list_parity = cur ^ 1;
+                st->list_age = 0;
                 st->launches += 1;
                 st->p3_done = 0u;
                 const unsigned long long t3 = globaltimer();
@@ -964,6 +1087,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E)
 __global__ void __launch_bounds__(BLOCK, 1) k_compact(Engine E, int parity)
 {
     compact_list(E, parity ? E.items1 : E.items0, &E.st->n_active[parity], 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) E.st->list_age = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1350,10 +1474,11 @@ int step_grid_size(int device)
     return sms * per_sm;
 }
 
-cudaError_t launch_step(const Engine &e, int grid, cudaStream_t s)
+cudaError_t launch_step(const Engine &e, int grid, int manage, cudaStream_t s)
 {
     Engine copy = e;
-    void *args[] = {&copy};
+    int m = manage;
+    void *args[] = {&copy, &m};
     const void *fn = e.storage == ST_BF16 ? (const void *)k_step<ST_BF16>
                      : e.storage == ST_F16 ? (const void *)k_step<ST_F16>
                                            : (const void *)k_step<ST_F32>;

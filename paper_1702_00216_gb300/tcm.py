@@ -28,7 +28,7 @@ def storage_code(storage) -> int:
     return STORAGES[storage] if isinstance(storage, str) else int(storage)
 
 EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "tcm_step",
-           "tcm_step_async", "tcm_sync", "tcm_read_field", "tcm_read_field_device",
+           "tcm_step_async", "tcm_sync", "tcm_set_schedule", "tcm_schedule", "tcm_read_field", "tcm_read_field_device",
            "tcm_active_count", "tcm_active_bricks", "tcm_updates", "tcm_energy",
            "tcm_energy_noalloc",
            "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_step_index",
@@ -86,6 +86,8 @@ def lib():
             "tcm_create": ([_vp, _vp, C.c_double, C.c_double, C.c_double, tcm_brick, _vp, _vp], C.c_int),
             "tcm_add_source": ([_vp, _i64, _i64, _i64, _vp, _i64], C.c_int),
             "tcm_set_field": ([_vp, _vp, _vp], C.c_int),
+            "tcm_set_schedule": ([_vp, C.c_int, C.c_int], C.c_int),
+            "tcm_schedule": ([_vp, _vp, _vp], C.c_int),
             "tcm_step": ([_vp, _i64], C.c_int),
             "tcm_step_async": ([_vp, _i64], C.c_int),
             "tcm_sync": ([_vp], C.c_int),
@@ -189,6 +191,16 @@ def tcm_set_field(h, now, prev):
     now = np.ascontiguousarray(now, dtype=np.float32)
     prev = np.ascontiguousarray(prev, dtype=np.float32)
     _chk(lib().tcm_set_field(h, _ptr(now), _ptr(prev)), "tcm_set_field")
+
+
+def tcm_set_schedule(h, interval=1, neighbours=6):
+    _chk(lib().tcm_set_schedule(h, int(interval), int(neighbours)), "tcm_set_schedule")
+
+
+def tcm_schedule(h):
+    iv, nb = C.c_int(0), C.c_int(0)
+    _chk(lib().tcm_schedule(h, C.byref(iv), C.byref(nb)), "tcm_schedule")
+    return iv.value, nb.value
 
 
 def tcm_step(h, n=1):
@@ -400,6 +412,8 @@ class Sim:
                 pool_bytes=pool, dense=dense, **kw)
         for x, y, z, w in wl.sources:
             s.add_source(x, y, z, np.asarray(w, dtype=np.float32))
+        if (wl.interval, wl.neighbours) != (1, 6):
+            s.set_schedule(wl.interval, wl.neighbours)
         return s
 
     @property
@@ -411,6 +425,12 @@ class Sim:
 
     def set_field(self, now, prev):
         tcm_set_field(self._h, now, prev)
+
+    def set_schedule(self, interval=1, neighbours=6):
+        tcm_set_schedule(self._h, interval, neighbours)
+
+    def schedule(self):
+        return tcm_schedule(self._h)
 
     def step(self, n=1):
         tcm_step(self._h, n)
@@ -512,6 +532,8 @@ class Batch:
         sim = Sim._wrap(h, wl.shape, wl.brick)
         for x, y, z, w in wl.sources:
             sim.add_source(x, y, z, np.asarray(w, dtype=np.float32))
+        if (getattr(wl, "interval", 1), getattr(wl, "neighbours", 6)) != (1, 6):
+            sim.set_schedule(wl.interval, wl.neighbours)
         self._sims.append(sim)
         return sim
 

@@ -173,6 +173,8 @@ class Workload:
     decay_alpha: float = 1.0
     decay_steps: int = 0
     pool_bytes: Optional[int] = None
+    interval: int = 1                                # update procedure every `interval` steps
+    neighbours: int = 6                              # 6 (faces) or 26
 
     @property
     def nx(self):
