@@ -255,12 +255,14 @@ def run_ours(args, rank, world, local_rank):
 
 def time_to_solution(torch, tcm, W, wl, dev, local_rank):
     """Full 1500-step runs from create to the final field on the device: TCM
-    (update procedure every step, face neighbours), TCM on the Eq. 5 schedule
-    (update every 8 steps, 26 neighbours), and the same kernel over every
-    brick (dense, no update procedure)."""
+    (update procedure every step, face neighbours, Eq. 6 decay), TCM on the
+    Eq. 5 schedule (update every 8 steps, 26 neighbours), TCM with the Eq. 7
+    shut-down (LPF pass 0.25, stop 0.5 of Nyquist), and the same kernel over
+    every brick (dense, no update procedure)."""
     import dataclasses
     runs = [("dense", wl, True), ("tcm", wl, False),
-            ("tcm_eq5_26", dataclasses.replace(wl, interval=0, neighbours=26), False)]
+            ("tcm_eq5_26", dataclasses.replace(wl, interval=0, neighbours=26), False),
+            ("tcm_lpf", dataclasses.replace(wl, lpf=(0.25, 0.5)), False)]
     out = {}
     ref = None
     for name, w, dense in runs:
@@ -291,7 +293,8 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
         "dense_cell_updates": out["dense"]["cell_updates"],
         "max_abs_diff_tcm_vs_dense": out["tcm"]["max_abs_diff_vs_dense"],
         "max_abs_field": out["dense"]["max_abs_field"],
-        "eq5_interval_26_neighbours": out["tcm_eq5_26"]}}
+        "eq5_interval_26_neighbours": out["tcm_eq5_26"],
+        "eq7_lpf_shutdown": out["tcm_lpf"]}}
 
 
 def precision_leg(torch, tcm, W, dev, local_rank):

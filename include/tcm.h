@@ -144,6 +144,23 @@ tcm_status tcm_set_field(tcm_sim *sim, const float *phi_now, const float *phi_pr
  * Default interval 1, neighbours 6.  Only before the first step (TCM_ESTATE
  * after); TCM_EINVAL for interval < 0 or another neighbour count. */
 tcm_status tcm_set_schedule(tcm_sim *sim, int interval, int neighbours);
+/* Frequency-domain shut-down (Eq. 7) instead of the time-domain decay of
+ * Eq. 6: at a run of the update procedure a brick that is not kept is
+ * released at once, and every boxed brick that stays (not claimed by this
+ * run) with such a released brick among its 26 neighbours -- one that held a
+ * non-zero value -- gets both time levels replaced by
+ * Phi~ = F^-1[F(Phi) LPF] evaluated on its 3x3x3-brick block (24^3 nodes;
+ * released, unboxed and outside bricks read zero) zero-padded to 64^3
+ * (spatial oversampling), LPF = H(kx) H(ky) H(kz), H = 1 up to `pass`, 0
+ * from `stop` (fractions of the Nyquist frequency), raised cosine between;
+ * the centre brick of the result is kept (FP64 arithmetic, rounded to the
+ * storage).  All filtered values come from the state before any is
+ * written.  decay_alpha / decay_steps are then unused.  0 < pass < stop <= 1
+ * (TCM_EINVAL otherwise); only before the first step (TCM_ESTATE).  At most
+ * 65536 bricks are filtered per run (beyond that the batch reports
+ * TCM_ENOMEM). */
+tcm_status tcm_set_lpf_shutdown(tcm_sim *sim, double pass, double stop);
+
 /* The schedule in use (interval resolved when 0 was given). */
 tcm_status tcm_schedule(const tcm_sim *sim, int *interval, int *neighbours);
 

@@ -75,6 +75,7 @@ def lib():
             getattr(L, f"orc_tcm_status_{sfx}").argtypes = [_vp]
             getattr(L, f"orc_tcm_set_storage_{sfx}").argtypes = [_vp, C.c_int]
             getattr(L, f"orc_tcm_set_schedule_{sfx}").argtypes = [_vp, C.c_int, C.c_int]
+            getattr(L, f"orc_tcm_set_lpf_{sfx}").argtypes = [_vp, _d, _d]
             getattr(L, f"orc_tcm_storage_scale_{sfx}").argtypes = [_vp]
             getattr(L, f"orc_tcm_storage_scale_{sfx}").restype = _d
             getattr(L, f"orc_tcm_brick_media_{sfx}").argtypes = [_vp, _i64, _vp]
@@ -84,6 +85,12 @@ def lib():
                                   _vp, _vp]
         L.orc_rules_c.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_fft.argtypes = [_vp, _vp, C.c_int, C.c_int]
+        L.orc_fft.restype = None
+        L.orc_lpf_response.argtypes = [C.c_int, C.c_int, _d, _d]
+        L.orc_lpf_response.restype = _d
+        L.orc_lpf_region.argtypes = [_vp, C.c_int, C.c_int, _d, _d]
+        L.orc_lpf_region.restype = None
         for name in ("orc_round_bf16", "orc_round_f16"):
             getattr(L, name).argtypes = [C.c_float]
             getattr(L, name).restype = C.c_float
@@ -175,6 +182,28 @@ def round_storage(v, storage) -> np.ndarray:
     return np.array([fn(float(x)) for x in a.ravel()], dtype=np.float32).reshape(a.shape)
 
 
+def fft(x, sign: int = -1) -> np.ndarray:
+    """The oracle's radix-2 DFT of a complex vector (length a power of two)."""
+    x = np.asarray(x, dtype=np.complex128)
+    re = np.ascontiguousarray(x.real)
+    im = np.ascontiguousarray(x.imag)
+    lib().orc_fft(_ptr(re), _ptr(im), len(x), int(sign))
+    return re + 1j * im
+
+
+def lpf_response(kappa: int, M: int, pass_: float, stop: float) -> float:
+    return float(lib().orc_lpf_response(int(kappa), int(M), float(pass_), float(stop)))
+
+
+def lpf_region(v: np.ndarray, M: int, pass_: float, stop: float) -> np.ndarray:
+    """Eq. 7 on a cubic region (zero-padded to M per axis); returns a copy."""
+    v = np.array(v, dtype=np.float64, order="C", copy=True)
+    L = v.shape[0]
+    assert v.shape == (L, L, L)
+    lib().orc_lpf_region(_ptr(v), L, int(M), float(pass_), float(stop))
+    return v
+
+
 def energy(k: np.ndarray, a: np.ndarray, b: np.ndarray) -> float:
     """Leapfrog discrete energy between phi^{n+1} = a and phi^n = b (FP64 sum)."""
     sfx = _sfx(k.dtype)
@@ -191,7 +220,8 @@ class OracleTCM:
     def __init__(self, shape, media, dx: float, dt: float, brick=(8, 8, 8),
                  thr_mode: int = THR_ABSOLUTE, tau: float = 0.0, decay_alpha: float = 1.0,
                  decay_steps: int = 0, max_slots: int = 0, dense: bool = False,
-                 dtype=np.float32, storage="f32", interval: int = 1, neighbours: int = 6):
+                 dtype=np.float32, storage="f32", interval: int = 1, neighbours: int = 6,
+                 lpf=None):
         self.dtype = np.dtype(dtype)
         self._s = _sfx(dtype)
         self.shape = tuple(int(v) for v in shape)
@@ -226,6 +256,9 @@ class OracleTCM:
                                                                          int(neighbours)) != 0:
             self.close()
             raise ValueError("invalid update schedule")
+        if lpf is not None and self._f("set_lpf")(h, float(lpf[0]), float(lpf[1])) != 0:
+            self.close()
+            raise ValueError("invalid low-pass shut-down")
         self.mx = -(-nx // bx)
         self.my = -(-ny // by)
         self.mz = -(-nz // bz)

@@ -8,6 +8,7 @@
  * The type-generic parts (dense FDTD and TCM) live in tcm_oracle_impl.inc,
  * included once with REAL = float and once with REAL = double.
  */
+#define _GNU_SOURCE
 #include "tcm_oracle.h"
 
 #include <math.h>
@@ -138,6 +139,102 @@ float orc_round_bf16(float v) { return round_to_format(v, 8, -133, 128); }
 /* binary16: 1+10 bits significand, bias 15: smallest subnormal 2^-24, largest
  * finite (2 - 2^-10) * 2^15 = 65504, everything rounding to 2^16 overflows. */
 float orc_round_f16(float v) { return round_to_format(v, 11, -24, 16); }
+
+/* ---- Fourier transform for the frequency-domain shut-down (Eq. 7) -------- */
+/* In-place complex DFT of length n (a power of two) by the radix-2
+ * Cooley-Tukey algorithm: X[k] = sum_j x[j] exp(sign * 2 pi i j k / n), no
+ * scaling.  Input permuted to bit-reversed order, then log2(n) butterfly
+ * passes. */
+void orc_fft(double *re, double *im, int n, int sign)
+{
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double t = re[i]; re[i] = re[j]; re[j] = t;
+            t = im[i]; im[i] = im[j]; im[j] = t;
+        }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        const double ang = sign * 2.0 * M_PI / len;
+        for (int i = 0; i < n; i += len)
+            for (int k = 0; k < len / 2; ++k) {
+                const double wr = cos(ang * k), wi = sin(ang * k);
+                const int a = i + k, b = i + k + len / 2;
+                const double xr = re[b] * wr - im[b] * wi, xi = re[b] * wi + im[b] * wr;
+                re[b] = re[a] - xr;
+                im[b] = im[a] - xi;
+                re[a] += xr;
+                im[a] += xi;
+            }
+    }
+}
+
+/* Low-pass response at DFT index kappa of length M: nu = min(kappa, M -
+ * kappa) / (M/2) in [0, 1] (1 = Nyquist); 1 up to `pass`, 0 from `stop`, a
+ * raised cosine between. */
+double orc_lpf_response(int kappa, int M, double pass, double stop)
+{
+    const int kk = kappa < M - kappa ? kappa : M - kappa;
+    const double nu = (double)kk / (M / 2.0);
+    if (nu <= pass) return 1.0;
+    if (nu >= stop) return 0.0;
+    return 0.5 * (1.0 + cos(M_PI * (nu - pass) / (stop - pass)));
+}
+
+/* Eq. 7 on one region: v (L*L*L doubles, x fastest) is zero-padded to
+ * M*M*M, transformed (3D DFT = 1D transforms along x, y, z), multiplied by
+ * H(kx) H(ky) H(kz), transformed back and scaled by 1/M^3; the real part of
+ * the first L*L*L samples replaces v. */
+void orc_lpf_region(double *v, int L, int M, double pass, double stop)
+{
+    const size_t n3 = (size_t)M * M * M;
+    double *re = (double *)calloc(n3, sizeof(double));
+    double *im = (double *)calloc(n3, sizeof(double));
+    double *lr = (double *)malloc((size_t)M * sizeof(double));
+    double *li = (double *)malloc((size_t)M * sizeof(double));
+    for (int z = 0; z < L; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) re[((size_t)z * M + y) * M + x] = v[((size_t)z * L + y) * L + x];
+    for (int pass_dir = 0; pass_dir < 2; ++pass_dir) {
+        const int sign = pass_dir == 0 ? -1 : 1;
+        for (int axis = 0; axis < 3; ++axis) {
+            const size_t stride = axis == 0 ? 1 : (axis == 1 ? (size_t)M : (size_t)M * M);
+            for (int a = 0; a < M; ++a)
+                for (int b = 0; b < M; ++b) {
+                    size_t base;
+                    if (axis == 0) base = ((size_t)a * M + b) * M;
+                    else if (axis == 1) base = (size_t)a * M * M + b;
+                    else base = (size_t)a * M + b;
+                    for (int k = 0; k < M; ++k) {
+                        lr[k] = re[base + k * stride];
+                        li[k] = im[base + k * stride];
+                    }
+                    orc_fft(lr, li, M, sign);
+                    for (int k = 0; k < M; ++k) {
+                        re[base + k * stride] = lr[k];
+                        im[base + k * stride] = li[k];
+                    }
+                }
+        }
+        if (pass_dir == 0)
+            for (int kz = 0; kz < M; ++kz)
+                for (int ky = 0; ky < M; ++ky)
+                    for (int kx = 0; kx < M; ++kx) {
+                        const double h = orc_lpf_response(kx, M, pass, stop) * orc_lpf_response(ky, M, pass, stop) *
+                                         orc_lpf_response(kz, M, pass, stop);
+                        const size_t i = ((size_t)kz * M + ky) * M + kx;
+                        re[i] *= h;
+                        im[i] *= h;
+                    }
+    }
+    const double inv = 1.0 / (double)n3;
+    for (int z = 0; z < L; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) v[((size_t)z * L + y) * L + x] = re[((size_t)z * M + y) * M + x] * inv;
+    free(re); free(im); free(lr); free(li);
+}
 
 /* ---- type-generic programs ---------------------------------------------- */
 #define REAL float

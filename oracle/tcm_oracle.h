@@ -100,6 +100,18 @@ float orc_round_f16(float v);
 
 enum { ORC_STORAGE_F32 = 0, ORC_STORAGE_BF16 = 1, ORC_STORAGE_F16 = 2 };
 
+/* ---- frequency-domain shut-down (Eq. 7) ---------------------------------- */
+/* Radix-2 complex DFT in place (n a power of two; sign -1 forward, +1
+ * inverse, unscaled). */
+void orc_fft(double *re, double *im, int n, int sign);
+/* Low-pass response at DFT index kappa of an M-point transform: 1 up to
+ * `pass`, 0 from `stop` (fractions of the Nyquist frequency), raised cosine
+ * between. */
+double orc_lpf_response(int kappa, int M, double pass, double stop);
+/* Phi~ = F^-1[F(Phi) LPF] (Eq. 7) on an L^3 region (x fastest), zero-padded
+ * to M^3 (spatial oversampling), LPF = H(kx) H(ky) H(kz); in place. */
+void orc_lpf_region(double *v, int L, int M, double pass, double stop);
+
 /* ---- Triggered Cells Method ---------------------------------------------- */
 typedef struct orc_tcm orc_tcm;
 
@@ -168,6 +180,20 @@ double orc_tcm_storage_scale_f64(const orc_tcm *t);
  * 0 .. interval-1), releasing nothing; with the 26-neighbour set, adding a
  * source boxes its cell's neighbourhood at once.  Returns ORC_EINVAL for
  * interval < 1 or another neighbour count, ORC_ESTATE after the first step. */
+/* Frequency-domain shut-down (Eq. 7) instead of the time-domain decay:
+ * at a run of the update procedure, a cell that is not kept is released at
+ * once (Q), and every boxed cell that stays and has among its 26 neighbours a
+ * cell of Q that held a non-zero value (removing an all-zero cell cuts
+ * nothing) gets both time levels (phi^{n+1}, phi^n) replaced by the centre
+ * cell of orc_lpf_region applied to the 3x3x3-cell block around it (cells of
+ * Q, unboxed cells and nodes outside the domain read zero; region L = 3 cell
+ * edges, padded to M = 64 per axis; results are rounded to the program's
+ * type and storage, and nodes outside the domain stay zero).  All filtered
+ * values come from the state before any is written.  Cells only, 8^3 bricks
+ * assumed for L = 24.  pass/stop as in orc_lpf_response; 0 < pass < stop <= 1.
+ * Before the first step. */
+int orc_tcm_set_lpf_f32(orc_tcm *t, double pass, double stop);
+int orc_tcm_set_lpf_f64(orc_tcm *t, double pass, double stop);
 int orc_tcm_set_schedule_f32(orc_tcm *t, int interval, int neighbours);
 int orc_tcm_set_schedule_f64(orc_tcm *t, int interval, int neighbours);
 int orc_tcm_step_f32(orc_tcm *t, int64_t n);

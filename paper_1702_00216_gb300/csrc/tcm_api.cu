@@ -45,6 +45,7 @@ struct HostSim {
     long long target = -1;   // freeze after this many steps (-1: never)
     double dx = 1, dt = 1;
     float c_max = 0.f;
+    double *lpf_a = nullptr;   // Eq. 7 filter operator (device)
     SimDev dev{};
 };
 
@@ -82,6 +83,7 @@ struct tcm_batch {
     long long launches = 0;
     int list_parity = 0;
     bool dirty_list = false;   // the active list must be rebuilt before the next step
+    int lpf_grid = 0;          // grid of the Eq. 7 kernel (0 until a sim uses it)
 };
 
 namespace {
@@ -361,6 +363,10 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
     if ((st = dalloc(b, &E.newslots, b->n_slots)) != TCM_OK) return fail(st);
     if ((st = dalloc(b, &E.sims, max_sims)) != TCM_OK) return fail(st);
     if ((st = dalloc(b, &E.st, 1)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.claim_step, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.lpf_mark, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.lpf_q, b->n_slots)) != TCM_OK) return fail(st);
+    if ((st = dalloc(b, &E.lpf_aff, b->n_slots)) != TCM_OK) return fail(st);
     E.n_sims = max_sims;
     b->sims.resize(max_sims);
     b->handles.assign(max_sims, nullptr);
@@ -374,6 +380,8 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
         cudaMemsetAsync(E.sim_of_word, 0, b->n_words * sizeof(unsigned short), q) != cudaSuccess ||
         cudaMemsetAsync(E.blocktot, 0, b->grid * sizeof(int), q) != cudaSuccess ||
         cudaMemsetAsync(E.sims, 0, max_sims * sizeof(SimDev), q) != cudaSuccess ||
+        cudaMemsetAsync(E.claim_step, 0xff, b->n_slots * sizeof(int), q) != cudaSuccess ||
+        cudaMemsetAsync(E.lpf_mark, 0, b->n_slots * sizeof(int), q) != cudaSuccess ||
         cudaMemcpyAsync(E.st, &es, sizeof(es), cudaMemcpyHostToDevice, q) != cudaSuccess ||
         launch_iota_desc(E.free_stack, b->n_slots, b->n_slots - 1, q) != cudaSuccess ||
         cudaStreamSynchronize(q) != cudaSuccess)
@@ -746,13 +754,18 @@ tcm_status batch_step_async(tcm_batch *b, long long n)
     TRYS(prime_all(b));
     for (long long i = 0; i < n; ++i) {
         TRYS(ensure_list(b));
-        // Does any simulation run the update procedure after this step?
-        int manage = 0;
-        for (int id = 0; id < b->max_sims && !manage; ++id) {
+        // Does any simulation run the update procedure after this step (and
+        // with the Eq. 7 shut-down)?
+        int manage = 0, lpf = 0;
+        for (int id = 0; id < b->max_sims; ++id) {
             const HostSim &h = b->sims[id];
-            if (h.used && h.live && !h.dense && (h.step + 1) % h.dev.interval == 0) manage = 1;
+            if (h.used && h.live && !h.dense && (h.step + 1) % h.dev.interval == 0) {
+                manage = 1;
+                lpf |= h.dev.lpf;
+            }
         }
         cudaError_t e = launch_step(b->E, b->grid, manage, b->stream);
+        if (e == cudaSuccess && lpf) e = launch_lpf(b->E, b->lpf_grid, b->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return poison(b, TCM_EDEVICE);
@@ -780,6 +793,7 @@ tcm_status sim_release(tcm_batch *b, int id)
     }
     TRY(cudaStreamSynchronize(b->stream));
     if (h.kslabs) cudaFree(h.kslabs);
+    if (h.lpf_a) cudaFree(h.lpf_a);
     range_free(b, h.brick_base, h.range_len);
     // the released entry stops stepping; clear it on the device
     SimDev zero{};
@@ -900,6 +914,51 @@ tcm_status tcm_set_schedule(tcm_sim *s, int interval, int neighbours)
     }
     h->dev.interval = interval;
     h->dev.neighbours = neighbours;
+    return TCM_OK;
+}
+
+tcm_status tcm_set_lpf_shutdown(tcm_sim *s, double pass, double stop)
+{
+    HostSim *h = sim_of(s);
+    if (!h || !(pass > 0) || !(stop > pass) || !(stop <= 1)) return TCM_EINVAL;
+    if (h->primed) return TCM_ESTATE;
+    tcm_batch *b = s->b;
+    DeviceGuard g(b->device);
+    if (!b->lpf_grid) {
+        b->lpf_grid = lpf_grid_size(b->device);
+        if (b->lpf_grid <= 0) return TCM_EDEVICE;
+    }
+    if (!b->E.lpf_out) {
+        const int cap = (int)std::min<long long>(b->n_slots, 65536);
+        TRYS(dalloc(b, &b->E.lpf_out, (size_t)cap * 2 * BVOL));
+        b->E.lpf_cap = cap;
+    }
+    // Centre rows of the 1-D operator P^T F^-1 diag(H) F P (zero-padding P of
+    // LPF_L nodes to LPF_M, DFT F): A[i][j] = (1/M) sum_k H(k) cos(2 pi k
+    // (i + C - j) / M) -- real because H(k) = H(M - k).
+    std::vector<double> A((size_t)LPF_C * LPF_L);
+    for (int i = 0; i < LPF_C; ++i)
+        for (int j = 0; j < LPF_L; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < LPF_M; ++k) {
+                const int kk = std::min(k, LPF_M - k);
+                const double nu = kk / (LPF_M / 2.0);
+                const double hk = nu <= pass ? 1.0 : nu >= stop ? 0.0 : 0.5 * (1.0 + std::cos(M_PI * (nu - pass) / (stop - pass)));
+                acc += hk * std::cos(2.0 * M_PI * (double)k * (double)(i + LPF_C - j) / LPF_M);
+            }
+            A[(size_t)i * LPF_L + j] = acc / LPF_M;
+        }
+    if (!h->lpf_a) {
+        if (cudaMalloc(&h->lpf_a, A.size() * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return TCM_ENOMEM;
+        }
+    }
+    TRY(cudaMemcpyAsync(h->lpf_a, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
+    h->dev.lpf = 1;
+    h->dev.lpf_a = h->lpf_a;
+    TRYS(upload_sim_header(b, s->id));
     return TCM_OK;
 }
 
@@ -1237,8 +1296,10 @@ void tcm_batch_destroy(tcm_batch *b)
     if (!b) return;
     DeviceGuard g(b->device);
     cudaStreamSynchronize(b->stream);
-    for (auto &h : b->sims)
+    for (auto &h : b->sims) {
         if (h.kslabs) cudaFree(h.kslabs);
+        if (h.lpf_a) cudaFree(h.lpf_a);
+    }
     for (tcm_sim *s : b->handles) delete s;
     for (void *p : b->allocs) cudaFree(p);
     if (b->d_src) cudaFree(b->d_src);

@@ -87,7 +87,8 @@ struct SimDev {
     float inv_scale;
     int interval;          // the update procedure runs after every interval-th step
     int neighbours;        // 6: activation across hot faces; 26: all neighbours of a hot cell
-    int pad1;
+    int lpf;               // 1: frequency-domain shut-down (Eq. 7) instead of the decay
+    const double *lpf_a;   // LPF_C x LPF_L centre rows of the 1-D filter operator (FP64)
     // mutable (device-owned)
     long long step;        // n of phi^n
     unsigned gmax[2];      // max |phi^{n+1}| of step n in gmax[n & 1] (float bits)
@@ -121,8 +122,16 @@ struct EngineState {
     unsigned long long t_start, t_p1, t_p2;   // globaltimer stamps of the current launch
     unsigned long long phase_ns[3];           // cumulative: time stepping, update, compaction
     int list_age;          // launches since the active list was built (phase of its nh)
-    int pad_age;
+    int n_lpf_q;           // bricks released this update that held values (Eq. 7 sources)
+    int n_lpf_aff;         // boxed bricks the Eq. 7 filter rewrites this update
+    int pad_lpf;
 };
+
+// Eq. 7 region: the 3x3x3-brick block around a brick (LPF_L nodes per axis),
+// zero-padded to LPF_M per axis; the filter keeps the centre LPF_C nodes.
+constexpr int LPF_C = 8;
+constexpr int LPF_L = 3 * LPF_C;
+constexpr int LPF_M = 64;
 
 struct Engine {
     void *phi;             // pool: 2 * BVOL elements of `storage` per box
@@ -148,6 +157,13 @@ struct Engine {
     int n_src;
     const float *wave;
     EngineState *st;
+    // Eq. 7 shut-down (per slot: claim step, mark; lists; filtered values)
+    int *claim_step;       // step index of the update that claimed the box
+    int *lpf_mark;         // 1 while the box is on the affected list
+    long long *lpf_q;      // released bricks (global ids) that held values
+    long long *lpf_aff;    // affected bricks (global ids)
+    float *lpf_out;        // filtered values, 2 * BVOL per affected brick
+    int lpf_cap;           // capacity of lpf_out in bricks
 };
 
 struct MediaDev {
@@ -208,6 +224,9 @@ cudaError_t launch_scatter_field(const Engine &e, const float *packed, const lon
 // manage = 0: no simulation runs the update procedure after this step (time
 // stepping only; the active list is kept).
 cudaError_t launch_step(const Engine &e, int grid, int manage, cudaStream_t s);
+// Eq. 7 filtering after a launch whose update released bricks of LPF sims.
+cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s);
+int lpf_grid_size(int device);
 int step_grid_size(int device);
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,

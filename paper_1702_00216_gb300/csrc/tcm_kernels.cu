@@ -562,6 +562,7 @@ __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_l
             continue;
         }
         const int ns = __ldcg(E.free_stack + idx);
+        E.claim_step[ns] = (int)__ldcg(&S->step);
         SlotMeta m;
         m.brick = b_local[i];
         m.kslab = E.kslab_of_brick[g];
@@ -738,6 +739,7 @@ struct SimCache {
     int sim = -1;
     bool dense = false;
     bool manage = false;   // this sim runs the update procedure after this step
+    bool lpf = false;
     int interval = 1;
     int neighbours = 6;
     long long step = 0;
@@ -754,6 +756,7 @@ __device__ __forceinline__ void sim_cache(const Engine &E, int sim, SimCache &c)
     c.interval = __ldg(&S->interval);
     c.neighbours = __ldg(&S->neighbours);
     c.manage = (c.step + 1) % c.interval == 0;
+    c.lpf = __ldg(&S->lpf) != 0;
     const double G = (double)__uint_as_float(__ldcg(&S->gmax[c.step & 1]));
     c.thr = __ldg(&S->thr_mode) == 1 ? __ldg(&S->tau) * G : __ldg(&S->tau);
 }
@@ -777,8 +780,8 @@ __device__ __forceinline__ void keep_or_release(const Engine &E, const WorkItem 
 // brick is triggered when its own maximum is above the level or a source
 // feeds it during the steps the update covers; it stays when it or any of
 // its 26 neighbours is triggered; a triggered brick boxes all 26 neighbours.
-__device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool above, double thr, int interval,
-                                       int sim, SimDev *S)
+__device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool above, bool nonzero, double thr,
+                                       int interval, bool lpf, int sim, SimDev *S)
 {
     const int b = w.brick;
     const int mx = __ldg(&S->mx), my = __ldg(&S->my), mz = __ldg(&S->mz);
@@ -828,6 +831,9 @@ __device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool 
     if (hot) {
         sd = 0;
         keep = true;
+    } else if (lpf) {
+        keep = false;
+        if (nonzero) E.lpf_q[agg_add(&E.st->n_lpf_q, 1)] = g0 + b;
     } else if (sd > 0) {
         sd = sd > (unsigned)interval ? sd - (unsigned)interval : 0u;
         keep = sd > 0;
@@ -860,7 +866,7 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
     const double thr = c.thr;
     const int b = w.brick;
     if (c.neighbours == 26) {
-        p2_item26(E, w, (double)r1.z > thr, thr, c.interval, sim, S);
+        p2_item26(E, w, (double)r1.z > thr, r1.z > 0.f, thr, c.interval, c.lpf, sim, S);
         return;
     }
     const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
@@ -882,6 +888,9 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
     if (hot) {
         sd = 0;
         keep = true;
+    } else if (c.lpf) {
+        keep = false;   // Eq. 7: released now, its neighbours filtered after the launch
+        if (r1.z > 0.f) E.lpf_q[agg_add(&E.st->n_lpf_q, 1)] = __ldg(&S->brick_base) + b;
     } else if (sd > 0) {
         // the count is in time steps; `interval` of them passed
         sd = sd > (unsigned)c.interval ? sd - (unsigned)c.interval : 0u;
@@ -944,6 +953,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int manage)
         st->free_top = ft;
         st->n_retired = 0;
         st->n_new = 0;
+        st->n_lpf_q = 0;
+        st->n_lpf_aff = 0;
     }
 
     // ---- P1: time stepping of every active brick -------------------------
@@ -1240,6 +1251,7 @@ __global__ void k_admit(Engine E, int sim, const long long *bricks, long long n)
             } else {
                 slot = E.free_stack[idx];
                 E.slot_of_brick[g] = slot;
+                E.claim_step[slot] = -1;
                 SlotMeta m;
                 m.brick = b;
                 m.kslab = E.kslab_of_brick[g];
@@ -1472,6 +1484,138 @@ int step_grid_size(int device)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_step<ST_F16>, BLOCK, 0) != cudaSuccess) return 0;
     per_sm = min(a, min(b, c));
     return sms * per_sm;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 7 frequency-domain shut-down, after an update that released bricks
+// holding values (lpf_q): (A) every boxed 26-neighbour of such a brick that
+// was not claimed by this update is listed once; (B) for each listed brick,
+// its 3x3x3-brick block (both halves; released, unboxed and outside bricks
+// read zero) goes through the separable filter operator A (x, then y, then
+// z, FP64 in a fixed order) and the centre brick is kept in lpf_out; (C) the
+// filtered values replace the bricks' halves (nodes outside the domain stay
+// zero).  Every filtered value comes from the state before (C).
+// ---------------------------------------------------------------------------
+constexpr size_t LPF_SMEM = (size_t)2 * LPF_L * LPF_L * LPF_L * sizeof(float) +
+                            (size_t)LPF_L * LPF_L * LPF_C * sizeof(double) +
+                            (size_t)LPF_L * LPF_C * LPF_C * sizeof(double) + (size_t)LPF_C * LPF_L * sizeof(double);
+
+__device__ __forceinline__ long long lpf_neighbour(const SimDev *S, long long base, int b, int dx, int dy, int dz)
+{
+    const int mx = S->mx, my = S->my, mz = S->mz;
+    const int ax = b % mx + dx, ay = (b / mx) % my + dy, az = b / (mx * my) + dz;
+    if (ax < 0 || ay < 0 || az < 0 || ax >= mx || ay >= my || az >= mz) return -1;
+    return base + ((long long)az * my + ay) * mx + ax;
+}
+
+__global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    EngineState *st = E.st;
+    const int nq = __ldcg(&st->n_lpf_q);
+    if (nq == 0) return;   // the same value for every block: nobody waits
+    const int gtid = blockIdx.x * BLOCK + threadIdx.x, nthr = gridDim.x * BLOCK;
+    // (A) the affected bricks
+    for (long long i = gtid; i < (long long)nq * 26; i += nthr) {
+        const long long q = E.lpf_q[i / 26];
+        const int k = (int)(i % 26);
+        const int kk = k < 13 ? k : k + 1;   // skip the centre of the 3x3x3 block
+        const SimDev *S = E.sims + E.sim_of_word[q >> 5];
+        const long long base = S->brick_base;
+        const long long g = lpf_neighbour(S, base, (int)(q - base), kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1);
+        if (g < 0) continue;
+        const int slot = __ldcg(E.slot_of_brick + g);
+        if (slot < 0) continue;
+        if (__ldcg(E.claim_step + slot) == (int)(__ldcg(&S->step) - 1)) continue;   // claimed by this update
+        if (atomicCAS(E.lpf_mark + slot, 0, 1) != 0) continue;
+        const int idx = atomicAdd(&st->n_lpf_aff, 1);
+        if (idx < E.lpf_cap) E.lpf_aff[idx] = g;
+        else atomicOr(&st->err, ERR_NOMEM);
+    }
+    if (!grid_barrier(st)) return;
+    const int naff = min(__ldcg(&st->n_lpf_aff), E.lpf_cap);
+    // (B) one block per affected brick
+    float *R = reinterpret_cast<float *>(smem);                         // [2][L][L][L]
+    double *T1 = reinterpret_cast<double *>(R + 2 * LPF_L * LPF_L * LPF_L);   // [L][L][C]
+    double *T2 = T1 + LPF_L * LPF_L * LPF_C;                               // [L][C][C]
+    double *A = T2 + LPF_L * LPF_C * LPF_C;                                // [C][L]
+    for (int c = blockIdx.x; c < naff; c += gridDim.x) {
+        const long long g = E.lpf_aff[c];
+        const SimDev *S = E.sims + E.sim_of_word[g >> 5];
+        const long long base = S->brick_base;
+        const int b = (int)(g - base);
+        const float sc = S->scale;
+        for (int i = threadIdx.x; i < LPF_C * LPF_L; i += BLOCK) A[i] = S->lpf_a[i];
+        for (int e = threadIdx.x; e < 27 * 2 * BVOL; e += BLOCK) {
+            const int nb = e / (2 * BVOL), h = (e / BVOL) & 1, loc = e % BVOL;
+            const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+            const long long gn = lpf_neighbour(S, base, b, dx, dy, dz);
+            const int slot = gn >= 0 ? __ldcg(E.slot_of_brick + gn) : -1;
+            const float v = slot >= 0 ? load_phys(E, slot, h, loc, sc) : 0.f;
+            const int lx = loc % BX, ly = (loc / BX) % BY, lz = loc / (BX * BY);
+            R[((h * LPF_L + (dz + 1) * LPF_C + lz) * LPF_L + (dy + 1) * LPF_C + ly) * LPF_L + (dx + 1) * LPF_C + lx] = v;
+        }
+        __syncthreads();
+        for (int h = 0; h < 2; ++h) {
+            for (int e = threadIdx.x; e < LPF_L * LPF_L * LPF_C; e += BLOCK) {   // along x
+                const int i = e % LPF_C, zy = e / LPF_C;
+                const float *row = R + ((size_t)h * LPF_L * LPF_L + zy) * LPF_L;
+                double acc = 0.0;
+                for (int j = 0; j < LPF_L; ++j) acc = __dadd_rn(acc, __dmul_rn(A[i * LPF_L + j], (double)row[j]));
+                T1[e] = acc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < LPF_L * LPF_C * LPF_C; e += BLOCK) {   // along y
+                const int x = e % LPF_C, i = (e / LPF_C) % LPF_C, z = e / (LPF_C * LPF_C);
+                double acc = 0.0;
+                for (int j = 0; j < LPF_L; ++j)
+                    acc = __dadd_rn(acc, __dmul_rn(A[i * LPF_L + j], T1[(z * LPF_L + j) * LPF_C + x]));
+                T2[e] = acc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < BVOL; e += BLOCK) {                     // along z
+                const int x = e % LPF_C, y = (e / LPF_C) % LPF_C, i = e / (LPF_C * LPF_C);
+                double acc = 0.0;
+                for (int j = 0; j < LPF_L; ++j)
+                    acc = __dadd_rn(acc, __dmul_rn(A[i * LPF_L + j], T2[(j * LPF_C + y) * LPF_C + x]));
+                E.lpf_out[(size_t)c * 2 * BVOL + h * BVOL + e] = (float)acc;
+            }
+            __syncthreads();
+        }
+    }
+    if (!grid_barrier(st)) return;
+    // (C) write back
+    for (long long i = gtid; i < (long long)naff * 2 * BVOL; i += nthr) {
+        const int c = (int)(i / (2 * BVOL)), e = (int)(i % (2 * BVOL));
+        const int h = e / BVOL, loc = e % BVOL;
+        const long long g = E.lpf_aff[c];
+        const SimDev *S = E.sims + E.sim_of_word[g >> 5];
+        const int b = (int)(g - S->brick_base);
+        const int slot = __ldcg(E.slot_of_brick + g);
+        const int mx = S->mx, my = S->my;
+        const int x = (b % mx) * BX + loc % BX, y = ((b / mx) % my) * BY + (loc / BX) % BY,
+                  z = (b / (mx * my)) * BZ + loc / (BX * BY);
+        const bool in = x < S->nx && y < S->ny && z < S->nz;
+        store_phys(E, slot, h, loc, in ? E.lpf_out[i] : 0.f, S->inv_scale);
+        if (e == 0) E.lpf_mark[slot] = 0;
+    }
+}
+
+int lpf_grid_size(int device)
+{
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_lpf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LPF_SMEM) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpf, BLOCK, LPF_SMEM) != cudaSuccess) return 0;
+    return sms * per_sm;
+}
+
+cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s)
+{
+    Engine copy = e;
+    void *args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void *)k_lpf, dim3(grid), dim3(BLOCK), args, LPF_SMEM, s);
 }
 
 cudaError_t launch_step(const Engine &e, int grid, int manage, cudaStream_t s)

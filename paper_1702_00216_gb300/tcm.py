@@ -28,7 +28,7 @@ def storage_code(storage) -> int:
     return STORAGES[storage] if isinstance(storage, str) else int(storage)
 
 EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "tcm_step",
-           "tcm_step_async", "tcm_sync", "tcm_set_schedule", "tcm_schedule", "tcm_read_field", "tcm_read_field_device",
+           "tcm_step_async", "tcm_sync", "tcm_set_schedule", "tcm_schedule", "tcm_set_lpf_shutdown", "tcm_read_field", "tcm_read_field_device",
            "tcm_active_count", "tcm_active_bricks", "tcm_updates", "tcm_energy",
            "tcm_energy_noalloc",
            "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_step_index",
@@ -88,6 +88,7 @@ def lib():
             "tcm_set_field": ([_vp, _vp, _vp], C.c_int),
             "tcm_set_schedule": ([_vp, C.c_int, C.c_int], C.c_int),
             "tcm_schedule": ([_vp, _vp, _vp], C.c_int),
+            "tcm_set_lpf_shutdown": ([_vp, C.c_double, C.c_double], C.c_int),
             "tcm_step": ([_vp, _i64], C.c_int),
             "tcm_step_async": ([_vp, _i64], C.c_int),
             "tcm_sync": ([_vp], C.c_int),
@@ -195,6 +196,10 @@ def tcm_set_field(h, now, prev):
 
 def tcm_set_schedule(h, interval=1, neighbours=6):
     _chk(lib().tcm_set_schedule(h, int(interval), int(neighbours)), "tcm_set_schedule")
+
+
+def tcm_set_lpf_shutdown(h, pass_, stop):
+    _chk(lib().tcm_set_lpf_shutdown(h, float(pass_), float(stop)), "tcm_set_lpf_shutdown")
 
 
 def tcm_schedule(h):
@@ -414,6 +419,8 @@ class Sim:
             s.add_source(x, y, z, np.asarray(w, dtype=np.float32))
         if (wl.interval, wl.neighbours) != (1, 6):
             s.set_schedule(wl.interval, wl.neighbours)
+        if wl.lpf is not None:
+            s.set_lpf_shutdown(*wl.lpf)
         return s
 
     @property
@@ -431,6 +438,9 @@ class Sim:
 
     def schedule(self):
         return tcm_schedule(self._h)
+
+    def set_lpf_shutdown(self, pass_, stop):
+        tcm_set_lpf_shutdown(self._h, pass_, stop)
 
     def step(self, n=1):
         tcm_step(self._h, n)
@@ -534,6 +544,8 @@ class Batch:
             sim.add_source(x, y, z, np.asarray(w, dtype=np.float32))
         if (getattr(wl, "interval", 1), getattr(wl, "neighbours", 6)) != (1, 6):
             sim.set_schedule(wl.interval, wl.neighbours)
+        if getattr(wl, "lpf", None) is not None:
+            sim.set_lpf_shutdown(*wl.lpf)
         self._sims.append(sim)
         return sim
 

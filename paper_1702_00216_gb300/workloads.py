@@ -175,6 +175,7 @@ class Workload:
     pool_bytes: Optional[int] = None
     interval: int = 1                                # update procedure every `interval` steps
     neighbours: int = 6                              # 6 (faces) or 26
+    lpf: Optional[Tuple[float, float]] = None        # Eq. 7 shut-down (pass, stop), else Eq. 6
 
     @property
     def nx(self):

@@ -1,0 +1,124 @@
+"""Frequency-domain shut-down (Eq. 7) on the GPU against the oracle: the
+affected set, the filtered values (FP64 filter, rounded to the storage) and
+the active sets, step by step; at threshold 0 equal to the dense grid."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00216_gb300 import tcm
+from paper_1702_00216_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+F32 = np.float32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def wave(shape=(34, 29, 41), tau=2e-3, mode=1, interval=1, neighbours=6, lpf=(0.25, 0.5), steps=100):
+    m = W.random_dense_media(shape, 31, 1.0, 1.8)
+    dt = 0.5 / m.c_max()
+    w = W.ricker(1 / 7, dt)
+    nz, ny, nx = shape
+    return W.Workload("lpf", shape, m, 1.0, dt, [(nx // 3, ny // 2, nz // 2, w)], steps, thr_mode=mode,
+                      tau=tau, interval=interval, neighbours=neighbours, lpf=lpf)
+
+
+def oracle_of(wl, storage="f32"):
+    o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, thr_mode=wl.thr_mode, tau=wl.tau,
+                         interval=wl.interval, neighbours=wl.neighbours, lpf=wl.lpf, storage=storage)
+    for x, y, z, w in wl.sources:
+        o.add_source(x, y, z, np.asarray(w, F32))
+    return o
+
+
+def close(a, b):
+    """Equal up to the rounding of the FP64 filter to binary32 (the oracle
+    filters with its FFT, the GPU with the separable operator)."""
+    scale = max(float(np.abs(b).max()), 1e-30)
+    return float(np.abs(a.astype(np.float64) - b).max()) <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("interval,neighbours", [(1, 6), (3, 26)])
+def test_lpf_threshold0_equals_dense(interval, neighbours):
+    wl = wave(tau=0.0, mode=0, interval=interval, neighbours=neighbours, steps=70)
+    s = tcm.Sim.from_workload(wl)
+    s.step(70)
+    d = tcm.Sim.from_workload(wave(tau=0.0, mode=0, lpf=None), dense=True)
+    d.step(70)
+    assert np.array_equal(s.read_field(0), d.read_field(0))
+    s.close()
+    d.close()
+
+
+@pytest.mark.parametrize("interval,neighbours,mode,tau", [(1, 6, 1, 2e-3), (2, 26, 0, 1e-3)])
+def test_lpf_matches_oracle(interval, neighbours, mode, tau):
+    wl = wave(tau=tau, mode=mode, interval=interval, neighbours=neighbours)
+    s = tcm.Sim.from_workload(wl)
+    o = oracle_of(wl)
+    exact = 0
+    for chunk in (10, 20, 30, 40):
+        s.step(chunk)
+        o.step(chunk)
+        a, b = s.read_field(0), o.read_field(0)
+        assert close(a, b) and close(s.read_field(1), o.read_field(1))
+        assert np.array_equal(s.active_bricks(), o.active_bricks())
+        exact += int(np.array_equal(a, b))
+    assert s.updates == o.updates
+    # the FP64 results agree far below binary32's resolution: the rounded
+    # values are the same
+    assert exact == 4
+    s.close()
+
+
+def test_lpf_worked_release_matches_oracle():
+    shape = (24, 24, 24)
+    rng = np.random.default_rng(11)
+    now = np.zeros(shape, F32)
+    now[8:16, 8:16, 8:16] = rng.uniform(0.5, 1.0, (8, 8, 8)).astype(F32)
+    now[0:8, 0:8, 0:8] = rng.uniform(-0.05, 0.05, (8, 8, 8)).astype(F32)
+    prev = (now * F32(0.9)).astype(F32)
+    s = tcm.Sim(shape, W.homogeneous(1.0), 1.0, 0.5, threshold=0.2)
+    s.set_lpf_shutdown(0.25, 0.5)
+    s.set_field(now, prev)
+    o = oracle.OracleTCM(shape, W.homogeneous(1.0), 1.0, 0.5, tau=0.2, lpf=(0.25, 0.5))
+    o.set_field(now, prev)
+    for _ in range(3):
+        s.step(1)
+        o.step(1)
+        assert np.array_equal(s.active_bricks(), o.active_bricks())
+        assert close(s.read_field(0), o.read_field(0)) and close(s.read_field(1), o.read_field(1))
+    s.close()
+
+
+def test_lpf_bf16_storage_matches_oracle():
+    wl = wave(tau=2e-3, mode=1, steps=60)
+    s = tcm.Sim.from_workload(wl, storage="bf16")
+    o = oracle_of(wl, storage="bf16")
+    s.step(60)
+    o.step(60)
+    assert np.array_equal(s.active_bricks(), o.active_bricks())
+    a, b = s.read_field(0), o.read_field(0)
+    # a filtered value may round to the other neighbour of a bf16 tie region
+    assert float(np.abs(a.astype(np.float64) - b).max()) <= 2 ** -7 * float(np.abs(b).max())
+    s.close()
+
+
+def test_lpf_sim_in_a_batch_equals_solo():
+    wls = [wave(tau=2e-3, mode=1), wave(shape=(30, 30, 30), tau=1e-3, mode=1, lpf=None)]
+    b = tcm.Batch(pool_bytes=20000 * tcm.tcm_slot_bytes(), max_bricks=30000, max_sims=4)
+    sims = [b.add(wl) for wl in wls]
+    b.step(80)
+    for wl, sim in zip(wls, sims):
+        s = tcm.Sim.from_workload(wl)
+        s.step(80)
+        assert np.array_equal(sim.read_field(0), s.read_field(0))
+        assert np.array_equal(sim.active_bricks(), s.active_bricks())
+        s.close()
+    b.close()
