@@ -764,7 +764,7 @@ tcm_status batch_step_async(tcm_batch *b, long long n)
                 lpf |= h.dev.lpf;
             }
         }
-        cudaError_t e = launch_step(b->E, b->grid, manage, b->stream);
+        cudaError_t e = launch_step(b->E, b->grid, b->list_parity, manage, b->stream);
         if (e == cudaSuccess && lpf) e = launch_lpf(b->E, b->lpf_grid, b->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();

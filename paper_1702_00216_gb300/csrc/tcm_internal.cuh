@@ -61,13 +61,13 @@ struct __align__(16) SlotMeta {
 struct __align__(16) WorkItem {
     int slot;
     int brick;
-    int kslab;
-    float kscal;
+    unsigned long long kp;   // bulked: address of the brick's k values; homogenic: KP_SCALAR | k bits
     unsigned flags;
     int nb[6];       // boxes of the face neighbours x-, x+, y-, y+, z-, z+ (-1 none, -3 outside)
     int nh;          // field half holding phi^n for the step that processes this item
 };
 static_assert(sizeof(WorkItem) == 48, "work item layout");
+constexpr unsigned long long KP_SCALAR = 1ull << 63;
 
 struct SimDev {
     // immutable after create
@@ -114,8 +114,8 @@ struct EngineState {
     int list_parity;       // which list holds the current active boxes
     int n_active[2];
     unsigned err;
-    unsigned bar_count;
-    unsigned bar_gen;
+    unsigned long long bar_count;      // step kernel's grid barrier: arrivals so far (only grows)
+    unsigned long long bar_count_lpf;  // the same for the Eq. 7 kernel
     unsigned p3_done;      // blocks finished with the compaction phase this launch
     unsigned long long updates;   // cumulative node updates
     unsigned long long launches;
@@ -223,7 +223,7 @@ cudaError_t launch_scatter_field(const Engine &e, const float *packed, const lon
                                  int now_half, cudaStream_t s);
 // manage = 0: no simulation runs the update procedure after this step (time
 // stepping only; the active list is kept).
-cudaError_t launch_step(const Engine &e, int grid, int manage, cudaStream_t s);
+cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaStream_t s);
 // Eq. 7 filtering after a launch whose update released bricks of LPF sims.
 cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s);
 int lpf_grid_size(int device);

@@ -57,34 +57,36 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Device-wide barrier for a cooperative launch.  The wait is bounded: after
-// BARRIER_TIMEOUT_NS the block records ERR_TIMEOUT and returns false, and the
-// caller leaves the kernel (the others then time out at their next barrier).
-__device__ bool grid_barrier(EngineState *st)
+// Device-wide barrier for a cooperative launch: one arrival per block on a
+// counter that only grows (the blocks of a launch arrive gridDim.x times per
+// barrier, so the barrier ends when the counter reaches the next multiple of
+// gridDim.x); thread 0 arrives with an acquire-release atomic after the
+// block's __syncthreads and waits with acquire loads, then the block
+// synchronises again.  The wait is bounded: after BARRIER_TIMEOUT_NS the
+// block records ERR_TIMEOUT and returns false, and the caller leaves the
+// kernel (the others then time out at their next barrier).
+__device__ bool grid_barrier(EngineState *st, unsigned long long *ctr)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = ld_acquire(&st->bar_gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            st_release(&st->bar_gen, gen + 1);
-        } else {
+        unsigned long long old;
+        asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], 1;" : "=l"(old) : "l"(ctr) : "memory");
+        const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
+        unsigned long long cur;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(ctr) : "memory");
+        if (cur < target) {
             const unsigned long long t0 = globaltimer();
-            while (ld_acquire(&st->bar_gen) == gen) {
-                __nanosleep(128);
+            do {
                 if (globaltimer() - t0 > BARRIER_TIMEOUT_NS) {
                     atomicOr(&st->err, ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
-            }
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(ctr) : "memory");
+            } while (cur < target);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -162,8 +164,7 @@ __device__ __forceinline__ WorkItem load_item(const WorkItem *L, int i)
     WorkItem w;
     w.slot = a.x;
     w.brick = a.y;
-    w.kslab = a.z;
-    w.kscal = __int_as_float(a.w);
+    w.kp = ((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.z;
     w.flags = (unsigned)b.x;
     w.nb[0] = b.y;
     w.nb[1] = b.z;
@@ -342,15 +343,14 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), sc);
 #pragma unroll
         for (int z = 0; z < BZ; ++z) M[z] = F::ld_stream(prv + 4 * (z * TPB + t), sc);
-        if (w.kslab >= 0) {
-            const float *kbase = reinterpret_cast<const float *>(
-                __ldg(reinterpret_cast<const unsigned long long *>(&S->kslabs)));
-            const float4 *k4 = reinterpret_cast<const float4 *>(kbase + (size_t)w.kslab * BVOL);
+        if (!(w.kp & KP_SCALAR)) {
+            const float4 *k4 = reinterpret_cast<const float4 *>(w.kp);
 #pragma unroll
             for (int z = 0; z < BZ; ++z) K[z] = __ldg(k4 + z * TPB + t);
         } else {
+            const float ks = __uint_as_float((unsigned)w.kp);
 #pragma unroll
-            for (int z = 0; z < BZ; ++z) K[z] = make_float4(w.kscal, w.kscal, w.kscal, w.kscal);
+            for (int z = 0; z < BZ; ++z) K[z] = make_float4(ks, ks, ks, ks);
         }
         if (w.nb[4] >= 0) Zm = F::ld(half_ptr<ST>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), sc);
         if (w.nb[5] >= 0) Zp = F::ld(half_ptr<ST>(E, w.nb[5], nh) + 4 * t, sc);
@@ -624,86 +624,113 @@ __device__ long long block_sum(long long v)
     return r;
 }
 
-// Work item of the boxed global brick g (state after the update procedure).
-// The sim is found from g (brick ranges), so the box, its metadata and the
-// six neighbour lookups are independent loads.
-__device__ __forceinline__ void build_item(const Engine &E, long long g, WorkItem *out, int step_ahead,
-                                           int &c_sim, long long &c_step)
+// Per-thread copy of one sim's geometry for building work items.
+struct ItemSim {
+    int sim = -1;
+    int mx = 1, my = 1, mz = 0;
+    long long bb = 0, step = 0;
+    unsigned long long kslabs = 0;
+};
+
+__device__ __forceinline__ void item_sim(const Engine &E, int si, ItemSim &c)
 {
-    const int si = __ldg(E.sim_of_word + (g >> 5));
+    if (si == c.sim) return;
     const SimDev *S = E.sims + si;
-    if (si != c_sim) {
-        c_sim = si;
-        c_step = __ldcg(&S->step);
-    }
-    const int mx = max(__ldg(&S->mx), 1), my = max(__ldg(&S->my), 1), mz = __ldg(&S->mz);
-    const long long bb = __ldg(&S->brick_base);
-    const int b = (int)(g - bb);
-    const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
-    // a brick outside its sim's grid (never listed) gets no box
-    const int slot = (b >= 0 && cz < mz) ? __ldcg(E.slot_of_brick + g) : -1;
-    const int kslab = __ldg(E.kslab_of_brick + g);
-    const float kscal = __ldg(E.kscal + g);
-    const unsigned sd = __ldcg(E.sd_of_brick + g);
-    int nb[6];
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
-        const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
-        const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
-        nb[f] = (ax >= 0 && ay >= 0 && az >= 0 && ax < mx && ay < my && az < mz)
-                    ? __ldcg(E.slot_of_brick + bb + ((long long)az * my + ay) * mx + ax)
-                    : -3;
-    }
-    const unsigned flags = ((unsigned)si << 16) | sd;   // sd word carries the has-source bit
-    // The item is processed by the next launch, which steps from phi^{n+1}.
-    const int nh = (int)((c_step + step_ahead) & 1);
-    int4 *p = reinterpret_cast<int4 *>(out);
-    p[0] = make_int4(slot, b, kslab, __float_as_int(kscal));
-    p[1] = make_int4((int)flags, nb[0], nb[1], nb[2]);
-    p[2] = make_int4(nb[3], nb[4], nb[5], nh);
+    c.sim = si;
+    c.step = __ldcg(&S->step);
+    c.mx = max(__ldg(&S->mx), 1);
+    c.my = max(__ldg(&S->my), 1);
+    c.mz = __ldg(&S->mz);
+    c.bb = __ldg(&S->brick_base);
+    c.kslabs = __ldg(reinterpret_cast<const unsigned long long *>(&S->kslabs));
 }
 
-// Two work items at once (independent loads interleaved); g2 < 0: one.
-__device__ __forceinline__ void build_item2(const Engine &E, long long g1, WorkItem *o1, long long g2, WorkItem *o2,
-                                            int step_ahead, int &c_sim, long long &c_step)
+// Work items of up to IB bricks g[0..n) (global ids) at once: every load of
+// all of them is issued before any is used.  An item holds the brick's box,
+// the boxes of its six face neighbours, its coefficient address (or scalar
+// k), its sim and shut-down word, and the half that holds phi^n when the
+// next launch steps it.
+constexpr int IB = 4;
+
+__device__ __forceinline__ void build_items(const Engine &E, const long long (&g)[IB], int n, WorkItem *const (&out)[IB],
+                                            int step_ahead, ItemSim &c)
 {
-    if (g2 < 0) {
-        build_item(E, g1, o1, step_ahead, c_sim, c_step);
-        return;
+    int si[IB];
+#pragma unroll
+    for (int k = 0; k < IB; ++k) si[k] = k < n ? (int)__ldg(E.sim_of_word + (g[k] >> 5)) : 0;
+    int b[IB], slot[IB], kslab[IB], nb[IB][6];
+    float kscal[IB];
+    unsigned sd[IB];
+    ItemSim ck[IB];
+#pragma unroll
+    for (int k = 0; k < IB; ++k) {
+        if (k >= n) continue;
+        item_sim(E, si[k], c);
+        ck[k] = c;
     }
-    WorkItem tmp1, tmp2;
-    build_item(E, g1, &tmp1, step_ahead, c_sim, c_step);
-    build_item(E, g2, &tmp2, step_ahead, c_sim, c_step);
-    const int4 *a = reinterpret_cast<const int4 *>(&tmp1);
-    const int4 *c = reinterpret_cast<const int4 *>(&tmp2);
-    int4 *p1 = reinterpret_cast<int4 *>(o1);
-    int4 *p2 = reinterpret_cast<int4 *>(o2);
-    p1[0] = a[0];
-    p1[1] = a[1];
-    p1[2] = a[2];
-    p2[0] = c[0];
-    p2[1] = c[1];
-    p2[2] = c[2];
+#pragma unroll
+    for (int k = 0; k < IB; ++k) {
+        if (k >= n) continue;
+        const ItemSim &q = ck[k];
+        b[k] = (int)(g[k] - q.bb);
+        const int cx = b[k] % q.mx, cy = (b[k] / q.mx) % q.my, cz = b[k] / (q.mx * q.my);
+        // a brick outside its sim's grid (never listed) gets no box
+        slot[k] = (b[k] >= 0 && cz < q.mz) ? __ldcg(E.slot_of_brick + g[k]) : -1;
+        kslab[k] = __ldg(E.kslab_of_brick + g[k]);
+        kscal[k] = __ldg(E.kscal + g[k]);
+        sd[k] = __ldcg(E.sd_of_brick + g[k]);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+            const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
+            const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
+            nb[k][f] = (ax >= 0 && ay >= 0 && az >= 0 && ax < q.mx && ay < q.my && az < q.mz)
+                           ? __ldcg(E.slot_of_brick + q.bb + ((long long)az * q.my + ay) * q.mx + ax)
+                           : -3;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < IB; ++k) {
+        if (k >= n) continue;
+        const ItemSim &q = ck[k];
+        const unsigned long long kp = kslab[k] >= 0 ? q.kslabs + (size_t)kslab[k] * BVOL * sizeof(float)
+                                                     : (KP_SCALAR | __float_as_uint(kscal[k]));
+        const unsigned flags = ((unsigned)si[k] << 16) | sd[k];   // sd word carries the has-source bit
+        // The item is processed by the next launch, which steps from phi^{n+1}.
+        const int nh = (int)((q.step + step_ahead) & 1);
+        int4 *p = reinterpret_cast<int4 *>(out[k]);
+        p[0] = make_int4(slot[k], b[k], (int)(unsigned)kp, (int)(unsigned)(kp >> 32));
+        p[1] = make_int4((int)flags, nb[k][0], nb[k][1], nb[k][2]);
+        p[2] = make_int4(nb[k][3], nb[k][4], nb[k][5], nh);
+    }
 }
 
-// Active list from the bitmap, in brick order: this block's word range gets
-// positions after the active bricks of all earlier ranges (per-range counts
-// are kept by the update procedure); ballot/popc + block scan place each set
-// bit, then the block builds the work items of its positions.
+// Rebuild the active list from the bitmap in brick order.  Each block owns
+// a range of bitmap words; its offset in the list is the sum of the
+// per-range counts (blocktot, kept by the update procedure) of the blocks
+// before it.  The brick ids of the range (popc + block scan) go to shared
+// memory when they fit, else to the global listids, and the block then
+// builds the items from there, IB per thread at a time.
+constexpr int SMEM_IDS = 4096;
+
 __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int step_ahead)
 {
+    __shared__ int s_ids[SMEM_IDS];
     long long before = 0, all = 0;
     for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) {
         const int v = __ldcg(E.blocktot + j);
         all += v;
         if (j < (int)blockIdx.x) before += v;
     }
+    const int mine = __ldcg(E.blocktot + blockIdx.x);
     before = block_sum(before);
     all = block_sum(all);
+    const bool local = mine <= SMEM_IDS;
+    int *ids = local ? s_ids : E.listids + before;
+    const int cap = local ? SMEM_IDS : (int)max(0ll, (long long)E.n_slots - before);
     const long long w0 = (long long)blockIdx.x * E.words_per_block;
     const long long w1 = min(w0 + E.words_per_block, E.n_words);
-    int off = (int)before;
+    int off = 0;
     for (long long wb = w0; wb < w1; wb += BLOCK) {
         const long long w = wb + threadIdx.x;
         unsigned bits = w < w1 ? __ldcg(E.bitmap + w) : 0u;
@@ -712,20 +739,27 @@ __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int st
         while (bits) {
             const int bit = __ffs(bits) - 1;
             bits &= bits - 1;
-            if (pos < E.n_slots) E.listids[pos] = (int)(w * 32 + bit);
+            if (pos < cap) ids[pos] = (int)(w * 32 + bit);
             ++pos;
         }
         off += total;
     }
     __syncthreads();
-    const int end = min(off, E.n_slots);
-    int c_sim = -1;
-    long long c_step = 0;
-    for (int pos = (int)before + threadIdx.x; pos < end; pos += 2 * BLOCK) {
-        const int pos2 = pos + BLOCK;
-        const long long g1 = E.listids[pos];
-        const long long g2 = pos2 < end ? (long long)E.listids[pos2] : -1;
-        build_item2(E, g1, Lout + pos, g2, g2 >= 0 ? Lout + pos2 : nullptr, step_ahead, c_sim, c_step);
+    const int n = min(off, cap);
+    const int end = (int)min((long long)n, (long long)E.n_slots - before);
+    ItemSim c;
+    for (int i = threadIdx.x; i < end; i += IB * BLOCK) {
+        long long g[IB];
+        WorkItem *o[IB];
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            const int ik = i + k * BLOCK;
+            g[k] = ik < end ? (long long)ids[ik] : 0;
+            o[k] = Lout + before + ik;
+            m += ik < end ? 1 : 0;
+        }
+        build_items(E, g, m, o, step_ahead, c);
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_out = (int)all;
 }
@@ -744,9 +778,15 @@ struct SimCache {
     int neighbours = 6;
     long long step = 0;
     double thr = 0.0;
+    // The level rounded down to binary32: for a binary32 value v,
+    // (double)v > thr exactly when v > thr_f (no binary32 lies between them),
+    // so the decisions stay in FP32 (the FP64 pipe is slow here).
+    float thr_f = 0.f;
 };
 
-__device__ __forceinline__ void sim_cache(const Engine &E, int sim, SimCache &c)
+// nh: the half holding phi^n this step (= step parity), known from the item,
+// so the domain maximum loads alongside the step counter.
+__device__ __forceinline__ void sim_cache(const Engine &E, int sim, int nh, SimCache &c)
 {
     if (sim == c.sim) return;
     const SimDev *S = E.sims + sim;
@@ -757,8 +797,9 @@ __device__ __forceinline__ void sim_cache(const Engine &E, int sim, SimCache &c)
     c.neighbours = __ldg(&S->neighbours);
     c.manage = (c.step + 1) % c.interval == 0;
     c.lpf = __ldg(&S->lpf) != 0;
-    const double G = (double)__uint_as_float(__ldcg(&S->gmax[c.step & 1]));
+    const double G = (double)__uint_as_float(__ldcg(&S->gmax[nh]));
     c.thr = __ldg(&S->thr_mode) == 1 ? __ldg(&S->tau) * G : __ldg(&S->tau);
+    c.thr_f = __double2float_rd(c.thr);
 }
 
 // Record the shut-down count of a kept brick, or release its box.
@@ -780,7 +821,7 @@ __device__ __forceinline__ void keep_or_release(const Engine &E, const WorkItem 
 // brick is triggered when its own maximum is above the level or a source
 // feeds it during the steps the update covers; it stays when it or any of
 // its 26 neighbours is triggered; a triggered brick boxes all 26 neighbours.
-__device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool above, bool nonzero, double thr,
+__device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool above, bool nonzero, float thr,
                                        int interval, bool lpf, int sim, SimDev *S)
 {
     const int b = w.brick;
@@ -823,7 +864,7 @@ __device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool 
         for (int i = 0; i < 26; ++i) nm[i] = nslot[i] >= 0 ? __ldcg(E.rec + (size_t)nslot[i] * 8 + 6) : 0.f;
 #pragma unroll
         for (int i = 0; i < 26; ++i)
-            if (nslot[i] >= 0 && (double)nm[i] > thr) hot = true;
+            if (nslot[i] >= 0 && nm[i] > thr) hot = true;
     }
     unsigned sd = w.flags & SD_MASK;
     const unsigned sd0 = sd;
@@ -855,22 +896,22 @@ __device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool 
 }
 
 __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, const float4 &r0, const float4 &r1,
-                                        SimCache &c)
+                                        int age_flip, SimCache &c)
 {
     const int slot = w.slot;
     const int sim = (int)(w.flags >> 16);
     SimDev *S = E.sims + sim;
-    sim_cache(E, sim, c);
+    sim_cache(E, sim, w.nh ^ age_flip, c);
     if (c.dense || !c.manage) return;
     const long long step = c.step;
-    const double thr = c.thr;
+    const float thr = c.thr_f;   // see SimCache
     const int b = w.brick;
     if (c.neighbours == 26) {
-        p2_item26(E, w, (double)r1.z > thr, r1.z > 0.f, thr, c.interval, c.lpf, sim, S);
+        p2_item26(E, w, r1.z > thr, r1.z > 0.f, thr, c.interval, c.lpf, sim, S);
         return;
     }
     const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
-    bool hot = (double)r1.z > thr;
+    bool hot = r1.z > thr;
     if (!hot) {
         // the touching faces of the boxed neighbours (loads in parallel)
         float nf[6];
@@ -878,7 +919,7 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
         for (int f = 0; f < 6; ++f) nf[f] = w.nb[f] >= 0 ? __ldcg(E.rec + (size_t)w.nb[f] * 8 + (f ^ 1)) : 0.f;
 #pragma unroll
         for (int f = 0; f < 6; ++f)
-            if (w.nb[f] >= 0 && (double)nf[f] > thr) hot = true;
+            if (w.nb[f] >= 0 && nf[f] > thr) hot = true;
     }
     // a source feeds it during the steps this update covers
     if (!hot && (w.flags & FLAG_HAS_SRC) && forced_in(E, S, b, step + 1, step + c.interval)) hot = true;
@@ -908,7 +949,7 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
     int n = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-        if (w.nb[f] == -1 && (double)fc[f] > thr) {
+        if (w.nb[f] == -1 && fc[f] > thr) {
             const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
             const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
             const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
@@ -921,10 +962,27 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
 // ---------------------------------------------------------------------------
 // The step kernel.
 // ---------------------------------------------------------------------------
-// Advance every live sim's step (after all blocks have read it this launch).
+// True in every thread of the last block to get here (block-uniform); the
+// other blocks' writes before their arrival are visible to it.
+__device__ bool last_block(EngineState *st)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const bool last = atomicAdd(&st->p3_done, 1u) == gridDim.x - 1;
+        if (last) __threadfence();
+        s_last = last;
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// Advance every live sim's step (after all blocks have read it this launch);
+// called by every thread of one block.
 __device__ void advance_steps(const Engine &E)
 {
-    for (int s = 0; s < E.n_sims; ++s) {
+    for (int s = threadIdx.x; s < E.n_sims; s += BLOCK) {
         SimDev *S = E.sims + s;
         if (!__ldcg(&S->live)) continue;
         const long long n = __ldcg(&S->step);
@@ -934,10 +992,9 @@ __device__ void advance_steps(const Engine &E)
 }
 
 template <int ST>
-__global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int manage)
+__global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage)
 {
     EngineState *st = E.st;
-    const int cur = __ldcg(&st->list_parity);
     const int age_flip = __ldcg(&st->list_age) & 1;
     const WorkItem *L = cur ? E.items1 : E.items0;
     WorkItem *Lnext = cur ? E.items0 : E.items1;
@@ -998,12 +1055,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int manage)
     if (!manage) {
         // Time stepping only: the last block to finish advances the step and
         // the age of the (kept) active list.
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            if (atomicAdd(&st->p3_done, 1u) == gridDim.x - 1) {
-                __threadfence();
-                advance_steps(E);
+        if (last_block(st)) {
+            advance_steps(E);
+            if (threadIdx.x == 0) {
                 st->list_age += 1;
                 st->launches += 1;
                 st->p3_done = 0u;
@@ -1012,7 +1066,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int manage)
         }
         return;
     }
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, &st->bar_count)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t_p1 = globaltimer();
 
     // ---- P2: updating active cells ---------------------------------------
@@ -1038,23 +1092,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int manage)
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (base + u * nthr < nact && w[u].slot >= 0) p2_item(E, w[u], r0[u], r1[u], sc);
+                if (base + u * nthr < nact && w[u].slot >= 0) p2_item(E, w[u], r0[u], r1[u], age_flip, sc);
         }
-        // Manual activation of source bricks still being fed during the
-        // steps this update covers (n+1 .. n+interval).
-        if (blockIdx.x == 0) {
-            for (int s = threadIdx.x; s < E.n_src; s += BLOCK) {
-                const SrcDev sd = E.src[s];
-                SimDev *S = E.sims + sd.sim;
-                if (S->dense) continue;
-                const long long n1 = __ldcg(&S->step) + 1;
-                const int iv = __ldg(&S->interval);
-                if (n1 % iv != 0) continue;   // this sim does not run the update now
-                if (n1 + iv - 1 >= sd.start && n1 < sd.start + sd.len) claim_bricks<1>(E, sd.sim, S, &sd.brick, 1);
-            }
-        }
+        // (Source bricks need no activation here: every source starts at its
+        // sim's first step, its brick is boxed when the sim starts, and the
+        // update keeps it while samples remain.)
     }
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, &st->bar_count)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t_p2 = globaltimer();
 
     // ---- P3: box recycling and compaction of the active list -------------
@@ -1073,12 +1117,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int manage)
         compact_list(E, Lnext, &st->n_active[cur ^ 1], 1);
         // The last block to finish advances the step: every block has read
         // the step counters by then.
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            if (atomicAdd(&st->p3_done, 1u) == gridDim.x - 1) {
-                __threadfence();
-                advance_steps(E);
+        if (last_block(st)) {
+            advance_steps(E);
+            if (threadIdx.x == 0) {
                 st->list_parity = cur ^ 1;
                 st->list_age = 0;
                 st->launches += 1;
@@ -1532,7 +1573,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
         if (idx < E.lpf_cap) E.lpf_aff[idx] = g;
         else atomicOr(&st->err, ERR_NOMEM);
     }
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, &st->bar_count_lpf)) return;
     const int naff = min(__ldcg(&st->n_lpf_aff), E.lpf_cap);
     // (B) one block per affected brick
     float *R = reinterpret_cast<float *>(smem);                         // [2][L][L][L]
@@ -1583,7 +1624,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
             __syncthreads();
         }
     }
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, &st->bar_count_lpf)) return;
     // (C) write back
     for (long long i = gtid; i < (long long)naff * 2 * BVOL; i += nthr) {
         const int c = (int)(i / (2 * BVOL)), e = (int)(i % (2 * BVOL));
@@ -1618,11 +1659,11 @@ cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s)
     return cudaLaunchCooperativeKernel((const void *)k_lpf, dim3(grid), dim3(BLOCK), args, LPF_SMEM, s);
 }
 
-cudaError_t launch_step(const Engine &e, int grid, int manage, cudaStream_t s)
+cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaStream_t s)
 {
     Engine copy = e;
-    int m = manage;
-    void *args[] = {&copy, &m};
+    int p = parity, m = manage;
+    void *args[] = {&copy, &p, &m};
     const void *fn = e.storage == ST_BF16 ? (const void *)k_step<ST_BF16>
                      : e.storage == ST_F16 ? (const void *)k_step<ST_F16>
                                            : (const void *)k_step<ST_F32>;
