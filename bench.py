@@ -198,6 +198,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = updates * BYTES_PER_UPDATE / (total_ms / 1e3) / 1e9
     traffic = profiled_traffic(updates / max(launches, 1))
     sim.close()
+    marginal = None
+    if not args.quick and world == 1:
+        marginal = per_cell_fit(tcm, W, wl, pool, local_rank, TOTAL_STEPS - K, step_ms, peaks["hbm_gbs"])
     del pool
     torch.cuda.empty_cache()
 
@@ -208,6 +211,7 @@ def run_ours(args, rank, world, local_rank):
     cpu = cpu_baseline(W, args, wl=wl) if (rank == 0 and world == 1 and not args.quick) else None
     serving = serving_leg(torch, W, args, local_rank) if (not args.quick and args.serving > 0) else None
     precision = precision_leg(torch, tcm, W, dev, local_rank) if (rank == 0 and not args.quick) else None
+    virtual = virtual_leg(torch, tcm, W, local_rank) if (rank == 0 and not args.quick and args.virtual) else None
 
     if rank != 0:
         return
@@ -236,6 +240,7 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": "k_step (persistent, one launch per step)"},
         "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                     "min": float(min(step_ms)), "max": float(max(step_ms))},
+        "per_active_cell": marginal,
         "phase_ms": {"time_stepping": ph[0] / 1e6, "update_active": ph[1] / 1e6,
                      "compaction": ph[2] / 1e6},
         "active_bricks_end": active_end[0],
@@ -250,7 +255,68 @@ def run_ours(args, rank, world, local_rank):
         line["serving"] = serving
     if precision is not None:
         line["precision"] = precision
+    if virtual is not None:
+        line["virtual_4096"] = virtual
     print(json.dumps(line), flush=True)
+
+
+def per_cell_fit(tcm, W, wl, pool, local_rank, first, step_ms, hbm_peak):
+    """Split the timed steps' CUDA-event times into a fixed cost per step and a
+    cost per active cell: the node updates of every step are recorded by an
+    untimed replay of the same (deterministic) run, one launch at a time, and
+    t_step = fixed + updates / rate is fitted by least squares.  Also the
+    whole-step rate of the last 200 steps (the largest active sets)."""
+    s = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
+    s.step(first)
+    upd = []
+    last = s.updates
+    for _ in range(len(step_ms)):
+        s.step(1)
+        u = s.updates
+        upd.append(u - last)
+        last = u
+    s.close()
+    u = np.asarray(upd, dtype=np.float64)
+    t = np.asarray(step_ms, dtype=np.float64) / 1e3
+    A = np.vstack([np.ones_like(u), u]).T
+    (fixed, per_update), *_ = np.linalg.lstsq(A, t, rcond=None)
+    rate = BYTES_PER_UPDATE / per_update / 1e9
+    late = slice(max(0, len(t) - 200), len(t))
+    late_gbs = u[late].sum() * BYTES_PER_UPDATE / t[late].sum() / 1e9
+    return {"fixed_us_per_step": fixed * 1e6, "marginal_gbs": rate, "marginal_frac": rate / hbm_peak,
+            "fixed_share_of_run": fixed * len(t) / t.sum(),
+            "last_200_steps_gbs": late_gbs, "last_200_steps_frac": late_gbs / hbm_peak,
+            "last_200_steps_mean_active_cells": float(u[late].mean()),
+            "how": "least squares t_step = fixed + updates/rate over the timed steps; updates per step "
+                   "from an untimed replay"}
+
+
+def virtual_leg(torch, tcm, W, local_rank):
+    """The virtual 4096^3 domain (a dense grid would need 4096^3 x 3 x 4 B =
+    824 GB): sphere inclusion, 3-cycle Ricker burst, relative threshold 1e-6,
+    20-step decay, pool capped at 120 GiB, 2500 steps from create to the last
+    step, device time."""
+    wl = W.virtual()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s = tcm.Sim.from_workload(wl, device=local_rank)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step_async(wl.steps)
+    e1.record()
+    s.sync()
+    ms = e0.elapsed_time(e1)
+    boxes, free = s.pool_info()
+    out = {"workload": f"{wl.name}, {wl.steps} steps", "create_s": t_create, "steps_s": ms / 1e3,
+           "cell_updates": s.updates, "updates_per_s": s.updates / (ms / 1e3),
+           "active_bricks_end": s.active_count()[0], "pool_boxes": boxes, "pool_boxes_free_end": free,
+           "dense_bytes_needed": 4096 ** 3 * 12, "pool_bytes": wl.pool_bytes}
+    s.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def time_to_solution(torch, tcm, W, wl, dev, local_rank):
@@ -486,6 +552,7 @@ def main():
                     help="skip time-to-solution, e2e, CPU baseline and serving")
     ap.add_argument("--serving", type=int, default=120, help="requests in the serving leg (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=8.0, help="serving arrivals per second")
+    ap.add_argument("--virtual", type=int, default=1, help="run the virtual 4096^3 leg (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
