@@ -98,6 +98,9 @@ typedef struct {
     int storage;        /* TCM_STORAGE_F32 / _BF16 / _F16 */
     int dense;          /* 1: box every brick and never release (dense comparator) */
     int device;         /* CUDA device ordinal */
+    int no_graphs;      /* 1: issue every step launch directly; 0: runs of launches up to
+                           the next change of the batch are captured once as a CUDA graph
+                           and replayed (same kernels, same results) */
 } tcm_options;
 
 /* Bytes of pool one box takes for this brick shape and storage (two field
@@ -233,6 +236,8 @@ tcm_status tcm_phase_ns(const tcm_sim *sim, int64_t *stepping, int64_t *update, 
 
 /* Kernel launches issued so far (one per step). */
 int64_t tcm_launch_count(const tcm_sim *sim);
+/* How many of those launches were replayed from captured CUDA graphs. */
+int64_t tcm_graph_launch_count(const tcm_sim *sim);
 
 /* Step index n of phi^n. */
 int64_t tcm_step_index(const tcm_sim *sim);
@@ -265,6 +270,7 @@ typedef struct {
     int storage;        /* TCM_STORAGE_F32 / _BF16 / _F16 */
     int64_t max_bricks; /* brick-table capacity summed over simulations (12 B per brick) */
     int max_sims;       /* simulation-table capacity */
+    int no_graphs;      /* as in tcm_options */
 } tcm_batch_options;
 
 tcm_status tcm_batch_create(const tcm_batch_options *options, tcm_batch **out);

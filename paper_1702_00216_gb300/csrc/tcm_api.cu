@@ -84,6 +84,19 @@ struct tcm_batch {
     int list_parity = 0;
     bool dirty_list = false;   // the active list must be rebuilt before the next step
     int lpf_grid = 0;          // grid of the Eq. 7 kernel (0 until a sim uses it)
+    // Captured CUDA graphs of launch sequences, keyed by their launch
+    // arguments; valid for the Engine they were captured with.
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;   // private stream to capture on (the user's may be the legacy one)
+    struct Graph {
+        std::vector<int> key;
+        cudaGraphExec_t exec;
+        unsigned long long last_use;
+    };
+    std::vector<Graph> graphs;
+    Engine graph_engine{};
+    unsigned long long graph_clock = 0;
+    long long graph_launches = 0;   // launches issued through graphs
 };
 
 namespace {
@@ -747,12 +760,131 @@ tcm_status freeze_sim(tcm_batch *b, int id)
     return TCM_OK;
 }
 
+void drop_graphs(tcm_batch *b)
+{
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+}
+
+// Launch arguments of the next m steps: per launch (list parity, whether any
+// sim runs the update procedure, whether any of those uses Eq. 7), from the
+// host copy of every sim's step counter.
+std::vector<int> step_args(const tcm_batch *b, long long m)
+{
+    std::vector<int> key;
+    key.reserve((size_t)(3 * m + 1));
+    key.push_back((int)m);
+    int parity = b->list_parity;
+    for (long long j = 0; j < m; ++j) {
+        int manage = 0, lpf = 0;
+        for (int id = 0; id < b->max_sims; ++id) {
+            const HostSim &h = b->sims[id];
+            if (h.used && h.live && !h.dense && (h.step + j + 1) % h.dev.interval == 0) {
+                manage = 1;
+                lpf |= h.dev.lpf;
+            }
+        }
+        key.push_back(parity);
+        key.push_back(manage);
+        key.push_back(lpf);
+        if (manage) parity ^= 1;
+    }
+    return key;
+}
+
+// Issue the launches described by `key` as one CUDA graph (captured on first
+// use and kept, up to 32 graphs).  Returns false if capture is unavailable;
+// nothing has been launched then.
+bool launch_graph(tcm_batch *b, const std::vector<int> &key)
+{
+    if (std::memcmp(&b->graph_engine, &b->E, sizeof(Engine)) != 0) {
+        drop_graphs(b);
+        std::memcpy(&b->graph_engine, &b->E, sizeof(Engine));
+    }
+    tcm_batch::Graph *hit = nullptr;
+    for (auto &g : b->graphs)
+        if (g.key == key) hit = &g;
+    if (!hit) {
+        cudaGraph_t graph = nullptr;
+        if (!b->cap_stream && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            b->cap_stream = nullptr;
+            b->use_graphs = false;
+            return false;
+        }
+        if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            b->use_graphs = false;
+            return false;
+        }
+        cudaError_t e = cudaSuccess;
+        const long long m = key[0];
+        for (long long j = 0; j < m && e == cudaSuccess; ++j) {
+            e = launch_step(b->E, b->grid, key[1 + 3 * j], key[2 + 3 * j], b->cap_stream);
+            if (e == cudaSuccess && key[3 + 3 * j]) e = launch_lpf(b->E, b->lpf_grid, b->cap_stream);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess && e2 == cudaSuccess && graph)
+            e = cudaGraphInstantiate(&exec, graph, 0);
+        else
+            e = e != cudaSuccess ? e : e2;
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || !exec) {
+            cudaGetLastError();
+            b->use_graphs = false;   // capture not available: launch directly from now on
+            return false;
+        }
+        if (b->graphs.size() >= 32) {
+            size_t old = 0;
+            for (size_t i = 1; i < b->graphs.size(); ++i)
+                if (b->graphs[i].last_use < b->graphs[old].last_use) old = i;
+            cudaGraphExecDestroy(b->graphs[old].exec);
+            b->graphs.erase(b->graphs.begin() + (long)old);
+        }
+        b->graphs.push_back({key, exec, 0});
+        hit = &b->graphs.back();
+    }
+    hit->last_use = ++b->graph_clock;
+    if (cudaGraphLaunch(hit->exec, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        b->use_graphs = false;
+        return false;
+    }
+    return true;
+}
+
 tcm_status batch_step_async(tcm_batch *b, long long n)
 {
     if (b->poisoned) return TCM_ESTATE;
     DeviceGuard g(b->device);
     TRYS(prime_all(b));
-    for (long long i = 0; i < n; ++i) {
+    for (long long i = 0; i < n;) {
+        TRYS(ensure_list(b));
+        // Launches up to the next freeze (a sim reaching its step count)
+        // form one graph.
+        long long m = std::min<long long>(n - i, 64);
+        for (int id = 0; id < b->max_sims; ++id) {
+            const HostSim &h = b->sims[id];
+            if (h.used && h.live && h.target > 0) m = std::min(m, h.target - h.step);
+        }
+        if (b->use_graphs && m >= 2) {
+            const std::vector<int> key = step_args(b, m);
+            if (launch_graph(b, key)) {
+                b->launches += m;
+                b->graph_launches += m;
+                for (long long j = 0; j < m; ++j)
+                    if (key[2 + 3 * j]) b->list_parity ^= 1;
+                for (int id = 0; id < b->max_sims; ++id) {
+                    HostSim &h = b->sims[id];
+                    if (!h.used || !h.live) continue;
+                    h.step += m;
+                    if (h.target > 0 && h.step >= h.target) TRYS(freeze_sim(b, id));
+                }
+                i += m;
+                continue;
+            }
+        }
         TRYS(ensure_list(b));
         // Does any simulation run the update procedure after this step (and
         // with the Eq. 7 shut-down)?
@@ -778,6 +910,7 @@ tcm_status batch_step_async(tcm_batch *b, long long n)
             h.step += 1;
             if (h.target > 0 && h.step >= h.target) TRYS(freeze_sim(b, id));
         }
+        ++i;
     }
     return TCM_OK;
 }
@@ -866,6 +999,7 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     tcm_batch *b = nullptr;
     TRYS(batch_new(options->device, (cudaStream_t)options->stream, options->pool_ptr, pool_bytes, options->storage,
                    n_bricks, 1, &b));
+    b->use_graphs = !options->no_graphs;
     DeviceGuard g(b->device);
     int id = -1;
     tcm_status st = sim_add(b, domain, velocity, dx, dt, c_max, threshold, options->threshold_mode,
@@ -1164,6 +1298,8 @@ tcm_status tcm_phase_ns(const tcm_sim *cs, int64_t *stepping, int64_t *update, i
 
 int64_t tcm_launch_count(const tcm_sim *s) { return sim_of(s) ? s->b->launches : -1; }
 
+int64_t tcm_graph_launch_count(const tcm_sim *s) { return sim_of(s) ? s->b->graph_launches : -1; }
+
 int64_t tcm_step_index(const tcm_sim *s)
 {
     HostSim *h = sim_of(s);
@@ -1201,8 +1337,10 @@ tcm_status tcm_batch_create(const tcm_batch_options *o, tcm_batch **out)
     if (!out) return TCM_EINVAL;
     *out = nullptr;
     if (!o) return TCM_EINVAL;
-    return batch_new(o->device, (cudaStream_t)o->stream, o->pool_ptr, o->pool_bytes, o->storage, o->max_bricks,
-                     o->max_sims, out);
+    const tcm_status st = batch_new(o->device, (cudaStream_t)o->stream, o->pool_ptr, o->pool_bytes, o->storage,
+                                    o->max_bricks, o->max_sims, out);
+    if (st == TCM_OK) (*out)->use_graphs = !o->no_graphs;
+    return st;
 }
 
 tcm_status tcm_batch_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_model *velocity, double dx,
@@ -1301,6 +1439,8 @@ void tcm_batch_destroy(tcm_batch *b)
         if (h.lpf_a) cudaFree(h.lpf_a);
     }
     for (tcm_sim *s : b->handles) delete s;
+    drop_graphs(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (void *p : b->allocs) cudaFree(p);
     if (b->d_src) cudaFree(b->d_src);
     if (b->d_wave) cudaFree(b->d_wave);

@@ -1642,6 +1642,23 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
     }
 }
 
+// Cooperative launch (every block resident at once, so the grid barriers
+// are safe) through cudaLaunchKernelEx, which stream capture accepts.
+cudaError_t launch_cooperative(const void *fn, int grid, size_t smem, void **args, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 int lpf_grid_size(int device)
 {
     int sms = 0, per_sm = 0;
@@ -1656,7 +1673,7 @@ cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s)
 {
     Engine copy = e;
     void *args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void *)k_lpf, dim3(grid), dim3(BLOCK), args, LPF_SMEM, s);
+    return launch_cooperative((const void *)k_lpf, grid, LPF_SMEM, args, s);
 }
 
 cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaStream_t s)
@@ -1667,7 +1684,7 @@ cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaS
     const void *fn = e.storage == ST_BF16 ? (const void *)k_step<ST_BF16>
                      : e.storage == ST_F16 ? (const void *)k_step<ST_F16>
                                            : (const void *)k_step<ST_F32>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, 0, s);
+    return launch_cooperative(fn, grid, 0, args, s);
 }
 
 cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,

@@ -31,7 +31,7 @@ EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "t
            "tcm_step_async", "tcm_sync", "tcm_set_schedule", "tcm_schedule", "tcm_set_lpf_shutdown", "tcm_read_field", "tcm_read_field_device",
            "tcm_active_count", "tcm_active_bricks", "tcm_updates", "tcm_energy",
            "tcm_energy_noalloc",
-           "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_step_index",
+           "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_graph_launch_count", "tcm_step_index",
            "tcm_status_string", "tcm_destroy", "tcm_batch_create", "tcm_batch_add",
            "tcm_batch_step", "tcm_batch_step_async", "tcm_batch_sync", "tcm_sim_done",
            "tcm_batch_remove", "tcm_batch_info", "tcm_batch_destroy"]
@@ -54,13 +54,13 @@ class tcm_brick(C.Structure):
 class tcm_options(C.Structure):
     _fields_ = [("threshold_mode", C.c_int), ("decay_alpha", C.c_float), ("decay_steps", C.c_int),
                 ("pool_ptr", C.c_void_p), ("pool_bytes", C.c_size_t), ("stream", C.c_void_p),
-                ("storage", C.c_int), ("dense", C.c_int), ("device", C.c_int)]
+                ("storage", C.c_int), ("dense", C.c_int), ("device", C.c_int), ("no_graphs", C.c_int)]
 
 
 class tcm_batch_options(C.Structure):
     _fields_ = [("pool_ptr", C.c_void_p), ("pool_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("device", C.c_int), ("storage", C.c_int), ("max_bricks", C.c_int64),
-                ("max_sims", C.c_int)]
+                ("max_sims", C.c_int), ("no_graphs", C.c_int)]
 
 
 class TCMError(RuntimeError):
@@ -103,6 +103,7 @@ def lib():
             "tcm_pool_info": ([_vp, _vp, _vp], C.c_int),
             "tcm_phase_ns": ([_vp, _vp, _vp, _vp], C.c_int),
             "tcm_launch_count": ([_vp], _i64),
+            "tcm_graph_launch_count": ([_vp], _i64),
             "tcm_step_index": ([_vp], _i64),
             "tcm_status_string": ([C.c_int], C.c_char_p),
             "tcm_destroy": ([_vp], None),
@@ -363,7 +364,8 @@ class Sim:
 
     def __init__(self, shape, media, dx, dt, threshold=0.0, brick=(8, 8, 8),
                  thr_mode=TCM_THR_ABSOLUTE, decay_alpha=1.0, decay_steps=0, pool_bytes=None,
-                 dense=False, device=0, stream=None, pool_tensor=None, storage=TCM_STORAGE_F32):
+                 dense=False, device=0, stream=None, pool_tensor=None, storage=TCM_STORAGE_F32,
+                 graphs=True):
         self.shape = tuple(int(v) for v in shape)
         self.storage = storage_code(storage)
         nz, ny, nx = self.shape
@@ -381,6 +383,7 @@ class Sim:
         opts.decay_steps = int(decay_steps)
         opts.pool_bytes = int(pool_bytes)
         opts.storage = self.storage
+        opts.no_graphs = 0 if graphs else 1
         opts.dense = int(bool(dense))
         opts.device = int(device)
         if pool_tensor is not None:
@@ -482,6 +485,9 @@ class Sim:
     def launches(self):
         return tcm_launch_count(self._h)
 
+    def graph_launches(self):
+        return int(lib().tcm_graph_launch_count(self._h))
+
     @property
     def step_index(self):
         return tcm_step_index(self._h)
@@ -511,10 +517,11 @@ class Batch:
     """Many simulations stepped together by one launch per step (tcm_batch_*)."""
 
     def __init__(self, pool_bytes, max_bricks, max_sims=64, device=0, stream=None,
-                 pool_tensor=None, storage=TCM_STORAGE_F32):
+                 pool_tensor=None, storage=TCM_STORAGE_F32, graphs=True):
         torch = _torch()
         self.storage = storage_code(storage)
         o = tcm_batch_options()
+        o.no_graphs = 0 if graphs else 1
         o.pool_bytes = int(pool_bytes)
         o.device = int(device)
         o.storage = self.storage
