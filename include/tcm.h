@@ -82,7 +82,9 @@ typedef struct {
     const float *sphere_c;
 } tcm_velocity_model;
 
-/* Brick ("cell") shape in nodes.  Supported: 8x8x8. */
+/* Brick ("cell") shape in nodes.  Supported: 4x4x4, 8x8x8 and 16x8x8
+ * (bx x by x bz); a batch holds one shape.  The library is built once per
+ * shape; a simulation or batch runs on the build of its shape. */
 typedef struct {
     int bx, by, bz;
 } tcm_brick;
@@ -133,8 +135,9 @@ tcm_status tcm_set_field(tcm_sim *sim, const float *phi_now, const float *phi_pr
 /* Schedule of the update procedure ("Updating active cells", Eq. 5, Fig. 3).
  * interval >= 1: the procedure runs after every interval-th step of this
  * simulation (after step n when (n+1) % interval == 0); launches in between
- * only step the active bricks.  interval = 0: Eq. 5, n = dx * 8 / (2 c_max
- * dt) rounded down (at least 1), 8 = the brick edge in nodes.  A run covers
+ * only step the active bricks.  interval = 0: Eq. 5, n = dx * L / (2 c_max
+ * dt) rounded down (at least 1), L = the shortest brick edge in nodes (8 for
+ * 8^3 bricks).  A run covers
  * the steps up to the next one: a source brick fed in any of them is kept or
  * boxed, and a shut-down count (in time steps) drops by interval.
  * neighbours = 6 (default): a brick stays if its maximum or the touching face
@@ -143,7 +146,7 @@ tcm_status tcm_set_field(tcm_sim *sim, const float *phi_now, const float *phi_pr
  * maximum is above the level or a source feeds it; it stays if it or a boxed
  * one of its 26 neighbours is triggered by its maximum; a triggered brick
  * boxes all 26 neighbours (the paper's nearest and diagonal cells) -- with
- * interval <= 8 and threshold 0 this equals the dense grid exactly.
+ * interval <= L and threshold 0 this equals the dense grid exactly.
  * Default interval 1, neighbours 6.  Only before the first step (TCM_ESTATE
  * after); TCM_EINVAL for interval < 0 or another neighbour count. */
 tcm_status tcm_set_schedule(tcm_sim *sim, int interval, int neighbours);
@@ -152,14 +155,16 @@ tcm_status tcm_set_schedule(tcm_sim *sim, int interval, int neighbours);
  * released at once, and every boxed brick that stays (not claimed by this
  * run) with such a released brick among its 26 neighbours -- one that held a
  * non-zero value -- gets both time levels replaced by
- * Phi~ = F^-1[F(Phi) LPF] evaluated on its 3x3x3-brick block (24^3 nodes;
- * released, unboxed and outside bricks read zero) zero-padded to 64^3
- * (spatial oversampling), LPF = H(kx) H(ky) H(kz), H = 1 up to `pass`, 0
+ * Phi~ = F^-1[F(Phi) LPF] evaluated on its 3x3x3-brick block (L = 3 brick
+ * edges per axis, e.g. 24^3 nodes for 8^3 bricks; released, unboxed and
+ * outside bricks read zero) zero-padded to M^3, M the power of two >= 2 L
+ * (spatial oversampling; 64 for 8^3 bricks), LPF = H(kx) H(ky) H(kz), H = 1 up to `pass`, 0
  * from `stop` (fractions of the Nyquist frequency), raised cosine between;
  * the centre brick of the result is kept (FP64 arithmetic, rounded to the
  * storage).  All filtered values come from the state before any is
  * written.  decay_alpha / decay_steps are then unused.  0 < pass < stop <= 1
- * (TCM_EINVAL otherwise); only before the first step (TCM_ESTATE).  At most
+ * and cubic bricks (TCM_EINVAL otherwise); only before the first step
+ * (TCM_ESTATE).  At most
  * 65536 bricks are filtered per run (beyond that the batch reports
  * TCM_ENOMEM). */
 tcm_status tcm_set_lpf_shutdown(tcm_sim *sim, double pass, double stop);
@@ -271,6 +276,7 @@ typedef struct {
     int64_t max_bricks; /* brick-table capacity summed over simulations (12 B per brick) */
     int max_sims;       /* simulation-table capacity */
     int no_graphs;      /* as in tcm_options */
+    tcm_brick brick;    /* brick shape of every simulation of the batch ({0,0,0}: 8x8x8) */
 } tcm_batch_options;
 
 tcm_status tcm_batch_create(const tcm_batch_options *options, tcm_batch **out);

@@ -2,8 +2,10 @@
 
 Only sm_103a code is generated.  Floating-point flags keep Eq. 3 bit-exact:
 no FMA contraction (-fmad=false), no flush-to-zero, IEEE division and square
-root.  The two translation units compile in parallel, then link into one
-shared library with the CUDA runtime linked statically.
+root.  The runtime and kernels compile once per supported brick shape (with
+their entry points renamed per shape), plus the dispatcher of the public C
+ABI; all translation units compile in parallel and link into one shared
+library with the CUDA runtime linked statically.
 """
 from __future__ import annotations
 
@@ -18,11 +20,30 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtcm.so")
 UNITS = ["tcm_kernels.cu", "tcm_api.cu", "tcm_noalloc.cu"]
-DEPS = UNITS + ["tcm_internal.cuh"]
+DISPATCH = "tcm_dispatch.cpp"
+DEPS = UNITS + ["tcm_internal.cuh", DISPATCH]
+# One build of the runtime and kernels per brick shape (bx, by, bz, name);
+# tcm_dispatch.cpp routes the public entry points to them.
+SHAPES = [(4, 4, 4, "b444"), (8, 8, 8, "b888"), (16, 8, 8, "b1688")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-ftz=false", "-prec-div=true",
          "-prec-sqrt=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I", os.path.join(ROOT, "include")]
+
+
+def public_names():
+    """Entry points declared in include/tcm.h (renamed per shape build)."""
+    import re
+    src = open(os.path.join(ROOT, "include", "tcm.h")).read()
+    return sorted(set(re.findall(r"\b(tcm_[a-z_]+)\s*\(", src)))
+
+
+def shape_defines(bx, by, bz, name):
+    d = [f"-DTCM_BX={bx}", f"-DTCM_BY={by}", f"-DTCM_BZ={bz}", f"-Dtcm=tcm_{name}",
+         f"-Dtcm_sim=tcm_{name}_sim", f"-Dtcm_batch=tcm_{name}_batch",
+         f"-Dtcm_internal_view=tcm_{name}_internal_view"]
+    d += [f"-D{f}=tcm_{name}_{f[4:]}" for f in public_names()]
+    return d
 
 
 def nvcc() -> str:
@@ -41,12 +62,12 @@ def _stale() -> bool:
     return any(os.path.getmtime(s) > t for s in srcs)
 
 
-def _compile(unit: str, extra) -> str:
-    obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+def _compile(unit: str, extra, tag: str = "") -> str:
+    obj = os.path.join(BUILD, unit.replace(".cu", "").replace(".cpp", "") + tag + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, unit), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed on {unit}:\n{r.stdout}\n{r.stderr}")
+        raise RuntimeError(f"nvcc failed on {unit}{tag}:\n{r.stdout}\n{r.stderr}")
     return obj
 
 
@@ -56,8 +77,10 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    with cf.ThreadPoolExecutor(len(UNITS)) as ex:
-        objs = list(ex.map(lambda u: _compile(u, extra), UNITS))
+    jobs = [(u, extra + shape_defines(*sh), "_" + sh[3]) for sh in SHAPES for u in UNITS]
+    jobs.append((DISPATCH, [], ""))
+    with cf.ThreadPoolExecutor(min(len(jobs), max(4, os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(lambda j: _compile(*j), jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

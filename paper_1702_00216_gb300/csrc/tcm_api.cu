@@ -1042,8 +1042,10 @@ tcm_status tcm_set_schedule(tcm_sim *s, int interval, int neighbours)
     if (!h || interval < 0 || (neighbours != 6 && neighbours != 26)) return TCM_EINVAL;
     if (h->primed) return TCM_ESTATE;
     if (interval == 0) {
-        // Eq. 5: n = dx * (cell length) / (2 c dt), cell length BX nodes
-        const double n = h->c_max > 0.f ? h->dx * BX / (2.0 * (double)h->c_max * h->dt) : 1.0;
+        // Eq. 5: n = dx * (cell length) / (2 c dt), cell length = the
+        // shortest brick edge in nodes
+        const int edge = std::min(BX, std::min(BY, BZ));
+        const double n = h->c_max > 0.f ? h->dx * edge / (2.0 * (double)h->c_max * h->dt) : 1.0;
         interval = (int)std::max(1.0, std::min(std::floor(n), 1e6));
     }
     h->dev.interval = interval;
@@ -1055,6 +1057,7 @@ tcm_status tcm_set_lpf_shutdown(tcm_sim *s, double pass, double stop)
 {
     HostSim *h = sim_of(s);
     if (!h || !(pass > 0) || !(stop > pass) || !(stop <= 1)) return TCM_EINVAL;
+    if (BX != BY || BX != BZ) return TCM_EINVAL;   // the filter region is a cube of bricks
     if (h->primed) return TCM_ESTATE;
     tcm_batch *b = s->b;
     DeviceGuard g(b->device);

@@ -27,7 +27,14 @@
 
 namespace tcm {
 
-constexpr int BX = 8, BY = 8, BZ = 8;
+// Brick shape of this build of the library (one build per supported shape;
+// the public entry points dispatch on the shape a simulation was created with).
+#ifndef TCM_BX
+#define TCM_BX 8
+#define TCM_BY 8
+#define TCM_BZ 8
+#endif
+constexpr int BX = TCM_BX, BY = TCM_BY, BZ = TCM_BZ;
 constexpr int BVOL = BX * BY * BZ;          // nodes per brick
 constexpr int XQ = BX / 4;                  // float4 columns per brick row
 constexpr int TPB = XQ * BY;                // threads per brick (one float4 column, all z)
@@ -37,6 +44,8 @@ constexpr int TPB = XQ * BY;                // threads per brick (one float4 col
 constexpr int P1_WARPS = TCM_P1_WARPS;      // warps per CTA of the step kernel
 constexpr int BLOCK = 32 * P1_WARPS;        // threads per CTA of the step kernel
 constexpr int BRICKS_PER_WARP = 32 / TPB;
+static_assert(BX % 4 == 0 && TPB <= 32 && 32 % TPB == 0, "a brick's float4 columns must tile a warp");
+static_assert(BRICKS_PER_WARP == 1 || XQ <= 2, "pair exchange lane mapping needs XQ <= 2");
 
 constexpr unsigned ERR_NOMEM = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
@@ -129,9 +138,10 @@ struct EngineState {
 
 // Eq. 7 region: the 3x3x3-brick block around a brick (LPF_L nodes per axis),
 // zero-padded to LPF_M per axis; the filter keeps the centre LPF_C nodes.
-constexpr int LPF_C = 8;
+constexpr int LPF_C = BX;   // cubic bricks only
 constexpr int LPF_L = 3 * LPF_C;
-constexpr int LPF_M = 64;
+constexpr int lpf_pow2(int v) { return v <= 1 ? 1 : 2 * lpf_pow2((v + 1) / 2); }
+constexpr int LPF_M = lpf_pow2(2 * LPF_L);   // at least 2x oversampling
 
 struct Engine {
     void *phi;             // pool: 2 * BVOL elements of `storage` per box

@@ -35,8 +35,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 4000000000ull;  // 4 s
 
-static_assert(XQ >= 2, "the lane layout needs at least two float4 columns per row");
-static_assert(32 % TPB == 0, "bricks must tile a warp");
+
 
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -331,11 +330,15 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 
     float4 P[BZ], M[BZ], K[BZ], YH[BZ];
     float XH[BZ];
+    float XH2[XQ == 1 ? BZ : 1];
     float4 Zm = f4zero(), Zp = f4zero();
     // y-edge lanes read the touching row of y- / y+, x-edge lanes the
     // touching column of x- / x+ (unless exchanged within the pair)
     const int ys = !valid ? -1 : (y == 0 ? w.nb[2] : (y == BY - 1 ? w.nb[3] : -1));
+    // x-edge lanes: the column of x- (x4 == 0) or x+ (x4 == XQ-1); with one
+    // float4 per row (XQ == 1) a lane is both, and xs2 is the x+ one
     const int xs = !valid ? -1 : (x4 == 0 ? (share_xm ? -1 : w.nb[0]) : (x4 == XQ - 1 ? (share_xp ? -1 : w.nb[1]) : -1));
+    const int xs2 = (XQ == 1 && valid && !share_xp) ? w.nb[1] : -1;
     if (valid) {
         const typename F::T *now = half_ptr<ST>(E, w.slot, nh);
         const typename F::T *prv = half_ptr<ST>(E, w.slot, nh ^ 1);
@@ -378,6 +381,16 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 #pragma unroll
         for (int z = 0; z < BZ; ++z) XH[z] = 0.f;
     }
+    if constexpr (XQ == 1) {
+        if (xs2 >= 0) {
+            const typename F::T *xb = half_ptr<ST>(E, xs2, nh) + y * BX;
+#pragma unroll
+            for (int z = 0; z < BZ; ++z) XH2[z] = F::ld1(xb + z * BY * BX, sc);
+        } else {
+#pragma unroll
+            for (int z = 0; z < BZ; ++z) XH2[z] = 0.f;
+        }
+    }
 
     const float alpha = __ldg(&S->alpha);
     const bool decay = (w.flags & SD_MASK) != 0u;
@@ -395,13 +408,24 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         // x neighbours inside the brick through shuffles; the edge value from
         // the loaded face column or, within a pair, from lane ^ 17 (the x = 7
         // column of the first brick / the x = 0 column of the second)
-        const float lw = __shfl_up_sync(FULL, p.w, 1, TPB);
-        const float rx = __shfl_down_sync(FULL, p.x, 1, TPB);
-        const float send = (x4 == XQ - 1) ? p.w : p.x;
-        const float recv = __shfl_xor_sync(FULL, send, TPB + 1);
-        const float xe = xrecv ? recv : XH[z];
-        const float xm0 = (x4 == 0) ? xe : lw;
-        const float xp3 = (x4 == XQ - 1) ? xe : rx;
+        float xm0, xp3;
+        if constexpr (XQ == 1) {
+            // the whole row in one float4: x- from the x- brick (or the pair's
+            // first brick), x+ from the x+ brick (or the pair's second)
+            float recv = 0.f;
+            if constexpr (BRICKS_PER_WARP >= 2) recv = __shfl_xor_sync(FULL, share_xp ? p.w : p.x, TPB);
+            xm0 = share_xm ? recv : XH[z];
+            xp3 = share_xp ? recv : XH2[z];
+        } else {
+            const float lw = __shfl_up_sync(FULL, p.w, 1, TPB);
+            const float rx = __shfl_down_sync(FULL, p.x, 1, TPB);
+            float recv = 0.f;
+            if constexpr (BRICKS_PER_WARP >= 2)
+                recv = __shfl_xor_sync(FULL, (x4 == XQ - 1) ? p.w : p.x, TPB + XQ - 1);
+            const float xe = xrecv ? recv : XH[z];
+            xm0 = (x4 == 0) ? xe : lw;
+            xp3 = (x4 == XQ - 1) ? xe : rx;
+        }
         // y neighbours inside the brick through shuffles
         float4 ym, yp;
         ym.x = __shfl_up_sync(FULL, p.x, XQ, TPB);
@@ -1035,13 +1059,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
             bool vn = pn < npairs && in < nact;
             const WorkItem wn = load_item(L, vn ? in : 0);
             vn = vn && wn.slot >= 0;
-            // is the second brick of the pair the x+ neighbour of the first?
-            const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
-            const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
-            const bool pair_x = seg == 0 ? (other_v && w.nb[1] >= 0 && w.nb[1] == other_slot)
-                                         : (v && w.nb[0] >= 0 && w.nb[0] == other_slot);
-            p1_brick<ST>(E, w, v, t, seg, seg == 1 && pair_x, seg == 0 && pair_x, age_flip, cells, scells, gacc,
-                         gsim, gnh);
+            // bricks 2j and 2j+1 of the warp form a pair: is the second the x+
+            // neighbour of the first?
+            bool pair_x = false;
+            const bool first = (seg & 1) == 0;
+            if constexpr (BRICKS_PER_WARP >= 2) {
+                const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
+                const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
+                pair_x = v && other_v &&
+                         (first ? (w.nb[1] >= 0 && w.nb[1] == other_slot) : (w.nb[0] >= 0 && w.nb[0] == other_slot));
+            }
+            p1_brick<ST>(E, w, v, t, seg, !first && pair_x, first && pair_x, age_flip, cells, scells, gacc, gsim,
+                         gnh);
             pr = pn;
             w = wn;
             v = vn;

@@ -60,7 +60,7 @@ class tcm_options(C.Structure):
 class tcm_batch_options(C.Structure):
     _fields_ = [("pool_ptr", C.c_void_p), ("pool_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("device", C.c_int), ("storage", C.c_int), ("max_bricks", C.c_int64),
-                ("max_sims", C.c_int), ("no_graphs", C.c_int)]
+                ("max_sims", C.c_int), ("no_graphs", C.c_int), ("brick", tcm_brick)]
 
 
 class TCMError(RuntimeError):
@@ -517,11 +517,13 @@ class Batch:
     """Many simulations stepped together by one launch per step (tcm_batch_*)."""
 
     def __init__(self, pool_bytes, max_bricks, max_sims=64, device=0, stream=None,
-                 pool_tensor=None, storage=TCM_STORAGE_F32, graphs=True):
+                 pool_tensor=None, storage=TCM_STORAGE_F32, graphs=True, brick=(8, 8, 8)):
         torch = _torch()
         self.storage = storage_code(storage)
+        self.brick = tuple(int(v) for v in brick)
         o = tcm_batch_options()
         o.no_graphs = 0 if graphs else 1
+        o.brick = tcm_brick(*self.brick)
         o.pool_bytes = int(pool_bytes)
         o.device = int(device)
         o.storage = self.storage
