@@ -212,6 +212,7 @@ def run_ours(args, rank, world, local_rank):
     serving = serving_leg(torch, W, args, local_rank) if (not args.quick and args.serving > 0) else None
     precision = precision_leg(torch, tcm, W, dev, local_rank) if (rank == 0 and not args.quick) else None
     virtual = virtual_leg(torch, tcm, W, local_rank) if (rank == 0 and not args.quick and args.virtual) else None
+    tuning = tuning_leg(torch, tcm, W, wl, dev, local_rank) if (rank == 0 and not args.quick) else None
 
     if rank != 0:
         return
@@ -257,6 +258,8 @@ def run_ours(args, rank, world, local_rank):
         line["precision"] = precision
     if virtual is not None:
         line["virtual_4096"] = virtual
+    if tuning is not None:
+        line["autotune"] = tuning
     print(json.dumps(line), flush=True)
 
 
@@ -315,6 +318,35 @@ def virtual_leg(torch, tcm, W, local_rank):
            "active_bricks_end": s.active_count()[0], "pool_boxes": boxes, "pool_boxes_free_end": free,
            "dense_bytes_needed": 4096 ** 3 * 12, "pool_bytes": wl.pool_bytes}
     s.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def tuning_leg(torch, tcm, W, wl, dev, local_rank):
+    """The autotuner on the benchmark workload (brick shapes x update
+    schedules, steps 600..800 timed), then the full create-to-result run with
+    its choice, compared with the dense result."""
+    from paper_1702_00216_gb300 import autotune
+    r = autotune.autotune(wl, start=600, count=200, allow_schedule=True, device=local_rank)
+    best = autotune.apply(wl, r["best"])
+    out = {"window": r["window"], "table": r["table"], "best": r["best"].label()}
+    runs = {}
+    for name, w, dense in (("dense", wl, True), ("tuned", best, False)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s = tcm.Sim.from_workload(w, dense=dense, device=local_rank)
+        s.step(TOTAL_STEPS)
+        buf = torch.empty(w.shape, dtype=torch.float32, device=dev)
+        tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), w.shape[::-1], buf.data_ptr())
+        torch.cuda.synchronize()
+        runs[name] = (time.perf_counter() - t, s.updates, buf)
+        s.close()
+    out["tuned_s"] = runs["tuned"][0]
+    out["tuned_cell_updates"] = runs["tuned"][1]
+    out["dense_s"] = runs["dense"][0]
+    out["speedup_vs_dense"] = runs["dense"][0] / runs["tuned"][0]
+    out["max_abs_diff_vs_dense"] = float((runs["tuned"][2] - runs["dense"][2]).abs().max().item())
+    del runs
     torch.cuda.empty_cache()
     return out
 

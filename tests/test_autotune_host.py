@@ -1,0 +1,33 @@
+"""Autotuner host logic with the timing replaced: candidate sets, the
+choice of the fastest window, caching and applying a choice."""
+import pytest
+
+from paper_1702_00216_gb300 import autotune as A
+from paper_1702_00216_gb300 import workloads as W
+
+
+def test_candidates():
+    assert [c.label() for c in A.candidates()] == ["4x4x4", "8x8x8", "16x8x8"]
+    labels = [c.label() for c in A.candidates(allow_schedule=True)]
+    assert labels[3:] == ["4x4x4/eq5-26", "8x8x8/eq5-26", "16x8x8/eq5-26"]
+
+
+def test_picks_fastest_window_and_caches(monkeypatch):
+    calls = []
+
+    def fake(wl, c, start, count, device=0, storage="f32"):
+        calls.append((c.label(), start, count))
+        ms = {"4x4x4": 3.0, "8x8x8": 1.0, "16x8x8": 2.0}[c.label()]
+        return {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
+                "window_ms": ms, "cell_updates": 1, "updates_per_s": 1.0}
+
+    monkeypatch.setattr(A, "measure", fake)
+    A._CACHE.clear()
+    wl = W.small(n=32, steps=100)
+    r = A.autotune(wl)
+    assert r["best"].brick == (8, 8, 8) and r["window"] == [40, 60]
+    assert [t["config"] for t in r["table"]] == ["8x8x8", "16x8x8", "4x4x4"]
+    n = len(calls)
+    assert A.autotune(wl) is r and len(calls) == n        # cached
+    w2 = A.apply(wl, A.Candidate((16, 8, 8), 0, 26))
+    assert w2.brick == (16, 8, 8) and (w2.interval, w2.neighbours) == (0, 26) and wl.brick == (8, 8, 8)
