@@ -24,7 +24,7 @@
  *    default stream) of device tcm_options.device.
  *  - Arithmetic: binary32 round-to-nearest, no contraction into FMA, no
  *    flush-to-zero, one fixed grouping of Eq. 3:
- *        s = ((xm + xp) + (ym + yp)) + (zm + zp);  lap = s - 6 p;
+ *        s = ((((xm + xp) + ym) + yp) + zm) + zp;  lap = s - 6 p;
  *        q = (2 p - pm) + k lap;   then + source sample;  then * alpha in shut-down.
  *    Results are bit-for-bit reproducible and independent of scheduling.
  *  - Nodes outside the domain read as zero (zero Dirichlet boundary); the

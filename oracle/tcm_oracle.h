@@ -23,7 +23,7 @@
  * Conventions shared by both programs (each implements them independently):
  *  - Arrays are x fastest: index = (z*ny + y)*nx + x.
  *  - Eq. 3 is evaluated with one fixed grouping, every + - * rounded separately:
- *        s   = ((xm + xp) + (ym + yp)) + (zm + zp)
+ *        s   = ((((xm + xp) + ym) + yp) + zm) + zp
  *        lap = s - 6*p
  *        q   = (2*p - pm) + k*lap
  *    then each source whose insertion window covers step n adds w[n - start];

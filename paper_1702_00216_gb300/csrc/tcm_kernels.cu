@@ -114,7 +114,7 @@ __device__ __forceinline__ void store_meta(SlotMeta *p, const SlotMeta &m)
 __device__ __forceinline__ float eq3(float p, float pm, float k, float xm, float xp, float ym,
                                      float yp, float zm, float zp)
 {
-    const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+    const float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(xm, xp), ym), yp), zm), zp);
     const float lap = __fsub_rn(s, __fmul_rn(6.0f, p));
     return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, p), pm), __fmul_rn(k, lap));
 }

@@ -195,8 +195,10 @@ def test_mirror_symmetry_gpu():
     g.step(45)
     a = g.read_field(0)
     assert np.abs(a).max() > 0
-    for t in (a[::-1], a[:, ::-1], a[:, :, ::-1], a.transpose(0, 2, 1)):
-        assert np.array_equal(a, t)
+    # x reflection exact (xm + xp is the first sum); the others to rounding
+    assert np.array_equal(a, a[:, :, ::-1])
+    for t in (a[::-1], a[:, ::-1], a.transpose(0, 2, 1)):
+        assert np.abs(a - t).max() <= 1e-5 * np.abs(a).max()
 
 
 def test_empty_simulation():

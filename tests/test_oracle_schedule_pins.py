@@ -99,8 +99,8 @@ def test_schedule_arguments():
 
 def _eq3(a, b, k):
     p = np.pad(a, 1)
-    s = ((p[1:-1, 1:-1, :-2] + p[1:-1, 1:-1, 2:]) + (p[1:-1, :-2, 1:-1] + p[1:-1, 2:, 1:-1])) + \
-        (p[:-2, 1:-1, 1:-1] + p[2:, 1:-1, 1:-1])
+    s = ((((p[1:-1, 1:-1, :-2] + p[1:-1, 1:-1, 2:]) + p[1:-1, :-2, 1:-1]) + p[1:-1, 2:, 1:-1]) +
+         p[:-2, 1:-1, 1:-1]) + p[2:, 1:-1, 1:-1]
     return (F32(2) * a - b) + k * (s - F32(6) * a)
 
 
