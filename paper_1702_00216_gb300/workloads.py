@@ -221,6 +221,43 @@ def virtual(n: int = 4096, steps: int = 2500, pool_bytes: int = 120 * 2**30) -> 
                     thr_mode=1, tau=1e-6, decay_alpha=0.8, decay_steps=20, pool_bytes=pool_bytes)
 
 
+def gaussian_derivative(sigma: float, dt: float, t0: Optional[float] = None) -> np.ndarray:
+    """Bi-polar pulse: the derivative of a Gaussian, -(t - t0)/sigma * exp(-(t - t0)^2 /
+    (2 sigma^2)) at t = i*dt, t0 = 4 sigma, truncated after 2 t0 (peak 1/sqrt(e); FP64)."""
+    if t0 is None:
+        t0 = 4.0 * sigma
+    n = int(math.ceil(2.0 * t0 / dt))
+    t = np.arange(n, dtype=np.float64) * dt - t0
+    return -(t / sigma) * np.exp(-0.5 * (t / sigma) ** 2)
+
+
+def scatterer(shape=(64, 64, 112), steps: int = 260, beam_sigma: float = 5.0, pulse_sigma: float = 0.01,
+              threshold: float = 0.0) -> Workload:
+    """The sound-soft scatterer scenario of the stability study, scaled down: c = 340 m/s,
+    dx = 1 m, dt = 1e-3 s (Courant 0.34); a sphere beside a cube, both with c = 0 (k = 0,
+    so their nodes never leave zero); a directional Gaussian beam from the x- boundary:
+    point sources on the plane x = 2 with Gaussian weights (sigma = beam_sigma cells),
+    all fed the derivative of a Gaussian (sigma = pulse_sigma s)."""
+    nz, ny, nx = shape
+    c = np.full(shape, 340.0, dtype=np.float64)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cx, cy, cz, r = nx * 0.55, ny * 0.5, nz * 0.42, min(nx, ny, nz) * 0.14
+    c[(x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2 <= r * r] = 0.0
+    half = r * 0.9
+    cube = (np.abs(x - cx) <= half) & (np.abs(y - cy) <= half) & (z >= cz + r - 1) & (z <= cz + r - 1 + 2 * half)
+    c[cube] = 0.0
+    dt = 1e-3
+    w = gaussian_derivative(pulse_sigma, dt)
+    srcs = []
+    for yy in range(ny):
+        for zz in range(nz):
+            g = math.exp(-((yy - cy) ** 2 + (zz - cz) ** 2) / (2 * beam_sigma ** 2))
+            if g > 0.1:
+                srcs.append((2, yy, zz, w * g))
+    return Workload(f"scatterer-{nx}x{ny}x{nz}-beam", shape, dense_media(c), 1.0, dt, srcs, steps,
+                    thr_mode=1 if threshold > 0 else 0, tau=threshold)
+
+
 def precision(n: int = 256, steps: int = 800) -> Workload:
     """The layered, perturbed medium and settings of layered() on a 256^3 grid
     (the storage-precision comparison)."""
