@@ -236,7 +236,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "peak_source": peak_kind,
+                     "peak_source": peak_kind, "frac_of_nominal_8tbs": achieved / 8000.0,
                      "algorithmic_bytes_per_update": BYTES_PER_UPDATE,
                      "kernel": "k_step (persistent, one launch per step)"},
         "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -527,10 +527,27 @@ def cpu_baseline(W, args, budget_s: float = 15.0, wl=None):
         steps += 10
     dt = time.perf_counter() - t
     upd = o.updates
+    # the same oracle on one core, on the next steps of the run (all cores
+    # timed on a window of the same length first, so both rates cover
+    # comparable active sets)
+    single = None
+    if steps < TOTAL_STEPS - 20:
+        u0 = o.updates
+        t1 = time.perf_counter()
+        o.step(10)
+        all_rate = (o.updates - u0) / (time.perf_counter() - t1)
+        oracle.set_threads(1)
+        u1 = o.updates
+        t2 = time.perf_counter()
+        o.step(10)
+        single = {"value": (o.updates - u1) / (time.perf_counter() - t2), "cores": 1,
+                  "all_cores_same_window": all_rate,
+                  "sample": f"steps {steps + 10}..{steps + 20} on 1 core, {steps}..{steps + 10} on all"}
+        oracle.set_threads(threads)
     o.close()
     return {"value": upd / dt, "unit": "cell-updates/s", "cores": used, "kind": "oracle",
             "sample": f"{wl.name}: steps 0..{steps} of {TOTAL_STEPS} ({upd} cell updates, "
-                      f"{dt:.1f} s)"}
+                      f"{dt:.1f} s)", "single_thread": single}
 
 
 def run_reference(args, rank, world):
