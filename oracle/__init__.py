@@ -75,6 +75,9 @@ def lib():
             getattr(L, f"orc_tcm_status_{sfx}").argtypes = [_vp]
             getattr(L, f"orc_tcm_set_storage_{sfx}").argtypes = [_vp, C.c_int]
             getattr(L, f"orc_tcm_set_schedule_{sfx}").argtypes = [_vp, C.c_int, C.c_int]
+            getattr(L, f"orc_tcm_set_velocity_form_{sfx}").argtypes = [_vp, C.c_int]
+            getattr(L, f"orc_tcm_set_field_velocity_{sfx}").argtypes = [_vp, _vp, _vp]
+            getattr(L, f"orc_tcm_read_velocity_{sfx}").argtypes = [_vp, _i64, _i64, _i64, _i64, _i64, _i64, _vp]
             getattr(L, f"orc_tcm_set_lpf_{sfx}").argtypes = [_vp, _d, _d]
             getattr(L, f"orc_tcm_storage_scale_{sfx}").argtypes = [_vp]
             getattr(L, f"orc_tcm_storage_scale_{sfx}").restype = _d
@@ -221,7 +224,7 @@ class OracleTCM:
                  thr_mode: int = THR_ABSOLUTE, tau: float = 0.0, decay_alpha: float = 1.0,
                  decay_steps: int = 0, max_slots: int = 0, dense: bool = False,
                  dtype=np.float32, storage="f32", interval: int = 1, neighbours: int = 6,
-                 lpf=None):
+                 lpf=None, velocity=None):
         self.dtype = np.dtype(dtype)
         self._s = _sfx(dtype)
         self.shape = tuple(int(v) for v in shape)
@@ -256,6 +259,9 @@ class OracleTCM:
                                                                          int(neighbours)) != 0:
             self.close()
             raise ValueError("invalid update schedule")
+        if velocity is not None and self._f("set_velocity_form")(h, int(bool(velocity))) != 0:
+            self.close()
+            raise ValueError("velocity form not available here")
         if lpf is not None and self._f("set_lpf")(h, float(lpf[0]), float(lpf[1])) != 0:
             self.close()
             raise ValueError("invalid low-pass shut-down")
@@ -304,6 +310,21 @@ class OracleTCM:
                                    int(origin[2]), wx, wy, wz, _ptr(out))
         if rc != 0:
             raise RuntimeError(f"orc_tcm_read_field failed: {rc}")
+        return out
+
+    def set_field_velocity(self, now, v):
+        now = np.ascontiguousarray(now, dtype=self.dtype)
+        v = np.ascontiguousarray(v, dtype=self.dtype)
+        rc = self._f("set_field_velocity")(self._h, _ptr(now), _ptr(v))
+        if rc != 0:
+            raise RuntimeError(f"orc_tcm_set_field_velocity failed: {rc}")
+
+    def read_velocity(self) -> np.ndarray:
+        out = np.zeros(self.shape, dtype=self.dtype)
+        nz, ny, nx = self.shape
+        rc = self._f("read_velocity")(self._h, 0, 0, 0, nx, ny, nz, _ptr(out))
+        if rc != 0:
+            raise RuntimeError(f"orc_tcm_read_velocity failed: {rc}")
         return out
 
     def active_count(self):

@@ -154,8 +154,29 @@ int orc_tcm_set_field_f64(orc_tcm *t, const double *now, const double *prev);
  * 2^(e-1) <= m < 2^e and m is the largest |value| among the source samples
  * and initial fields at the first step (s = 1 when m = 0; e - 8 clamped to
  * [-100, 100]); BF16 and F32 use s = 1.  Only the _f32 program takes a
- * 16-bit storage (the _f64 one would round twice); it returns ORC_EINVAL. */
+ * 16-bit storage (the _f64 one would round twice); it returns ORC_EINVAL.
+ * A 16-bit storage also selects the velocity form (orc_tcm_set_velocity_form). */
 int orc_tcm_set_storage_f32(orc_tcm *t, int storage);
+/* Velocity form of the recursion (before the first step; on with any 16-bit
+ * storage, optional with F32 and F64): each box holds phi^n and v^n = phi^n -
+ * phi^{n-1} instead of phi^n and phi^{n-1}.  A step computes
+ * v' = v + k lap (lap as in Eq. 3), v' += w for a source node,
+ * phi^{n+1} = phi^n + v', and in shut-down phi^{n+1} *= alpha, v' = phi^{n+1} -
+ * phi^n; phi^{n+1} and v' are then written in the storage format.  In exact
+ * arithmetic it is Eq. 3; rounding a stored phi no longer acts on the
+ * velocity.  Initial fields give v^0 = phi^0 - phi^{-1} (before rounding);
+ * reading which = 1 returns phi^n - v^n; after an Eq. 7 filter v is set to the
+ * difference of the filtered levels. */
+int orc_tcm_set_velocity_form_f32(orc_tcm *t, int on);
+int orc_tcm_set_velocity_form_f64(orc_tcm *t, int on);
+/* Velocity form: initial phi^0 and v^0 directly (dense nx*ny*nz arrays),
+ * and a window of v^n (zeros where no box is allocated). */
+int orc_tcm_set_field_velocity_f32(orc_tcm *t, const float *now, const float *v);
+int orc_tcm_set_field_velocity_f64(orc_tcm *t, const double *now, const double *v);
+int orc_tcm_read_velocity_f32(const orc_tcm *t, int64_t x0, int64_t y0, int64_t z0,
+                              int64_t wx, int64_t wy, int64_t wz, float *out);
+int orc_tcm_read_velocity_f64(const orc_tcm *t, int64_t x0, int64_t y0, int64_t z0,
+                              int64_t wx, int64_t wy, int64_t wz, double *out);
 int orc_tcm_set_storage_f64(orc_tcm *t, int storage);
 /* The scale s in use (1 before the first step). */
 double orc_tcm_storage_scale_f32(const orc_tcm *t);

@@ -3,11 +3,14 @@ binary16, arithmetic in binary32).
 
 The rounding routines are pinned to independent library conversions (numpy's
 binary16 cast, torch's bfloat16 cast, both round to nearest even).  The
-storage form of the TCM program is pinned as a composition of pinned parts:
-one binary32 dense step of the oracle (pinned elsewhere against closed forms)
-followed by the library rounding, repeated step by step, must give the
-16-bit run bit for bit; at threshold 0 the 16-bit TCM must equal the 16-bit
-dense grid (the method skips only nodes that hold no wave, in any storage).
+16-bit storage uses the velocity form of Eq. 3 (phi^n and v^n = phi^n -
+phi^{n-1} per box).  Its algebra is pinned by equality to rounding with the
+leapfrog form (the plain Eq. 3, pinned elsewhere against closed forms) in
+binary64 and binary32; the storage form is pinned as a composition of pinned
+parts: one binary32 velocity-form step followed by the library rounding,
+repeated step by step, must give the 16-bit run bit for bit; at threshold 0
+the 16-bit TCM must equal the 16-bit dense grid (the method skips only nodes
+that hold no wave, in any storage).
 """
 import math
 
@@ -73,7 +76,8 @@ def dense_case():
 
 
 def composed_run(m, dt, storage, src, steps):
-    """binary32 dense step of the oracle, then library rounding, repeated."""
+    """binary32 velocity-form step of the oracle, then library rounding of
+    phi^{n+1} and v^{n+1}, repeated."""
     shape = m.c.shape
     x, y, z, w = src
     w = np.asarray(w, F32)
@@ -82,34 +86,55 @@ def composed_run(m, dt, storage, src, steps):
         e = math.frexp(float(np.max(np.abs(w))))[1] - 8
         scale = 2.0 ** e
     now = np.zeros(shape, F32)
-    prev = np.zeros(shape, F32)
+    v = np.zeros(shape, F32)
     for n in range(steps):
-        o = oracle.OracleTCM(shape, m, 1.0, dt, dense=True)
-        o.set_field(now, prev)
+        o = oracle.OracleTCM(shape, m, 1.0, dt, dense=True, velocity=True)
+        o.set_field_velocity(now, v)
         if n < len(w):
             o.add_source(x, y, z, w[n:n + 1])
         o.step(1)
-        q = o.read_field(0)
+        now, v = lib_round(o.read_field(0), storage, scale), lib_round(o.read_velocity(), storage, scale)
         o.close()
-        prev, now = now, lib_round(q, storage, scale)
-    return now, prev, scale
+    return now, v, scale
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (F32, 2e-5)])
+def test_velocity_form_equals_leapfrog_to_rounding(dtype, tol):
+    # the velocity form is Eq. 3 rearranged: equal to rounding in binary64 and
+    # binary32, so a dropped term or a wrong sign would show
+    m, dt = dense_case()
+    w = W.ricker(1 / 6, dt)
+    runs = []
+    for vel in (False, True):
+        o = oracle.OracleTCM(m.c.shape, m, 1.0, dt, dtype=dtype, velocity=vel, thr_mode=1, tau=1e-4,
+                             decay_alpha=0.8, decay_steps=4)
+        o.add_source(11, 9, 8, w)
+        o.step(90)
+        runs.append((o.read_field(0), o.read_field(1), o.active_bricks()))
+    (a0, a1, ia), (b0, b1, ib) = runs
+    g = np.abs(a0).max()
+    assert g > 0 and np.abs(a0 - b0).max() <= tol * g and np.abs(a1 - b1).max() <= tol * g
+    assert np.array_equal(ia, ib)
+    if dtype == F32:
+        assert not np.array_equal(a0, b0)          # not the same program
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
-def test_storage_run_equals_f32_step_then_library_rounding(storage):
+def test_storage_run_equals_velocity_step_then_library_rounding(storage):
     m, dt = dense_case()
     w = W.ricker(1 / 6, dt).astype(F32) * F32(3.7)
     src = (11, 9, 8, w)
     steps = 40
-    now, prev, scale = composed_run(m, dt, storage, src, steps)
+    now, v, scale = composed_run(m, dt, storage, src, steps)
     o = oracle.OracleTCM(m.c.shape, m, 1.0, dt, dense=True, storage=storage)
     o.add_source(*src[:3], w)
     o.step(steps)
     assert o.storage_scale == scale
     assert np.array_equal(o.read_field(0), now)
-    assert np.array_equal(o.read_field(1), prev)
+    assert np.array_equal(o.read_velocity(), v)
+    assert np.array_equal(o.read_field(1), (now - v).astype(F32))
     # and the rounding is really there: the binary32 run differs
-    o32 = oracle.OracleTCM(m.c.shape, m, 1.0, dt, dense=True)
+    o32 = oracle.OracleTCM(m.c.shape, m, 1.0, dt, dense=True, velocity=True)
     o32.add_source(*src[:3], w)
     o32.step(steps)
     assert not np.array_equal(o32.read_field(0), now)
@@ -141,12 +166,14 @@ def test_f16_scale_rule_and_initial_field_rounding():
     o.step(1)
     peak = float(max(np.abs(now).max(), np.abs(prev).max()))
     e = math.frexp(peak)[1] - 8
-    assert o.storage_scale == 2.0 ** e and 128 <= peak / 2.0 ** e < 256
-    # one step from the rounded initial fields
-    r = oracle.OracleTCM(m.c.shape, m, 1.0, dt)
-    r.set_field(lib_round(now, "f16", 2.0 ** e), lib_round(prev, "f16", 2.0 ** e))
+    s = 2.0 ** e
+    assert o.storage_scale == s and 128 <= peak / s < 256
+    # one velocity-form step from phi^0 and v^0 = phi^0 - phi^{-1}, each rounded
+    r = oracle.OracleTCM(m.c.shape, m, 1.0, dt, velocity=True)
+    r.set_field_velocity(lib_round(now, "f16", s), lib_round(now - prev, "f16", s))
     r.step(1)
-    assert np.array_equal(o.read_field(0), lib_round(r.read_field(0), "f16", 2.0 ** e))
+    assert np.array_equal(o.read_field(0), lib_round(r.read_field(0), "f16", s))
+    assert np.array_equal(o.read_velocity(), lib_round(r.read_velocity(), "f16", s))
 
 
 def test_f64_program_refuses_16bit_storage():
