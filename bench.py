@@ -430,7 +430,7 @@ def precision_leg(torch, tcm, W, dev, local_rank):
         buf = torch.empty(wl.shape, dtype=torch.float32, device=dev)
         tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
         torch.cuda.synchronize()
-        bpu = 16 if st == "f32" else 10
+        bpu = 16 if st == "f32" else 12   # 16-bit: read phi, v (2 B each), k (4 B); write phi, v
         r = {"updates_per_s": upd / (ms / 1e3), "ms": ms, "bytes_per_update": bpu,
              "hbm_gbs": upd * bpu / (ms / 1e3) / 1e9,
              "energy_drift": abs(en_b - en_a) / abs(en_a) if en_a else None}

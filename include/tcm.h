@@ -54,11 +54,16 @@ typedef enum {
 
 enum { TCM_MEDIA_DENSE = 0, TCM_MEDIA_RULES = 1 };
 enum { TCM_THR_ABSOLUTE = 0, TCM_THR_RELATIVE = 1 };
-/* Field storage in the pool.  F32: binary32.  BF16 / F16: bfloat16 or IEEE
- * binary16 holding phi / s, with s a power of two per simulation (1 for BF16;
- * for F16 chosen when the simulation starts so that its largest source sample
- * or initial value is stored in [128, 256)).  Every storage computes Eq. 3 in
- * binary32 with binary32 k; values are rounded to nearest-even on store. */
+/* Field storage in the pool.  F32: binary32, a box holds phi^n and phi^{n-1}.
+ * BF16 / F16: bfloat16 or IEEE binary16 holding value / s, with s a power of
+ * two per simulation (1 for BF16; for F16 chosen when the simulation starts
+ * so that its largest source sample or initial value is stored in
+ * [128, 256)); a box holds phi^n, the phi^{n+1} being written and
+ * v^n = phi^n - phi^{n-1} (the velocity form of Eq. 3: v' = v + k lap,
+ * phi^{n+1} = phi^n + v', so rounding a stored phi does not act on the
+ * velocity).  Every storage computes in binary32 with binary32 k; values are
+ * rounded to nearest-even on store.  With 16-bit storage, reading phi^{n-1}
+ * returns phi^n - v^n (binary32). */
 enum { TCM_STORAGE_F32 = 0, TCM_STORAGE_BF16 = 1, TCM_STORAGE_F16 = 2 };
 
 typedef struct {
@@ -105,8 +110,9 @@ typedef struct {
                            and replayed (same kernels, same results) */
 } tcm_options;
 
-/* Bytes of pool one box takes for this brick shape and storage (two field
- * halves).  TCM_EINVAL for unsupported shapes. */
+/* Bytes of pool one box takes for this brick shape and storage (binary32:
+ * two field arrays of 4 B per node; 16-bit: three arrays of 2 B per node).
+ * TCM_EINVAL for unsupported shapes or storages. */
 tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out);
 
 /* Create a simulation (Cells construction, Media / HBM bulking, Boxes).

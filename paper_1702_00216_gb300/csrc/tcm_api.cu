@@ -314,7 +314,7 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
 {
     *out = nullptr;
     if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16) return TCM_EINVAL;
-    const size_t slot_bytes = (size_t)2 * BVOL * storage_bytes(storage);
+    const size_t slot_bytes = (size_t)slot_elems(storage) * storage_bytes(storage);
     const long long n_slots_ll = (long long)(pool_bytes / slot_bytes);
     if (n_slots_ll < 1 || max_bricks < 1 || max_sims < 1 || max_sims > 65535) return TCM_EINVAL;
     if (pool_ptr && reinterpret_cast<uintptr_t>(pool_ptr) % 16 != 0) return TCM_EINVAL;
@@ -703,7 +703,9 @@ tcm_status sim_prime(tcm_batch *b, int id)
                 if (x >= h.nx || y >= h.ny || z >= h.nz) continue;
                 const size_t i0 = (size_t)((z * h.ny + y) * h.nx + x);
                 packed[(size_t)(i * 2 * bvol + e)] = h.init_now[i0];
-                packed[(size_t)(i * 2 * bvol + bvol + e)] = h.init_prev[i0];
+                // binary32: phi^{-1}; velocity form (16-bit): v^0 = phi^0 - phi^{-1}
+                packed[(size_t)(i * 2 * bvol + bvol + e)] =
+                    b->E.storage == ST_F32 ? h.init_prev[i0] : h.init_now[i0] - h.init_prev[i0];
             }
         }
         float *d_packed = nullptr;
@@ -975,7 +977,7 @@ tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out)
 {
     if (!out || brick.bx != BX || brick.by != BY || brick.bz != BZ) return TCM_EINVAL;
     if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16) return TCM_EINVAL;
-    *out = (size_t)2 * BVOL * storage_bytes(storage);
+    *out = (size_t)slot_elems(storage) * storage_bytes(storage);
     return TCM_OK;
 }
 
@@ -1149,8 +1151,8 @@ tcm_status tcm_read_field_device(const tcm_sim *cs, int which, int64_t x0, int64
     tcm_batch *b = cs->b;
     DeviceGuard g(b->device);
     TRYS(ready_for_read(b, cs->id));
-    const int half = which == 0 ? (int)(h->step & 1) : (int)((h->step + 1) & 1);
-    TRY(launch_read_window(b->E, cs->id, half, x0, y0, z0, wx, wy, wz, device_out, b->stream));
+    TRY(launch_read_window(b->E, cs->id, (int)(h->step & 1), which, x0, y0, z0, wx, wy, wz, device_out,
+                           b->stream));
     return TCM_OK;
 }
 

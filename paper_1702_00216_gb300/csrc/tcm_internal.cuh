@@ -58,6 +58,11 @@ enum { MEDIA_DENSE = 0, MEDIA_RULES = 1 };
 // phi / scale (scale a power of two per simulation; compute is binary32).
 enum { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
 __host__ __device__ constexpr int storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
+// Elements per box: the two field halves (phi^n, phi^{n-1}) in binary32; with
+// a 16-bit storage the velocity form keeps the two phi halves (phi^n and the
+// phi^{n+1} being written) plus v^n = phi^n - phi^{n-1} as a third array.
+__host__ __device__ constexpr int slot_elems(int st) { return st == ST_F32 ? 2 * BVOL : 3 * BVOL; }
+constexpr int V_HALF = 2;   // index of the v array in a 16-bit box
 
 struct __align__(16) SlotMeta {
     int brick;       // local brick id within its sim (Box2cell)
@@ -144,7 +149,7 @@ constexpr int lpf_pow2(int v) { return v <= 1 ? 1 : 2 * lpf_pow2((v + 1) / 2); }
 constexpr int LPF_M = lpf_pow2(2 * LPF_L);   // at least 2x oversampling
 
 struct Engine {
-    void *phi;             // pool: 2 * BVOL elements of `storage` per box
+    void *phi;             // pool: slot_elems(storage) elements of `storage` per box
     int storage;
     int n_slots;
     int *slot_of_brick;
@@ -188,10 +193,11 @@ struct MediaDev {
     const float *sph_c;
 };
 
-// Element e of box half (slot, half), as a physical value (x scale).
+// Element e of box array (slot, half) -- half 0/1 a field half, V_HALF the
+// velocity (16-bit storages) -- as a physical value (x scale).
 __device__ __forceinline__ float load_phys(const Engine &E, int slot, int half, int e, float scale)
 {
-    const size_t i = ((size_t)slot * 2 + half) * BVOL + e;
+    const size_t i = (size_t)slot * slot_elems(E.storage) + (size_t)half * BVOL + e;
     if (E.storage == ST_F32) return static_cast<const float *>(E.phi)[i] * scale;
     const unsigned short bits = static_cast<const unsigned short *>(E.phi)[i];
     if (E.storage == ST_BF16) return __uint_as_float((unsigned)bits << 16) * scale;
@@ -201,11 +207,19 @@ __device__ __forceinline__ float load_phys(const Engine &E, int slot, int half, 
 // Store a physical value v into element e of box half (slot, half).
 __device__ __forceinline__ void store_phys(const Engine &E, int slot, int half, int e, float v, float inv_scale)
 {
-    const size_t i = ((size_t)slot * 2 + half) * BVOL + e;
+    const size_t i = (size_t)slot * slot_elems(E.storage) + (size_t)half * BVOL + e;
     const float s = v * inv_scale;
     if (E.storage == ST_F32) static_cast<float *>(E.phi)[i] = s;
     else if (E.storage == ST_BF16) static_cast<__nv_bfloat16 *>(E.phi)[i] = __float2bfloat16_rn(s);
     else static_cast<__half *>(E.phi)[i] = __float2half_rn(s);
+}
+
+// phi^{n-1} at element e of a box whose phi^n is in half now_half: the other
+// half in binary32; phi^n - v^n (binary32 subtraction) in the velocity form.
+__device__ __forceinline__ float load_prev_phys(const Engine &E, int slot, int now_half, int e, float scale)
+{
+    if (E.storage == ST_F32) return load_phys(E, slot, now_half ^ 1, e, scale);
+    return __fsub_rn(load_phys(E, slot, now_half, e, scale), load_phys(E, slot, V_HALF, e, scale));
 }
 
 // ---- launchers (tcm_kernels.cu) -------------------------------------------
@@ -238,7 +252,7 @@ cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaS
 cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s);
 int lpf_grid_size(int device);
 int step_grid_size(int device);
-cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
+cudaError_t launch_read_window(const Engine &e, int sim, int now_half, int which, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,
                                cudaStream_t s);
 cudaError_t launch_energy(const Engine &e, int sim, int now_half, int list_parity, double *out,

@@ -119,6 +119,26 @@ __device__ __forceinline__ float eq3(float p, float pm, float k, float xm, float
     return __fadd_rn(__fsub_rn(__fmul_rn(2.0f, p), pm), __fmul_rn(k, lap));
 }
 
+// Velocity form (16-bit storages): v + k lap, the same lap as eq3.
+__device__ __forceinline__ float vel3(float p, float v, float k, float xm, float xp, float ym, float yp, float zm,
+                                      float zp)
+{
+    const float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(xm, xp), ym), yp), zm), zp);
+    const float lap = __fsub_rn(s, __fmul_rn(6.0f, p));
+    return __fadd_rn(v, __fmul_rn(k, lap));
+}
+
+__device__ __forceinline__ float4 vel3v(float4 p, float4 v, float4 k, float xm0, float xp3, float4 ym, float4 yp,
+                                        float4 zm, float4 zp)
+{
+    float4 q;
+    q.x = vel3(p.x, v.x, k.x, xm0, p.y, ym.x, yp.x, zm.x, zp.x);
+    q.y = vel3(p.y, v.y, k.y, p.x, p.z, ym.y, yp.y, zm.y, zp.y);
+    q.z = vel3(p.z, v.z, k.z, p.y, p.w, ym.z, yp.z, zm.z, zp.z);
+    q.w = vel3(p.w, v.w, k.w, p.z, xp3, ym.w, yp.w, zm.w, zp.w);
+    return q;
+}
+
 __device__ __forceinline__ float4 eq3v(float4 p, float4 pm, float4 k, float xm0, float xp3, float4 ym,
                                        float4 yp, float4 zm, float4 zp)
 {
@@ -271,18 +291,19 @@ struct Fld<ST_F16> {
     static __device__ __forceinline__ void st(T *p, V v) { __stcg(reinterpret_cast<uint2 *>(p), v); }
 };
 
+// Array `half` of a box: 0/1 the field halves, V_HALF the velocity (16-bit).
 template <int ST>
 __device__ __forceinline__ typename Fld<ST>::T *half_ptr(const Engine &E, int slot, int half)
 {
-    return static_cast<typename Fld<ST>::T *>(E.phi) + ((size_t)slot * 2 + half) * BVOL;
+    return static_cast<typename Fld<ST>::T *>(E.phi) + (size_t)slot * slot_elems(ST) + (size_t)half * BVOL;
 }
 
-// Zero one box (both halves) with the lanes of a warp.
+// Zero one box (every array of it) with the lanes of a warp.
 __device__ __forceinline__ void zero_box(const Engine &E, int slot, int lane)
 {
-    const int n16 = 2 * BVOL * storage_bytes(E.storage) / 16;
-    float4 *p = reinterpret_cast<float4 *>(static_cast<unsigned char *>(E.phi) +
-                                           (size_t)slot * 2 * BVOL * storage_bytes(E.storage));
+    const size_t bytes = (size_t)slot_elems(E.storage) * storage_bytes(E.storage);
+    const int n16 = (int)(bytes / 16);
+    float4 *p = reinterpret_cast<float4 *>(static_cast<unsigned char *>(E.phi) + (size_t)slot * bytes);
     for (int e = lane; e < n16; e += 32) p[e] = f4zero();
 }
 
@@ -341,7 +362,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const int xs2 = (XQ == 1 && valid && !share_xp) ? w.nb[1] : -1;
     if (valid) {
         const typename F::T *now = half_ptr<ST>(E, w.slot, nh);
-        const typename F::T *prv = half_ptr<ST>(E, w.slot, nh ^ 1);
+        // phi^{n-1} in binary32; v^n in the velocity form (16-bit storages)
+        const typename F::T *prv = half_ptr<ST>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF);
 #pragma unroll
         for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), sc);
 #pragma unroll
@@ -397,6 +419,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const bool ragged = (cx + 1) * BX > nx || (cy + 1) * BY > ny || (cz + 1) * BZ > nz;
     const int gx0 = cx * BX + 4 * x4, gy = cy * BY + y, gz0 = cz * BZ;
     typename F::T *out = half_ptr<ST>(E, w.slot, nh ^ 1);
+    typename F::T *vout = half_ptr<ST>(E, w.slot, V_HALF);   // used by 16-bit storages only
     const bool src = valid && (w.flags & FLAG_HAS_SRC);
     const long long step = src ? __ldcg(&S->step) : 0;
     const bool xrecv = (x4 == 0 && share_xm) || (x4 == XQ - 1 && share_xp);
@@ -440,7 +463,12 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         if (y == BY - 1) yp = YH[z];
         const float4 zm = (z > 0) ? P[z > 0 ? z - 1 : 0] : Zm;
         const float4 zp = (z < BZ - 1) ? P[z < BZ - 1 ? z + 1 : 0] : Zp;
-        float4 q = eq3v(p, M[z], K[z], xm0, xp3, ym, yp, zm, zp);
+        // binary32: q = phi^{n+1} by Eq. 3.  Velocity form: vq = v + k lap
+        // (+ source), then q = phi^n + vq.
+        float4 q, vq;
+        if constexpr (ST == ST_F32) q = eq3v(p, M[z], K[z], xm0, xp3, ym, yp, zm, zp);
+        else vq = vel3v(p, M[z], K[z], xm0, xp3, ym, yp, zm, zp);
+        float4 &acc = (ST == ST_F32) ? q : vq;
         if (src) {
             // Source insertion in box coordinates: every sample of this
             // plane, in source order.
@@ -451,14 +479,26 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
                 if (tt < 0 || tt >= sd.len) continue;
                 const int lx = sd.local % BX, ly = (sd.local / BX) % BY, lz = sd.local / (BX * BY);
                 if (lz != z || ly != y || (lx >> 2) != x4) continue;
-                add_comp(q, lx & 3, E.wave[sd.w_off + tt]);
+                add_comp(acc, lx & 3, E.wave[sd.w_off + tt]);
             }
+        }
+        if constexpr (ST != ST_F32) {
+            q.x = __fadd_rn(p.x, vq.x);
+            q.y = __fadd_rn(p.y, vq.y);
+            q.z = __fadd_rn(p.z, vq.z);
+            q.w = __fadd_rn(p.w, vq.w);
         }
         if (decay) {
             q.x = __fmul_rn(alpha, q.x);
             q.y = __fmul_rn(alpha, q.y);
             q.z = __fmul_rn(alpha, q.z);
             q.w = __fmul_rn(alpha, q.w);
+            if constexpr (ST != ST_F32) {
+                vq.x = __fsub_rn(q.x, p.x);
+                vq.y = __fsub_rn(q.y, p.y);
+                vq.z = __fsub_rn(q.z, p.z);
+                vq.w = __fsub_rn(q.w, p.w);
+            }
         }
         if (ragged) {
             const bool rowin = gy < ny && gz0 + z < nz;
@@ -466,12 +506,23 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
             if (!rowin || gx0 + 1 >= nx) q.y = 0.f;
             if (!rowin || gx0 + 2 >= nx) q.z = 0.f;
             if (!rowin || gx0 + 3 >= nx) q.w = 0.f;
+            if constexpr (ST != ST_F32) {
+                if (!rowin || gx0 + 0 >= nx) vq.x = 0.f;
+                if (!rowin || gx0 + 1 >= nx) vq.y = 0.f;
+                if (!rowin || gx0 + 2 >= nx) vq.z = 0.f;
+                if (!rowin || gx0 + 3 >= nx) vq.w = 0.f;
+            }
         }
         // phi^{n+1} is what the storage holds: maxima and thresholds see the
         // stored (rounded) value.
         typename F::V qs;
         q = F::rnd(q, sc, isc, qs);
         if (valid) F::st(out + 4 * (z * TPB + t), qs);
+        if constexpr (ST != ST_F32) {
+            typename F::V vs;
+            F::rnd(vq, sc, isc, vs);
+            if (valid) F::st(vout + 4 * (z * TPB + t), vs);
+        }
         const float mq = max4abs(q);
         qm = fmaxf(qm, mq);
         mc = fmaxf(mc, fmaxf(mq, max4abs(p)));
@@ -1379,14 +1430,15 @@ __global__ void k_scatter_field(Engine E, const float *packed, const long long *
         const long long bi = i / (2 * BVOL);
         const int r = (int)(i % (2 * BVOL));
         const int which = r / BVOL, e = r % BVOL;
-        const int half = which == 0 ? now_half : (now_half ^ 1);
+        // the second array is phi^{-1} in binary32, v^0 in the velocity form
+        const int half = which == 0 ? now_half : (E.storage == ST_F32 ? (now_half ^ 1) : V_HALF);
         const long long g = gids[bi];
         const int slot = E.slot_of_brick[g];
         if (slot >= 0) store_phys(E, slot, half, e, packed[i], E.sims[E.sim_of_word[g >> 5]].inv_scale);
     }
 }
 
-__global__ void k_read_window(Engine E, int sim, int half, long long x0, long long y0, long long z0,
+__global__ void k_read_window(Engine E, int sim, int now_half, int which, long long x0, long long y0, long long z0,
                               long long wx, long long wy, long long wz, float *out)
 {
     const SimDev *S = E.sims + sim;
@@ -1399,7 +1451,8 @@ __global__ void k_read_window(Engine E, int sim, int half, long long x0, long lo
             const int slot = E.slot_of_brick[S->brick_base + b];
             if (slot >= 0) {
                 const int e = (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX));
-                v = load_phys(E, slot, half, e, S->scale);
+                v = which == 0 ? load_phys(E, slot, now_half, e, S->scale)
+                               : load_prev_phys(E, slot, now_half, e, S->scale);
             }
         }
         out[i] = v;
@@ -1407,14 +1460,14 @@ __global__ void k_read_window(Engine E, int sim, int half, long long x0, long lo
 }
 
 // phi^{n-1} at global node (x,y,z) of sim, zero outside or when inactive.
-__device__ __forceinline__ double prev_at(const Engine &E, const SimDev *S, int prev_half, long long x,
+__device__ __forceinline__ double prev_at(const Engine &E, const SimDev *S, int now_half, long long x,
                                           long long y, long long z)
 {
     if (x < 0 || y < 0 || z < 0 || x >= S->nx || y >= S->ny || z >= S->nz) return 0.0;
     const long long b = ((z / BZ) * S->my + (y / BY)) * S->mx + (x / BX);
     const int slot = E.slot_of_brick[S->brick_base + b];
     if (slot < 0) return 0.0;
-    return (double)load_phys(E, slot, prev_half, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
+    return (double)load_prev_phys(E, slot, now_half, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
 }
 
 __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *out)
@@ -1422,7 +1475,6 @@ __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *ou
     const SimDev *S = E.sims + sim;
     const WorkItem *L = parity ? E.items1 : E.items0;
     const long long n = (long long)E.st->n_active[parity] * BVOL;
-    const int ph = now_half ^ 1;
     double acc = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int slot = L[i / BVOL].slot;
@@ -1435,10 +1487,11 @@ __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *ou
         const long long z = (long long)(b / (S->mx * S->my)) * BZ + e / (BX * BY);
         if (x >= S->nx || y >= S->ny || z >= S->nz) continue;
         const double a = (double)load_phys(E, slot, now_half, e, S->scale);
-        const double bb = (double)load_phys(E, slot, ph, e, S->scale);
-        const double nb = prev_at(E, S, ph, x - 1, y, z) + prev_at(E, S, ph, x + 1, y, z) +
-                          prev_at(E, S, ph, x, y - 1, z) + prev_at(E, S, ph, x, y + 1, z) +
-                          prev_at(E, S, ph, x, y, z - 1) + prev_at(E, S, ph, x, y, z + 1);
+        const double bb = (double)load_prev_phys(E, slot, now_half, e, S->scale);
+        const int nh = now_half;
+        const double nb = prev_at(E, S, nh, x - 1, y, z) + prev_at(E, S, nh, x + 1, y, z) +
+                          prev_at(E, S, nh, x, y - 1, z) + prev_at(E, S, nh, x, y + 1, z) +
+                          prev_at(E, S, nh, x, y, z - 1) + prev_at(E, S, nh, x, y, z + 1);
         const double k = m.kslab >= 0 ? (double)S->kslabs[(size_t)m.kslab * BVOL + e] : (double)m.kscal;
         const double d = a - bb;
         acc += d * d / k + a * (6.0 * bb - nb);
@@ -1654,10 +1707,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
         }
     }
     if (!grid_barrier(st, &st->bar_count_lpf)) return;
-    // (C) write back
-    for (long long i = gtid; i < (long long)naff * 2 * BVOL; i += nthr) {
-        const int c = (int)(i / (2 * BVOL)), e = (int)(i % (2 * BVOL));
-        const int h = e / BVOL, loc = e % BVOL;
+    // (C) write back, one node (both levels) per thread; in the velocity
+    // form v becomes the difference of the two stored filtered levels
+    for (long long i = gtid; i < (long long)naff * BVOL; i += nthr) {
+        const int c = (int)(i / BVOL), loc = (int)(i % BVOL);
         const long long g = E.lpf_aff[c];
         const SimDev *S = E.sims + E.sim_of_word[g >> 5];
         const int b = (int)(g - S->brick_base);
@@ -1666,8 +1719,15 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
         const int x = (b % mx) * BX + loc % BX, y = ((b / mx) % my) * BY + (loc / BX) % BY,
                   z = (b / (mx * my)) * BZ + loc / (BX * BY);
         const bool in = x < S->nx && y < S->ny && z < S->nz;
-        store_phys(E, slot, h, loc, in ? E.lpf_out[i] : 0.f, S->inv_scale);
-        if (e == 0) E.lpf_mark[slot] = 0;
+        const size_t o = (size_t)c * 2 * BVOL + loc;
+        store_phys(E, slot, 0, loc, in ? E.lpf_out[o] : 0.f, S->inv_scale);
+        store_phys(E, slot, 1, loc, in ? E.lpf_out[o + BVOL] : 0.f, S->inv_scale);
+        if (E.storage != ST_F32) {
+            const int nh = (int)(__ldcg(&S->step) & 1);   // the half holding phi^{n+1}
+            const float sn = load_phys(E, slot, nh, loc, S->scale), so = load_phys(E, slot, nh ^ 1, loc, S->scale);
+            store_phys(E, slot, V_HALF, loc, __fsub_rn(sn, so), S->inv_scale);
+        }
+        if (loc == 0) E.lpf_mark[slot] = 0;
     }
 }
 
@@ -1716,13 +1776,13 @@ cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaS
     return launch_cooperative(fn, grid, 0, args, s);
 }
 
-cudaError_t launch_read_window(const Engine &e, int sim, int half, long long x0, long long y0,
+cudaError_t launch_read_window(const Engine &e, int sim, int now_half, int which, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,
                                cudaStream_t s)
 {
     const long long n = wx * wy * wz;
     if (n <= 0) return cudaSuccess;
-    k_read_window<<<grid_for(n, 256), 256, 0, s>>>(e, sim, half, x0, y0, z0, wx, wy, wz, out);
+    k_read_window<<<grid_for(n, 256), 256, 0, s>>>(e, sim, now_half, which, x0, y0, z0, wx, wy, wz, out);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ static __device__ __align__(256) double g_energy_partials[NOALLOC_MAX_BRICKS];
 double *g_partials_addr[NOALLOC_MAX_DEVICES] = {};
 
 // phi^{n-1} at a global node of the sim, zero outside or when inactive.
-__device__ __forceinline__ double prev_node(const tcm::Engine &E, const tcm::SimDev *S, int ph,
+__device__ __forceinline__ double prev_node(const tcm::Engine &E, const tcm::SimDev *S, int now_half,
                                             long long x, long long y, long long z)
 {
     using namespace tcm;
@@ -37,7 +37,8 @@ __device__ __forceinline__ double prev_node(const tcm::Engine &E, const tcm::Sim
     const long long b = ((z / BZ) * S->my + (y / BY)) * S->mx + (x / BX);
     const int slot = E.slot_of_brick[S->brick_base + b];
     if (slot < 0) return 0.0;
-    return (double)load_phys(E, slot, ph, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
+    return (double)load_prev_phys(E, slot, now_half, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)),
+                                  S->scale);
 }
 
 // One warp per active brick: its energy contribution, reduced in a fixed
@@ -48,7 +49,7 @@ __global__ void k_energy_partials(tcm::Engine E, int sim, int now_half, int pari
     const int lane = threadIdx.x & 31;
     const WorkItem *L = parity ? E.items1 : E.items0;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int ph = now_half ^ 1;
+    const int ph = now_half;   // prev_node derives phi^{n-1} from the half holding phi^n
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const int slot = L[i].slot;
         const int4 mv = *reinterpret_cast<const int4 *>(E.meta + slot);
@@ -66,7 +67,7 @@ __global__ void k_energy_partials(tcm::Engine E, int sim, int now_half, int pari
             const long long x = bx0 + e % BX, y = by0 + (e / BX) % BY, z = bz0 + e / (BX * BY);
             if (x >= S->nx || y >= S->ny || z >= S->nz) continue;
             const double a = (double)load_phys(E, slot, now_half, e, S->scale);
-            const double bb = (double)load_phys(E, slot, ph, e, S->scale);
+            const double bb = (double)load_prev_phys(E, slot, now_half, e, S->scale);
             const double nb = prev_node(E, S, ph, x - 1, y, z) + prev_node(E, S, ph, x + 1, y, z) +
                               prev_node(E, S, ph, x, y - 1, z) + prev_node(E, S, ph, x, y + 1, z) +
                               prev_node(E, S, ph, x, y, z - 1) + prev_node(E, S, ph, x, y, z + 1);

@@ -76,10 +76,10 @@ def test_16bit_threshold0_equals_dense(storage):
 
 @pytest.mark.parametrize("storage,bound", [("bf16", 6e-2), ("f16", 1e-2)])
 def test_16bit_error_against_fp64(storage, bound):
-    # Layered 48^3, 200 steps.  The rounding of phi^{n+1} to 8 (bf16) or 11
+    # Layered 48^3, 200 steps.  Rounding phi^{n+1} and v to 8 (bf16) or 11
     # (f16) significant bits each step leaves max|error| / max|phi| of about
-    # 3.3e-2 and 4.9e-3 (the storage form of the oracle gives the same
-    # numbers); the bounds allow 2x.
+    # 2.3e-2 and 3.1e-3 (the storage form of the oracle gives the same
+    # numbers); the bounds allow 2x or more.
     n, steps = 48, 200
     m = W.Media(kind="rules", c_background=1.0, layers=[(n * 0.5, 1.6)])
     dt = 0.5 / m.c_max()
@@ -159,9 +159,10 @@ def test_precision_workload_error_against_fp64_dense(capsys):
     with capsys.disabled():
         print("\nprecision 256^3 x 800 vs FP64 dense (max rel, rms rel):",
               {k_: tuple(float(f"{v:.3e}") for v in e) for k_, e in errs.items()})
-    # measured: f32 6.5e-6, f16 1.4e-2, bf16 0.45 (max rel).  The leapfrog
-    # recursion turns each rounding of phi^{n+1} into a velocity kick, so the
-    # error of a 16-bit store grows with the steps per period (~50 here).
+    # measured: f32 6.5e-6, f16 5.7e-3, bf16 4.1e-2 (max rel) with the
+    # velocity form (phi and v = phi^n - phi^{n-1} stored); storing phi^n and
+    # phi^{n-1} in 16 bits gave 1.4e-2 and 0.45, because each rounding of
+    # phi^{n+1} then acts as a velocity kick.  Bounds: 2x the measurements.
     assert errs["f32"][0] < 1e-4
-    assert errs["f16"][0] < 3e-2 and errs["bf16"][0] < 0.9
-    assert errs["f16"][0] < errs["bf16"][0] / 8
+    assert errs["f16"][0] < 1.2e-2 and errs["bf16"][0] < 8e-2
+    assert errs["f16"][0] < errs["bf16"][0] / 4

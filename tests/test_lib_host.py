@@ -46,8 +46,9 @@ def test_slot_bytes(lib):
     # every supported shape, every storage (two halves per box)
     for brick, n in (((4, 4, 4), 64), ((8, 8, 8), 512), ((16, 8, 8), 1024)):
         assert tcm.tcm_slot_bytes(brick, tcm.TCM_STORAGE_F32) == 2 * n * 4
-        assert tcm.tcm_slot_bytes(brick, tcm.TCM_STORAGE_BF16) == 2 * n * 2
-        assert tcm.tcm_slot_bytes(brick, tcm.TCM_STORAGE_F16) == 2 * n * 2
+        # 16-bit: two field halves plus the velocity array
+        assert tcm.tcm_slot_bytes(brick, tcm.TCM_STORAGE_BF16) == 3 * n * 2
+        assert tcm.tcm_slot_bytes(brick, tcm.TCM_STORAGE_F16) == 3 * n * 2
     for bad in ((8, 8, 16), (4, 4, 8), (2, 2, 2)):
         with pytest.raises(tcm.TCMError):
             tcm.tcm_slot_bytes(bad)
