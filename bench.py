@@ -120,6 +120,18 @@ def profiled_traffic(updates_per_launch: float):
     return float(d["dram_bytes_per_update"]) * updates_per_launch
 
 
+def job_totals(torch, total_ms: float, updates: int, world: int, dev):
+    """Whole-job figures over the replicas: the slowest rank's time (max) and
+    the node updates of all ranks (sum); the identity on one rank."""
+    if world <= 1:
+        return total_ms, float(updates)
+    tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    uu = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(uu)
+    return float(tt.item()), float(uu.item())
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -183,15 +195,7 @@ def run_ours(args, rank, world, local_rank):
     ph = [b - a for a, b in zip(ph0, sim.phase_ns())]
     active_end = sim.active_count()
 
-    t_max = total_ms
-    upd_all = updates
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-        uu = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(uu)
-        upd_all = float(uu.item())
+    t_max, upd_all = job_totals(torch, total_ms, updates, world, dev)
     value = upd_all / (t_max / 1e3)
 
     peaks, peak_kind = measured_peaks()
