@@ -604,31 +604,40 @@ __device__ __forceinline__ int agg_add_n(int *ctr, int n)
     return base + incl - n;
 }
 
-// Trigger up to six bricks of one sim (Boxes: "Boxing new cells in vacant
+// Trigger up to N bricks of one sim (Boxes: "Boxing new cells in vacant
 // boxes"): claim each with a CAS on Cell2box (-1 -> -2; another thread may
-// be boxing it), pop one vacant box per claim won, then publish.  The
-// steps are batched so the thread waits for each kind of atomic once.
+// be boxing it), pop one vacant box per claim won, then publish.  All a new
+// box's record needs (the vacant box, coefficients, has-source bit from the
+// shut-down word) loads in one round after the reservation, so a won claim
+// costs three rounds of dependent accesses: the CAS, the reservation, those
+// loads.  The shut-down word of an unboxed brick is written only by the
+// thread that wins its claim.
 template <int N>
 __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_local, int n)
 {
+    static_assert(N <= 32, "one bit per candidate");
     const long long bb = S->brick_base;
-    bool won[N];
-    int nw = 0;
+    const int step = (int)__ldcg(&S->step);
+    unsigned won = 0;
 #pragma unroll
-    for (int i = 0; i < N; ++i) won[i] = i < n && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1;
-#pragma unroll
-    for (int i = 0; i < N; ++i) nw += won[i] ? 1 : 0;
-    if (nw == 0) return;
+    for (int i = 0; i < N; ++i)
+        if (i < n && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1) won |= 1u << i;
+    if (won == 0) return;
+    const int nw = __popc(won);
     // vacant boxes free_stack[top - nw .. top - 1]
     const int top = atomicSub(&E.st->free_top, nw);
     const int nn = agg_add_n(&E.st->n_new, nw);
     int k = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        if (!won[i]) continue;
+        if (!(won >> i & 1u)) continue;
         const long long g = bb + b_local[i];
+        const int kslab = __ldg(E.kslab_of_brick + g);
+        const float kscal = __ldg(E.kscal + g);
+        const unsigned short sdw = __ldcg(E.sd_of_brick + g);
         const int idx = top - 1 - k;
-        if (idx < 0) {
+        const int ns = idx >= 0 ? __ldcg(E.free_stack + idx) : -1;
+        if (ns < 0) {   // no vacant box left
             atomicExch(E.slot_of_brick + g, -1);
             atomicOr(&E.st->err, ERR_NOMEM);
             atomicOr(&S->poisoned, 1u);
@@ -636,15 +645,14 @@ __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_l
             ++k;
             continue;
         }
-        const int ns = __ldcg(E.free_stack + idx);
-        E.claim_step[ns] = (int)__ldcg(&S->step);
+        E.claim_step[ns] = step;
         SlotMeta m;
         m.brick = b_local[i];
-        m.kslab = E.kslab_of_brick[g];
-        m.kscal = E.kscal[g];
-        m.flags = ((unsigned)sim << 16) | (brick_has_src(E, S, b_local[i]) ? FLAG_HAS_SRC : 0u);
+        m.kslab = kslab;
+        m.kscal = kscal;
+        m.flags = ((unsigned)sim << 16) | (sdw & FLAG_HAS_SRC);
         store_meta(E.meta + ns, m);
-        E.sd_of_brick[g] &= (unsigned short)FLAG_HAS_SRC;   // not shutting down
+        E.sd_of_brick[g] = (unsigned short)(sdw & FLAG_HAS_SRC);   // not shutting down
         atomicOr(E.bitmap + (g >> 5), 1u << (unsigned)(g & 31));
         atomicAdd(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
         E.newslots[nn + k] = ns;
@@ -839,9 +847,6 @@ __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int st
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_out = (int)all;
 }
 
-// Updating active cells for one active brick (item w, its own maxima r0/r1):
-// keep / shut down / release it, and trigger its neighbours across faces
-// above the level (Fig. 3a).
 // Per-thread copy of one sim's step state (step counter, level): every
 // item of the same sim reuses it instead of re-reading one shared address.
 struct SimCache {
@@ -970,21 +975,16 @@ __device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool 
     }
 }
 
-__device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, const float4 &r0, const float4 &r1,
-                                        int age_flip, SimCache &c)
+// The update of one brick in general (6-neighbour set): `thr` its sim's
+// level, `step`, `interval`, `lpf` its sim's schedule.  Out of line, so the
+// unrolled call sites of the caller stay small.
+__device__ __noinline__ void p2_item_general(const Engine &E, const WorkItem w, const float4 r0, const float4 r1,
+                                             float thr, long long step, int interval, bool lpf)
 {
     const int slot = w.slot;
     const int sim = (int)(w.flags >> 16);
     SimDev *S = E.sims + sim;
-    sim_cache(E, sim, w.nh ^ age_flip, c);
-    if (c.dense || !c.manage) return;
-    const long long step = c.step;
-    const float thr = c.thr_f;   // see SimCache
     const int b = w.brick;
-    if (c.neighbours == 26) {
-        p2_item26(E, w, r1.z > thr, r1.z > 0.f, thr, c.interval, c.lpf, sim, S);
-        return;
-    }
     const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
     bool hot = r1.z > thr;
     if (!hot) {
@@ -997,19 +997,19 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
             if (w.nb[f] >= 0 && nf[f] > thr) hot = true;
     }
     // a source feeds it during the steps this update covers
-    if (!hot && (w.flags & FLAG_HAS_SRC) && forced_in(E, S, b, step + 1, step + c.interval)) hot = true;
+    if (!hot && (w.flags & FLAG_HAS_SRC) && forced_in(E, S, b, step + 1, step + interval)) hot = true;
     unsigned sd = w.flags & SD_MASK;
     const unsigned sd0 = sd;
     bool keep;
     if (hot) {
         sd = 0;
         keep = true;
-    } else if (c.lpf) {
+    } else if (lpf) {
         keep = false;   // Eq. 7: released now, its neighbours filtered after the launch
         if (r1.z > 0.f) E.lpf_q[agg_add(&E.st->n_lpf_q, 1)] = __ldg(&S->brick_base) + b;
     } else if (sd > 0) {
         // the count is in time steps; `interval` of them passed
-        sd = sd > (unsigned)c.interval ? sd - (unsigned)c.interval : 0u;
+        sd = sd > (unsigned)interval ? sd - (unsigned)interval : 0u;
         keep = sd > 0;
     } else if (__ldg(&S->decay_steps) > 0) {
         sd = (unsigned)__ldg(&S->decay_steps);
@@ -1032,6 +1032,33 @@ __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, cons
         }
     }
     if (n > 0) claim_bricks<6>(E, sim, S, nbs, n);
+}
+
+// Updating active cells for one active brick (item w, its own maxima
+// r0/r1): keep / shut down / release it, and trigger its neighbours across
+// faces above the level (Fig. 3a).  Most bricks are above the level, not
+// shutting down and have no face above it towards an unboxed neighbour:
+// for them the update changes nothing, which is decided here without a
+// memory access; the rest take the general path.
+__device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, const float4 &r0, const float4 &r1,
+                                        int age_flip, SimCache &c)
+{
+    const int sim = (int)(w.flags >> 16);
+    sim_cache(E, sim, w.nh ^ age_flip, c);
+    if (c.dense || !c.manage) return;
+    const float thr = c.thr_f;   // see SimCache
+    if (c.neighbours == 26) {
+        p2_item26(E, w, r1.z > thr, r1.z > 0.f, thr, c.interval, c.lpf, sim, E.sims + sim);
+        return;
+    }
+    if (r1.z > thr && (w.flags & SD_MASK) == 0) {
+        const float fc[6] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y};
+        bool edge = false;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) edge = edge || (w.nb[f] == -1 && fc[f] > thr);
+        if (!edge) return;
+    }
+    p2_item_general(E, w, r0, r1, thr, c.step, c.interval, c.lpf);
 }
 
 // ---------------------------------------------------------------------------
