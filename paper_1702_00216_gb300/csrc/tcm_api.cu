@@ -11,6 +11,7 @@
 #include <cstring>
 #include <algorithm>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/tcm.h"
@@ -248,16 +249,55 @@ void range_free(tcm_batch *b, long long base, long long len)
     b->free_ranges.swap(merged);
 }
 
+// Largest value of c[0..n) and whether any is negative, NaN or infinite;
+// branch-free, so the compiler can vectorise it.
+void scan_c(const float *c, long long n, float *cmax, bool *bad)
+{
+    float m = 0.f;
+    unsigned flag = 0;
+    for (long long i = 0; i < n; ++i) {
+        const float x = c[i];
+        m = x > m ? x : m;
+        flag |= (unsigned)!(x >= 0.f) | (unsigned)(x == INFINITY);
+    }
+    *cmax = m;
+    *bad = flag != 0;
+}
+
 float model_c_max(const tcm_domain *d, const tcm_velocity_model *v, bool *bad)
 {
     *bad = false;
     float cmax = 0.f;
     if (v->kind == TCM_MEDIA_DENSE) {
+        // A dense model can hold 1e8+ values: the scan is split over host
+        // threads (max and "any bad" do not depend on the split).
         const long long n = d->nx * d->ny * d->nz;
-        for (long long i = 0; i < n; ++i) {
-            const float c = v->c[i];
-            if (!(c >= 0.f) || std::isinf(c)) *bad = true;
-            cmax = std::max(cmax, c);
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nt = (int)std::min<long long>(std::min(hw, 16u), std::max(1LL, n >> 22));
+        std::vector<float> part_max((size_t)nt, 0.f);
+        std::vector<char> part_bad((size_t)nt, 0);
+        std::vector<std::thread> pool;
+        const long long chunk = (n + nt - 1) / nt;
+        for (int t = 0; t < nt; ++t) {
+            const long long i0 = std::min(n, (long long)t * chunk), i1 = std::min(n, i0 + chunk);
+            auto job = [=, &part_max, &part_bad]() {
+                bool b = false;
+                scan_c(v->c + i0, i1 - i0, &part_max[(size_t)t], &b);
+                part_bad[(size_t)t] = b;
+            };
+            if (t + 1 < nt) {
+                try {
+                    pool.emplace_back(job);
+                    continue;
+                } catch (...) {
+                }
+            }
+            job();   // the last chunk (or one no thread could be started for)
+        }
+        for (auto &th : pool) th.join();
+        for (int t = 0; t < nt; ++t) {
+            cmax = std::max(cmax, part_max[(size_t)t]);
+            if (part_bad[(size_t)t]) *bad = true;
         }
         return cmax;
     }

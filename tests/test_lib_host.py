@@ -82,6 +82,23 @@ def test_create_rejects_cfl_violation(lib, courant, expect):
     assert e.value.status == expect
 
 
+@pytest.mark.parametrize("where", [0, 4_000_000, 16 * 1024 * 1024 - 1])
+def test_dense_model_scan_split_over_threads(lib, where):
+    """A dense model of 2^24 nodes is scanned in chunks on several host
+    threads: one bad value or one too-fast node anywhere (first, middle,
+    last chunk) is still found."""
+    shape = (256, 256, 256)
+    c = np.full(shape, 1.0, np.float32)
+    flat = c.reshape(-1)
+    for value, expect in ((np.nan, tcm.TCM_EINVAL), (np.inf, tcm.TCM_EINVAL), (-0.5, tcm.TCM_EINVAL),
+                          (1.2, tcm.TCM_ECFL)):
+        flat[where] = value
+        with pytest.raises(tcm.TCMError) as e:
+            tcm.tcm_create(shape, W.dense_media(c), 1.0, 0.5, 0.0, (8, 8, 8), _opts())
+        assert e.value.status == expect, (value, where)
+        flat[where] = 1.0
+
+
 @pytest.mark.parametrize("bad", ["shape", "dx", "dt", "thr", "brick", "decay", "mode", "cneg",
                                  "pool"])
 def test_create_rejects_bad_arguments(lib, bad):
