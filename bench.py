@@ -55,15 +55,21 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once sampling runs
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.005)
+            self.first = len(self.lines)
         except Exception:
             self.proc = None
         return self
@@ -81,9 +87,13 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        """Samples taken during the region (the one taken just before it when
+        the region was too short for any)."""
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        during = self.lines[self.first:]
+        lines = during if during else self.lines[-1:]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -96,7 +106,8 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 50,
+                "during_region": bool(during)}
 
 
 def kernel_source_hash() -> str:
@@ -175,21 +186,21 @@ def run_ours(args, rank, world, local_rank):
     u0 = sim.updates
     l0 = sim.launches
     ph0 = sim.phase_ns()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    # The timed region: the K steps in one call of the public API (one
+    # launch per step, replayed from a CUDA graph captured inside the call).
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         ev[0].record()
-        for i in range(K):
-            sim.step_async(1)
-            ev[i + 1].record()
+        sim.step_async(K)
+        ev[1].record()
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     sim.sync()
-    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
-    total_ms = ev[0].elapsed_time(ev[K])
+    total_ms = ev[0].elapsed_time(ev[1])
     updates = sim.updates - u0
     launches = sim.launches - l0
     ph = [b - a for a, b in zip(ph0, sim.phase_ns())]
@@ -202,9 +213,10 @@ def run_ours(args, rank, world, local_rank):
     achieved = updates * BYTES_PER_UPDATE / (total_ms / 1e3) / 1e9
     traffic = profiled_traffic(updates / max(launches, 1))
     sim.close()
-    marginal = None
+    marginal, step_ms = None, None
     if not args.quick and world == 1:
-        marginal = per_cell_fit(tcm, W, wl, pool, local_rank, TOTAL_STEPS - K, step_ms, peaks["hbm_gbs"])
+        marginal, step_ms = per_cell_fit(torch, tcm, W, wl, pool, local_rank, TOTAL_STEPS - K, K,
+                                         peaks["hbm_gbs"])
     del pool
     torch.cuda.empty_cache()
 
@@ -243,8 +255,10 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": peak_kind, "frac_of_nominal_8tbs": achieved / 8000.0,
                      "algorithmic_bytes_per_update": BYTES_PER_UPDATE,
                      "kernel": "k_step (persistent, one launch per step)"},
-        "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                    "min": float(min(step_ms)), "max": float(max(step_ms))},
+        "step_ms": None if step_ms is None else {
+            "p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+            "min": float(min(step_ms)), "max": float(max(step_ms)),
+            "how": "untimed replay of the timed steps, one call and one event per step"},
         "per_active_cell": marginal,
         "phase_ms": {"time_stepping": ph[0] / 1e6, "update_active": ph[1] / 1e6,
                      "compaction": ph[2] / 1e6},
@@ -267,17 +281,32 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def per_cell_fit(tcm, W, wl, pool, local_rank, first, step_ms, hbm_peak):
-    """Split the timed steps' CUDA-event times into a fixed cost per step and a
-    cost per active cell: the node updates of every step are recorded by an
-    untimed replay of the same (deterministic) run, one launch at a time, and
-    t_step = fixed + updates / rate is fitted by least squares.  Also the
-    whole-step rate of the last 200 steps (the largest active sets)."""
+def per_cell_fit(torch, tcm, W, wl, pool, local_rank, first, K, hbm_peak):
+    """Split the time of steps first..first+K into a fixed cost per step and a
+    cost per active cell.  Two untimed replays of the same (deterministic)
+    run: one call and one CUDA event per step (the step times; each includes
+    its call's launch gap, so the fixed cost is an upper bound), and one
+    synchronous step at a time (the node updates of every step).  Then
+    t_step = fixed + updates / rate by least squares, and the whole-step rate
+    of the last 200 steps (the largest active sets).  Returns the fit and the
+    per-step times in ms."""
+    s = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
+    s.step(first)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record()
+    for i in range(K):
+        s.step_async(1)
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    s.sync()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+    s.close()
     s = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
     s.step(first)
     upd = []
     last = s.updates
-    for _ in range(len(step_ms)):
+    for _ in range(K):
         s.step(1)
         u = s.updates
         upd.append(u - last)
@@ -294,8 +323,8 @@ def per_cell_fit(tcm, W, wl, pool, local_rank, first, step_ms, hbm_peak):
             "fixed_share_of_run": fixed * len(t) / t.sum(),
             "last_200_steps_gbs": late_gbs, "last_200_steps_frac": late_gbs / hbm_peak,
             "last_200_steps_mean_active_cells": float(u[late].mean()),
-            "how": "least squares t_step = fixed + updates/rate over the timed steps; updates per step "
-                   "from an untimed replay"}
+            "how": "least squares t_step = fixed + updates/rate over an untimed replay of the timed "
+                   "steps (one call and event per step); updates per step from a second replay"}, step_ms
 
 
 def virtual_leg(torch, tcm, W, local_rank):
