@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 TOTAL_STEPS = 1500
 BYTES_PER_UPDATE = 16          # read phi^n, phi^{n-1}, k; write phi^{n+1} (FP32, per-node k)
+BYTES_PER_UPDATE_16 = 12       # 16-bit velocity form: read phi^n, v^n (2 B), k (4 B); write phi, v
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_layered256_traffic.txt")
 
 
@@ -166,9 +167,11 @@ def run_ours(args, rank, world, local_rank):
     K, Wm = args.steps, args.warmup
     wl = W.layered(n=args.grid, steps=TOTAL_STEPS)
     # enough boxes for every brick of the grid (the layered wave reaches most of it)
-    pool_bytes = (args.grid // 8) ** 3 * tcm.tcm_slot_bytes(wl.brick)
+    storage = tcm.STORAGES[args.storage]
+    bpu = BYTES_PER_UPDATE if args.storage == "f32" else BYTES_PER_UPDATE_16
+    pool_bytes = (args.grid // 8) ** 3 * tcm.tcm_slot_bytes(wl.brick, storage)
     pool = torch.empty(pool_bytes, dtype=torch.uint8, device=dev)
-    sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
+    sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank, storage=storage)
     t0 = max(0, TOTAL_STEPS - K - Wm)
     if args.trace:
         # one step at a time, recording the node updates of every launch
@@ -210,13 +213,14 @@ def run_ours(args, rank, world, local_rank):
     value = upd_all / (t_max / 1e3)
 
     peaks, peak_kind = measured_peaks()
-    achieved = updates * BYTES_PER_UPDATE / (total_ms / 1e3) / 1e9
-    traffic = profiled_traffic(updates / max(launches, 1))
+    achieved = updates * bpu / (total_ms / 1e3) / 1e9
+    # the committed counters are those of the binary32 kernel
+    traffic = profiled_traffic(updates / max(launches, 1)) if args.storage == "f32" else None
     sim.close()
     marginal, step_ms = None, None
     if not args.quick and world == 1:
         marginal, step_ms = per_cell_fit(torch, tcm, W, wl, pool, local_rank, TOTAL_STEPS - K, K,
-                                         peaks["hbm_gbs"])
+                                         peaks["hbm_gbs"], storage, bpu)
     del pool
     torch.cuda.empty_cache()
 
@@ -247,13 +251,14 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": wl.name, "grid": list(wl.shape[::-1]), "brick": list(wl.brick),
                    "threshold": "relative 1e-6", "decay": "alpha 0.8, 20 steps",
+                   "storage": args.storage,
                    "timed_steps": [TOTAL_STEPS - K, TOTAL_STEPS],
                    "l2": "inputs larger than L2 (fields + per-node k > 1.5 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peak_kind, "frac_of_nominal_8tbs": achieved / 8000.0,
-                     "algorithmic_bytes_per_update": BYTES_PER_UPDATE,
+                     "algorithmic_bytes_per_update": bpu,
                      "kernel": "k_step (persistent, one launch per step)"},
         "step_ms": None if step_ms is None else {
             "p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -281,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def per_cell_fit(torch, tcm, W, wl, pool, local_rank, first, K, hbm_peak):
+def per_cell_fit(torch, tcm, W, wl, pool, local_rank, first, K, hbm_peak, storage=0, bpu=16):
     """Split the time of steps first..first+K into a fixed cost per step and a
     cost per active cell.  Two untimed replays of the same (deterministic)
     run: one call and one CUDA event per step (the step times; each includes
@@ -290,7 +295,7 @@ def per_cell_fit(torch, tcm, W, wl, pool, local_rank, first, K, hbm_peak):
     t_step = fixed + updates / rate by least squares, and the whole-step rate
     of the last 200 steps (the largest active sets).  Returns the fit and the
     per-step times in ms."""
-    s = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
+    s = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank, storage=storage)
     s.step(first)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
@@ -302,7 +307,7 @@ def per_cell_fit(torch, tcm, W, wl, pool, local_rank, first, K, hbm_peak):
     s.sync()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
     s.close()
-    s = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank)
+    s = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank, storage=storage)
     s.step(first)
     upd = []
     last = s.updates
@@ -316,9 +321,9 @@ def per_cell_fit(torch, tcm, W, wl, pool, local_rank, first, K, hbm_peak):
     t = np.asarray(step_ms, dtype=np.float64) / 1e3
     A = np.vstack([np.ones_like(u), u]).T
     (fixed, per_update), *_ = np.linalg.lstsq(A, t, rcond=None)
-    rate = BYTES_PER_UPDATE / per_update / 1e9
+    rate = bpu / per_update / 1e9
     late = slice(max(0, len(t) - 200), len(t))
-    late_gbs = u[late].sum() * BYTES_PER_UPDATE / t[late].sum() / 1e9
+    late_gbs = u[late].sum() * bpu / t[late].sum() / 1e9
     return {"fixed_us_per_step": fixed * 1e6, "marginal_gbs": rate, "marginal_frac": rate / hbm_peak,
             "fixed_share_of_run": fixed * len(t) / t.sum(),
             "last_200_steps_gbs": late_gbs, "last_200_steps_frac": late_gbs / hbm_peak,
@@ -480,6 +485,40 @@ def precision_leg(torch, tcm, W, dev, local_rank):
         s.close()
     del ref
     torch.cuda.empty_cache()
+    out["layered_512"] = storage_throughput(torch, tcm, W, local_rank)
+    return out
+
+
+def storage_throughput(torch, tcm, W, local_rank):
+    """Each storage on the 512^3 layered workload as the headline measures it:
+    steps 5..1500 in one call (CUDA events around it), node updates/s and HBM
+    GB/s at the storage's algorithmic bytes per update, as a fraction of the
+    measured copy bandwidth."""
+    wl = W.layered(steps=TOTAL_STEPS)
+    peaks, _ = measured_peaks()
+    n_bricks = (wl.shape[0] // 8) * (wl.shape[1] // 8) * (wl.shape[2] // 8)
+    out = {"workload": f"{wl.name}, steps 5..{TOTAL_STEPS} in one call"}
+    for st in ("f32", "bf16", "f16"):
+        code = tcm.STORAGES[st]
+        s = tcm.Sim.from_workload(wl, device=local_rank, storage=st,
+                                  pool_bytes=n_bricks * tcm.tcm_slot_bytes(wl.brick, code))
+        s.step(5)
+        torch.cuda.synchronize()
+        u0 = s.updates
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step_async(TOTAL_STEPS - 5)
+        e1.record()
+        s.sync()
+        ms = e0.elapsed_time(e1)
+        upd = s.updates - u0
+        s.close()
+        bpu = 16 if st == "f32" else 12
+        gbs = upd * bpu / (ms / 1e3) / 1e9
+        out[st] = {"updates_per_s": upd / (ms / 1e3), "ms": ms, "bytes_per_update": bpu, "hbm_gbs": gbs,
+                   "frac_of_measured": gbs / peaks["hbm_gbs"]}
+    torch.cuda.empty_cache()
     return out
 
 
@@ -627,6 +666,8 @@ def main():
     ap.add_argument("--steps", type=int, default=TOTAL_STEPS - 5)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--grid", type=int, default=512, help="edge of the layered workload")
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
+                    help="field storage of the timed run (the arithmetic is binary32 in all)")
     ap.add_argument("--trace", default=None,
                     help="write per-launch node updates of the untimed steps (JSON lines)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
