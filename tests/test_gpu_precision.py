@@ -166,3 +166,31 @@ def test_precision_workload_error_against_fp64_dense(capsys):
     assert errs["f32"][0] < 1e-4
     assert errs["f16"][0] < 1.2e-2 and errs["bf16"][0] < 8e-2
     assert errs["f16"][0] < errs["bf16"][0] / 4
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_16bit_layered_512_first_steps_full_size(storage):
+    """The 512^3 layered, perturbed workload with 16-bit storage at full size,
+    as the bench's per-storage leg runs it (pool for every brick, relative
+    threshold 1e-6, 20-step decay): the first 160 steps against the oracle's
+    storage form, bit for bit on the window the wave occupies, and the same
+    active set."""
+    wl = W.layered(steps=160)
+    code = tcm.STORAGES[storage]
+    n_bricks = (512 // 8) ** 3
+    s = tcm.Sim.from_workload(wl, storage=storage, pool_bytes=n_bricks * tcm.tcm_slot_bytes(wl.brick, code))
+    o = oracle_of(wl, storage)
+    s.step(160)
+    o.step(160)
+    ids = o.active_bricks()
+    assert np.array_equal(s.active_bricks(), ids)
+    assert len(ids) > 8
+    bx, by, bz = ids % 64, (ids // 64) % 64, ids // 4096
+    lo = [int(v.min()) * 8 for v in (bx, by, bz)]
+    hi = [int(v.max()) * 8 + 8 for v in (bx, by, bz)]
+    size = [h - l for h, l in zip(hi, lo)]
+    for which in (0, 1):
+        a = s.read_field(which, origin=lo, size=size)
+        b = o.read_field(which, origin=lo, size=size)
+        assert np.array_equal(a, b), which
+    assert s.updates == o.updates
