@@ -1093,6 +1093,29 @@ __device__ void advance_steps(const Engine &E)
     }
 }
 
+// Ask L2 to fetch the field arrays (and per-node k) of a brick that this
+// warp steps next, so its loads find them in L2: bulk prefetches of whole
+// contiguous arrays, no registers or shared memory held.  Only arrays that
+// the stepping will load are named (valid items, per-node k only).
+template <int ST>
+__device__ __forceinline__ void prefetch_brick(const Engine &E, const WorkItem &w, bool v, int t, int age_flip)
+{
+    if (!v || t >= 3) return;
+    const int nh = w.nh ^ age_flip;
+    const void *p;
+    unsigned bytes = BVOL * (unsigned)sizeof(typename Fld<ST>::T);
+    if (t == 0) {
+        p = half_ptr<ST>(E, w.slot, nh);
+    } else if (t == 1) {
+        p = half_ptr<ST>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF);
+    } else {
+        if (w.kp & KP_SCALAR) return;
+        p = reinterpret_cast<const void *>(w.kp);
+        bytes = BVOL * (unsigned)sizeof(float);
+    }
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int ST>
 __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage)
 {
@@ -1130,13 +1153,20 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
         bool v = pr < npairs && i < nact;
         WorkItem w = load_item(L, v ? i : 0);
         v = v && w.slot >= 0;
+        int pn = pr + nwarps;
+        int in = pn * BRICKS_PER_WARP + seg;
+        bool vn = pn < npairs && in < nact;
+        WorkItem wn = load_item(L, vn ? in : 0);
+        vn = vn && wn.slot >= 0;
         while (pr < npairs) {
-            // the next pair's item, loaded while this pair is stepped
-            const int pn = pr + nwarps;
-            const int in = pn * BRICKS_PER_WARP + seg;
-            bool vn = pn < npairs && in < nact;
-            const WorkItem wn = load_item(L, vn ? in : 0);
-            vn = vn && wn.slot >= 0;
+            // the item two pairs ahead, loaded while this pair is stepped;
+            // the next pair's arrays fetched into L2 meanwhile
+            const int pnn = pn + nwarps;
+            const int inn = pnn * BRICKS_PER_WARP + seg;
+            bool vnn = pnn < npairs && inn < nact;
+            const WorkItem wnn = load_item(L, vnn ? inn : 0);
+            vnn = vnn && wnn.slot >= 0;
+            prefetch_brick<ST>(E, wn, vn, t, age_flip);
             // bricks 2j and 2j+1 of the warp form a pair: is the second the x+
             // neighbour of the first?
             bool pair_x = false;
@@ -1152,6 +1182,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
             pr = pn;
             w = wn;
             v = vn;
+            pn = pnn;
+            wn = wnn;
+            vn = vnn;
         }
         flush_gmax(E, gacc, gsim, gnh);
         flush_updates(E, scells, gsim);
