@@ -336,7 +336,8 @@ def virtual_leg(torch, tcm, W, local_rank):
     """The virtual 4096^3 domain (a dense grid would need 4096^3 x 3 x 4 B =
     824 GB): sphere inclusion, 3-cycle Ricker burst, relative threshold 1e-6,
     20-step decay, pool capped at 120 GiB, 2500 steps from create to the last
-    step, device time."""
+    step, device time; the steps once more with the L2 prefetch off."""
+    import dataclasses
     wl = W.virtual()
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -356,16 +357,25 @@ def virtual_leg(torch, tcm, W, local_rank):
            "active_bricks_end": s.active_count()[0], "pool_boxes": boxes, "pool_boxes_free_end": free,
            "dense_bytes_needed": 4096 ** 3 * 12, "pool_bytes": wl.pool_bytes}
     s.close()
+    s = tcm.Sim.from_workload(dataclasses.replace(wl, prefetch=False), device=local_rank)
+    e0.record()
+    s.step_async(wl.steps)
+    e1.record()
+    s.sync()
+    ms = e0.elapsed_time(e1)
+    out["no_prefetch"] = {"steps_s": ms / 1e3, "updates_per_s": s.updates / (ms / 1e3)}
+    s.close()
     torch.cuda.empty_cache()
     return out
 
 
 def tuning_leg(torch, tcm, W, wl, dev, local_rank):
     """The autotuner on the benchmark workload (brick shapes x update
-    schedules, steps 600..800 timed), then the full create-to-result run with
-    its choice, compared with the dense result."""
+    schedules, then the fastest with the L2 prefetch off; steps 600..800
+    timed), then the full create-to-result run with its choice, compared with
+    the dense result."""
     from paper_1702_00216_gb300 import autotune
-    r = autotune.autotune(wl, start=600, count=200, allow_schedule=True, device=local_rank)
+    r = autotune.autotune(wl, start=600, count=200, allow_schedule=True, device=local_rank, allow_prefetch=True)
     best = autotune.apply(wl, r["best"])
     out = {"window": r["window"], "table": r["table"], "best": r["best"].label()}
     runs = {}

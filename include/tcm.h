@@ -108,6 +108,10 @@ typedef struct {
     int no_graphs;      /* 1: issue every step launch directly; 0: runs of launches up to
                            the next change of the batch are captured once as a CUDA graph
                            and replayed (same kernels, same results) */
+    int no_prefetch;    /* 1: no L2 prefetch in the time stepping; 0: while a warp steps a
+                           brick pair it asks L2 for the next pair's field arrays and
+                           per-node k (same results; faster on dense active regions,
+                           measured slower on very large pools) */
 } tcm_options;
 
 /* Bytes of pool one box takes for this brick shape and storage (binary32:
@@ -283,6 +287,7 @@ typedef struct {
     int max_sims;       /* simulation-table capacity */
     int no_graphs;      /* as in tcm_options */
     tcm_brick brick;    /* brick shape of every simulation of the batch ({0,0,0}: 8x8x8) */
+    int no_prefetch;    /* as in tcm_options */
 } tcm_batch_options;
 
 tcm_status tcm_batch_create(const tcm_batch_options *options, tcm_batch **out);

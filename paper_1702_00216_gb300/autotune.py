@@ -12,6 +12,8 @@ because the cells differ).  Candidates:
                    allow_schedule, also the Eq. 5 interval with the 26
                    neighbour set (at threshold 0 both equal the dense grid;
                    above it the active sets differ slightly)
+  L2 prefetch      on (always); with allow_prefetch, the fastest of the
+                   above is timed once more with it off (same results)
 
 Results are cached per (workload name, shape, window, candidates) in the
 process, and the chosen configuration can be applied with `apply`.
@@ -32,10 +34,12 @@ class Candidate:
     brick: Tuple[int, int, int]
     interval: int = 1
     neighbours: int = 6
+    prefetch: bool = True
 
     def label(self) -> str:
         b = "x".join(map(str, self.brick))
-        return b if (self.interval, self.neighbours) == (1, 6) else f"{b}/eq5-26"
+        b = b if (self.interval, self.neighbours) == (1, 6) else f"{b}/eq5-26"
+        return b if self.prefetch else f"{b}/no-prefetch"
 
 
 def candidates(allow_schedule: bool = False, bricks: Sequence = BRICKS) -> List[Candidate]:
@@ -46,8 +50,9 @@ def candidates(allow_schedule: bool = False, bricks: Sequence = BRICKS) -> List[
 
 
 def apply(wl, c: Candidate):
-    """The workload with the candidate's brick shape and schedule."""
-    return dataclasses.replace(wl, brick=tuple(c.brick), interval=c.interval, neighbours=c.neighbours)
+    """The workload with the candidate's brick shape, schedule and prefetch."""
+    return dataclasses.replace(wl, brick=tuple(c.brick), interval=c.interval, neighbours=c.neighbours,
+                               prefetch=c.prefetch)
 
 
 def _pool_bytes(wl, brick) -> Optional[int]:
@@ -79,11 +84,11 @@ def measure(wl, c: Candidate, start: int, count: int, device: int = 0, storage="
     finally:
         s.close()
     return {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
-            "window_ms": ms, "cell_updates": upd, "updates_per_s": upd / (ms / 1e3) if ms > 0 else 0.0}
+            "prefetch": c.prefetch, "window_ms": ms, "cell_updates": upd, "updates_per_s": upd / (ms / 1e3) if ms > 0 else 0.0}
 
 
 def autotune(wl, start: Optional[int] = None, count: Optional[int] = None, allow_schedule: bool = False,
-             device: int = 0, storage="f32", bricks: Sequence = BRICKS) -> dict:
+             device: int = 0, storage="f32", bricks: Sequence = BRICKS, allow_prefetch: bool = False) -> dict:
     """Time every candidate on steps [start, start+count) of the workload and
     return {"best": Candidate, "table": [...]} (fastest window first)."""
     steps = max(int(wl.steps), 1)
@@ -91,7 +96,8 @@ def autotune(wl, start: Optional[int] = None, count: Optional[int] = None, allow
         count = max(1, min(200, steps // 5))
     if start is None:
         start = max(0, min(steps - count, (steps * 2) // 5))
-    key = (wl.name, tuple(wl.shape), start, count, allow_schedule, storage, tuple(map(tuple, bricks)))
+    key = (wl.name, tuple(wl.shape), start, count, allow_schedule, storage, tuple(map(tuple, bricks)),
+           allow_prefetch)
     if key in _CACHE:
         return _CACHE[key]
     table = []
@@ -100,6 +106,12 @@ def autotune(wl, start: Optional[int] = None, count: Optional[int] = None, allow
         r["candidate"] = c
         table.append(r)
     table.sort(key=lambda r: r["window_ms"])
+    if allow_prefetch:
+        c = dataclasses.replace(table[0]["candidate"], prefetch=False)
+        r = measure(wl, c, start, count, device, storage)
+        r["candidate"] = c
+        table.append(r)
+        table.sort(key=lambda r: r["window_ms"])
     out = {"best": table[0]["candidate"], "window": [start, start + count],
            "table": [{k: v for k, v in r.items() if k != "candidate"} for r in table]}
     _CACHE[key] = out

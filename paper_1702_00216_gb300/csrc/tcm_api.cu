@@ -421,6 +421,7 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
     if ((st = dalloc(b, &E.lpf_q, b->n_slots)) != TCM_OK) return fail(st);
     if ((st = dalloc(b, &E.lpf_aff, b->n_slots)) != TCM_OK) return fail(st);
     E.n_sims = max_sims;
+    E.prefetch = 1;
     b->sims.resize(max_sims);
     b->handles.assign(max_sims, nullptr);
     b->free_ranges.push_back({0, b->cap_bricks});
@@ -1042,6 +1043,7 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     TRYS(batch_new(options->device, (cudaStream_t)options->stream, options->pool_ptr, pool_bytes, options->storage,
                    n_bricks, 1, &b));
     b->use_graphs = !options->no_graphs;
+    b->E.prefetch = options->no_prefetch ? 0 : 1;
     DeviceGuard g(b->device);
     int id = -1;
     tcm_status st = sim_add(b, domain, velocity, dx, dt, c_max, threshold, options->threshold_mode,
@@ -1384,7 +1386,10 @@ tcm_status tcm_batch_create(const tcm_batch_options *o, tcm_batch **out)
     if (!o) return TCM_EINVAL;
     const tcm_status st = batch_new(o->device, (cudaStream_t)o->stream, o->pool_ptr, o->pool_bytes, o->storage,
                                     o->max_bricks, o->max_sims, out);
-    if (st == TCM_OK) (*out)->use_graphs = !o->no_graphs;
+    if (st == TCM_OK) {
+        (*out)->use_graphs = !o->no_graphs;
+        (*out)->E.prefetch = o->no_prefetch ? 0 : 1;
+    }
     return st;
 }
 

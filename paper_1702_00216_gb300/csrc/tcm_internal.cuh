@@ -179,6 +179,7 @@ struct Engine {
     long long *lpf_aff;    // affected bricks (global ids)
     float *lpf_out;        // filtered values, 2 * BVOL per affected brick
     int lpf_cap;           // capacity of lpf_out in bricks
+    int prefetch;          // 1: L2 prefetch of the next brick pair's arrays in the time stepping
 };
 
 struct MediaDev {

@@ -1093,27 +1093,29 @@ __device__ void advance_steps(const Engine &E)
     }
 }
 
-// Ask L2 to fetch the field arrays (and per-node k) of a brick that this
-// warp steps next, so its loads find them in L2: bulk prefetches of whole
-// contiguous arrays, no registers or shared memory held.  Only arrays that
-// the stepping will load are named (valid items, per-node k only).
+// Ask L2 for the field arrays (and per-node k) of the brick this lane's
+// segment steps next, one 128-byte line per lane and array, so that the
+// stepping's loads of them find L2 instead of HBM; no registers or shared
+// memory stay held.  Only arrays that the stepping will load are named
+// (valid items; per-node k only).
 template <int ST>
 __device__ __forceinline__ void prefetch_brick(const Engine &E, const WorkItem &w, bool v, int t, int age_flip)
 {
-    if (!v || t >= 3) return;
+    if (!v) return;
     const int nh = w.nh ^ age_flip;
-    const void *p;
-    unsigned bytes = BVOL * (unsigned)sizeof(typename Fld<ST>::T);
-    if (t == 0) {
-        p = half_ptr<ST>(E, w.slot, nh);
-    } else if (t == 1) {
-        p = half_ptr<ST>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF);
-    } else {
-        if (w.kp & KP_SCALAR) return;
-        p = reinterpret_cast<const void *>(w.kp);
-        bytes = BVOL * (unsigned)sizeof(float);
+    constexpr int LINE = 128;
+    constexpr int HB = BVOL * (int)sizeof(typename Fld<ST>::T);
+    const char *a = reinterpret_cast<const char *>(half_ptr<ST>(E, w.slot, nh));
+    const char *b = reinterpret_cast<const char *>(half_ptr<ST>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF));
+    for (int o = t * LINE; o < HB; o += TPB * LINE) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a + o) : "memory");
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(b + o) : "memory");
     }
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+    if (!(w.kp & KP_SCALAR)) {
+        const char *k = reinterpret_cast<const char *>(w.kp);
+        for (int o = t * LINE; o < BVOL * (int)sizeof(float); o += TPB * LINE)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(k + o) : "memory");
+    }
 }
 
 template <int ST>
@@ -1166,7 +1168,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
             bool vnn = pnn < npairs && inn < nact;
             const WorkItem wnn = load_item(L, vnn ? inn : 0);
             vnn = vnn && wnn.slot >= 0;
-            prefetch_brick<ST>(E, wn, vn, t, age_flip);
+            if (E.prefetch) prefetch_brick<ST>(E, wn, vn, t, age_flip);
             // bricks 2j and 2j+1 of the warp form a pair: is the second the x+
             // neighbour of the first?
             bool pair_x = false;

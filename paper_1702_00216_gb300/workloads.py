@@ -176,6 +176,7 @@ class Workload:
     interval: int = 1                                # update procedure every `interval` steps
     neighbours: int = 6                              # 6 (faces) or 26
     lpf: Optional[Tuple[float, float]] = None        # Eq. 7 shut-down (pass, stop), else Eq. 6
+    prefetch: bool = True                            # L2 prefetch in the time stepping
 
     @property
     def nx(self):

@@ -31,3 +31,23 @@ def test_picks_fastest_window_and_caches(monkeypatch):
     assert A.autotune(wl) is r and len(calls) == n        # cached
     w2 = A.apply(wl, A.Candidate((16, 8, 8), 0, 26))
     assert w2.brick == (16, 8, 8) and (w2.interval, w2.neighbours) == (0, 26) and wl.brick == (8, 8, 8)
+
+
+def test_prefetch_refinement(monkeypatch):
+    """With allow_prefetch the fastest configuration is timed once more with
+    the L2 prefetch off, and the faster of the two is chosen."""
+    calls = []
+
+    def fake(wl, c, start, count, device=0, storage="f32"):
+        calls.append(c.label())
+        ms = {"4x4x4": 3.0, "8x8x8": 1.0, "16x8x8": 2.0, "8x8x8/no-prefetch": 0.5}[c.label()]
+        return {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
+                "prefetch": c.prefetch, "window_ms": ms, "cell_updates": 1, "updates_per_s": 1.0}
+
+    monkeypatch.setattr(A, "measure", fake)
+    A._CACHE.clear()
+    wl = W.small(n=32, steps=100)
+    r = A.autotune(wl, allow_prefetch=True)
+    assert calls == ["4x4x4", "8x8x8", "16x8x8", "8x8x8/no-prefetch"]
+    assert r["best"].brick == (8, 8, 8) and r["best"].prefetch is False
+    assert A.apply(wl, r["best"]).prefetch is False and wl.prefetch is True

@@ -263,3 +263,21 @@ def test_virtual_4096_first_steps():
     lo = [int(v.min()) * 8 for v in (bx, by, bz)]
     hi = [int(v.max()) * 8 + 8 for v in (bx, by, bz)]
     assert_same(g, o, window=(lo, [h - l for h, l in zip(hi, lo)]))
+
+
+@pytest.mark.parametrize("prefetch", [True, False])
+def test_l2_prefetch_on_and_off_match_oracle(prefetch):
+    """The L2 prefetch of the time stepping is a hint: with it on or off the
+    fields and active sets equal the oracle's (relative threshold, decay,
+    releases and claims on a ragged grid)."""
+    shape = (40, 48, 56)
+    media = W.random_dense_media(shape, 5, 1.0, 1.8)
+    dt = 0.5 / media.c_max()
+    wl = W.Workload("pf", shape, media, 1.0, dt, [(20, 24, 10, W.ricker(1 / 8, dt))], 150,
+                    thr_mode=tcm.TCM_THR_RELATIVE, tau=1e-4, decay_alpha=0.8, decay_steps=5, prefetch=prefetch)
+    g, o = pair(wl)
+    for _ in range(3):
+        g.step(50)
+        o.step(50)
+        assert_same(g, o)
+    assert g.updates == o.updates

@@ -152,3 +152,35 @@ def test_product_path_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "tcm_oracle" not in txt, f
+
+
+def test_option_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes mirrors of tcm_options and tcm_batch_options have
+    the C layout of include/tcm.h (sizes and every field offset, read from a
+    C program compiled against the header)."""
+    import ctypes
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tcm.h"', "int main(void) {"]
+    for ct, c_name in ((tcm.tcm_options, "tcm_options"), (tcm.tcm_batch_options, "tcm_batch_options")):
+        lines.append(f'printf("{c_name} size %zu\\n", sizeof({c_name}));')
+        for f, _ in ct._fields_:
+            lines.append(f'printf("{c_name} {f} %zu\\n", offsetof({c_name}, {f}));')
+    lines.append("return 0; }")
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            name, field, val = ln.split()
+            got[(name, field)] = int(val)
+    for ct, c_name in ((tcm.tcm_options, "tcm_options"), (tcm.tcm_batch_options, "tcm_batch_options")):
+        assert got[(c_name, "size")] == ctypes.sizeof(ct)
+        for f, _ in ct._fields_:
+            assert got[(c_name, f)] == getattr(ct, f).offset, (c_name, f)
