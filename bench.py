@@ -404,7 +404,8 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
     (update procedure every step, face neighbours, Eq. 6 decay), TCM on the
     Eq. 5 schedule (update every 8 steps, 26 neighbours), TCM with the Eq. 7
     shut-down (LPF pass 0.25, stop 0.5 of Nyquist), and the same kernel over
-    every brick (dense, no update procedure)."""
+    every brick (dense, no update procedure); each run twice, the faster
+    reported."""
     import dataclasses
     runs = [("dense", wl, True), ("tcm", wl, False),
             ("tcm_eq5_26", dataclasses.replace(wl, interval=0, neighbours=26), False),
@@ -412,15 +413,21 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
     out = {}
     ref = None
     for name, w, dense in runs:
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        s = tcm.Sim.from_workload(w, dense=dense, device=local_rank, pool_bytes=None)
-        s.step(TOTAL_STEPS)
-        buf = torch.empty(w.shape, dtype=torch.float32, device=dev)
-        tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), w.shape[::-1], buf.data_ptr())
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t
-        r = {"seconds": dt, "cell_updates": s.updates, "schedule": list(s.schedule())}
+        dts = []
+        for rep in range(2):   # best of two (the first pays one-off allocation costs)
+            if rep:
+                del buf
+                s.close()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            s = tcm.Sim.from_workload(w, dense=dense, device=local_rank, pool_bytes=None)
+            s.step(TOTAL_STEPS)
+            buf = torch.empty(w.shape, dtype=torch.float32, device=dev)
+            tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), w.shape[::-1], buf.data_ptr())
+            torch.cuda.synchronize()
+            dts.append(time.perf_counter() - t)
+        dt = min(dts)
+        r = {"seconds": dt, "seconds_each": dts, "cell_updates": s.updates, "schedule": list(s.schedule())}
         if ref is None:
             ref = buf
             r["max_abs_field"] = float(buf.abs().max().item())
