@@ -281,3 +281,26 @@ def test_l2_prefetch_on_and_off_match_oracle(prefetch):
         o.step(50)
         assert_same(g, o)
     assert g.updates == o.updates
+
+
+def test_layered_512_whole_benchmarked_run():
+    """The benchmarked run itself: the 512^3 layered workload over all 1500
+    steps (relative threshold 1e-6, 20-step decay, pool for every brick,
+    steps in one call as the bench issues them) against the oracle run on
+    all host cores; the final fields over the whole domain, the active set
+    and the node-update count agree exactly."""
+    import os
+    wl = W.layered(steps=1500)
+    pool = (512 // 8) ** 3 * tcm.tcm_slot_bytes(wl.brick)
+    g, o = pair(wl, pool_bytes=pool)
+    used = oracle.set_threads(os.cpu_count() or 1)
+    assert used >= 1
+    g.step(5)
+    g.step(1495)
+    o.step(1500)
+    assert g.updates == o.updates
+    assert np.array_equal(g.active_bricks(), o.active_bricks())
+    for which in (0, 1):
+        a, b = g.read_field(which), o.read_field(which)
+        assert np.array_equal(a, b), f"half {which}: max |d| = {float(np.max(np.abs(a - b)))}"
+    g.close()
