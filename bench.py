@@ -228,8 +228,14 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.quick:
         extra = time_to_solution(torch, tcm, W, wl, dev, local_rank)
     e2e = end_to_end(torch, tcm, W, wl, local_rank) if not args.quick else None
+    if e2e is not None and world > 1:
+        # whole job over the replicas: every rank ran the same end-to-end call
+        t_e, u_e = job_totals(torch, e2e["seconds"] * 1e3, e2e["cell_updates"], world, dev)
+        e2e.update({"value": u_e / (t_e / 1e3), "seconds": t_e / 1e3, "cell_updates": u_e,
+                    "h2d_bytes_per_step": e2e["h2d_bytes_per_step"] * world,
+                    "d2h_bytes_per_step": e2e["d2h_bytes_per_step"] * world, "replicas": world})
     cpu = cpu_baseline(W, args, wl=wl) if (rank == 0 and world == 1 and not args.quick) else None
-    serving = serving_leg(torch, W, args, local_rank) if (not args.quick and args.serving > 0) else None
+    serving = serving_leg(torch, W, args, local_rank) if (rank == 0 and not args.quick and args.serving > 0) else None
     precision = precision_leg(torch, tcm, W, dev, local_rank) if (rank == 0 and not args.quick) else None
     virtual = virtual_leg(torch, tcm, W, local_rank) if (rank == 0 and not args.quick and args.virtual) else None
     tuning = tuning_leg(torch, tcm, W, wl, dev, local_rank) if (rank == 0 and not args.quick) else None
@@ -592,7 +598,7 @@ def end_to_end(torch, tcm, W, wl, local_rank):
     d2h = out_host.numel() * 4
     return {"value": upd / dt, "unit": "cell-updates/s",
             "h2d_bytes_per_step": h2d / TOTAL_STEPS, "d2h_bytes_per_step": d2h / TOTAL_STEPS,
-            "seconds": dt, "steps": TOTAL_STEPS,
+            "seconds": dt, "steps": TOTAL_STEPS, "cell_updates": upd,
             "what": "tcm_create from host velocity + tcm_add_source + tcm_step(1500) + "
                     "tcm_read_field of the whole grid to pinned host memory"}
 
