@@ -166,6 +166,10 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     K, Wm = args.steps, args.warmup
     wl = W.layered(n=args.grid, steps=TOTAL_STEPS)
+    if args.lpf:
+        # the Eq. 7 shut-down instead of the Eq. 6 decay (pass, stop of Nyquist)
+        import dataclasses
+        wl = dataclasses.replace(wl, lpf=tuple(float(v) for v in args.lpf.split(",")))
     # enough boxes for every brick of the grid (the layered wave reaches most of it)
     storage = tcm.STORAGES[args.storage]
     bpu = BYTES_PER_UPDATE if args.storage == "f32" else BYTES_PER_UPDATE_16
@@ -258,6 +262,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl.name, "grid": list(wl.shape[::-1]), "brick": list(wl.brick),
                    "threshold": "relative 1e-6", "decay": "alpha 0.8, 20 steps",
                    "storage": args.storage,
+                   "shutdown": f"Eq. 7 LPF {args.lpf}" if args.lpf else "Eq. 6 decay",
                    "timed_steps": [TOTAL_STEPS - K, TOTAL_STEPS],
                    "l2": "inputs larger than L2 (fields + per-node k > 1.5 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -691,6 +696,8 @@ def main():
     ap.add_argument("--grid", type=int, default=512, help="edge of the layered workload")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="field storage of the timed run (the arithmetic is binary32 in all)")
+    ap.add_argument("--lpf", default=None, metavar="PASS,STOP",
+                    help="time the run with the Eq. 7 shut-down (fractions of Nyquist), e.g. 0.25,0.5")
     ap.add_argument("--trace", default=None,
                     help="write per-launch node updates of the untimed steps (JSON lines)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
