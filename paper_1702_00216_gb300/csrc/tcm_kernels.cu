@@ -1693,6 +1693,17 @@ __device__ __forceinline__ long long lpf_neighbour(const SimDev *S, long long ba
     return base + ((long long)az * my + ay) * mx + ax;
 }
 
+// Four consecutive elements e..e+3 (e a multiple of 4) of box half (slot,
+// half) as physical binary32 values, in one vector load.
+__device__ __forceinline__ float4 load_phys4(const Engine &E, int slot, int half, int e, float scale)
+{
+    const size_t i = (size_t)slot * slot_elems(E.storage) + (size_t)half * BVOL + e;
+    if (E.storage == ST_F32) return scale4(__ldcg(reinterpret_cast<const float4 *>(static_cast<const float *>(E.phi) + i)), scale);
+    const uint2 u = __ldcg(reinterpret_cast<const uint2 *>(static_cast<const unsigned short *>(E.phi) + i));
+    if (E.storage == ST_BF16) return Fld<ST_BF16>::cvt(u, scale);
+    return Fld<ST_F16>::cvt(u, scale);
+}
+
 __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1720,6 +1731,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
     if (!grid_barrier(st, &st->bar_count_lpf)) return;
     const int naff = min(__ldcg(&st->n_lpf_aff), E.lpf_cap);
     // (B) one block per affected brick
+    __shared__ int s_nbslot[27];   // boxes of the 3x3x3 block (-1: none)
     float *R = reinterpret_cast<float *>(smem);                         // [2][L][L][L]
     double *T1 = reinterpret_cast<double *>(R + 2 * LPF_L * LPF_L * LPF_L);   // [L][L][C]
     double *T2 = T1 + LPF_L * LPF_L * LPF_C;                               // [L][C][C]
@@ -1730,40 +1742,97 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
         const long long base = S->brick_base;
         const int b = (int)(g - base);
         const float sc = S->scale;
+        if (threadIdx.x < 27) {
+            const int nb = threadIdx.x;
+            const long long gn = lpf_neighbour(S, base, b, nb % 3 - 1, (nb / 3) % 3 - 1, nb / 9 - 1);
+            s_nbslot[nb] = gn >= 0 ? __ldcg(E.slot_of_brick + gn) : -1;
+        }
         for (int i = threadIdx.x; i < LPF_C * LPF_L; i += BLOCK) A[i] = S->lpf_a[i];
-        for (int e = threadIdx.x; e < 27 * 2 * BVOL; e += BLOCK) {
-            const int nb = e / (2 * BVOL), h = (e / BVOL) & 1, loc = e % BVOL;
-            const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
-            const long long gn = lpf_neighbour(S, base, b, dx, dy, dz);
-            const int slot = gn >= 0 ? __ldcg(E.slot_of_brick + gn) : -1;
-            const float v = slot >= 0 ? load_phys(E, slot, h, loc, sc) : 0.f;
+        __syncthreads();
+        // the block's two levels, four x-consecutive nodes per vector (a row
+        // of a brick is x-contiguous in its box and in R)
+        constexpr int Q = BVOL / 4;
+#pragma unroll 4
+        for (int e4 = threadIdx.x; e4 < 27 * 2 * Q; e4 += BLOCK) {
+            const int nb = e4 / (2 * Q), h = (e4 / Q) & 1, loc = (e4 % Q) * 4;
+            const int slot = s_nbslot[nb];
+            const float4 v = slot >= 0 ? load_phys4(E, slot, h, loc, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
             const int lx = loc % BX, ly = (loc / BX) % BY, lz = loc / (BX * BY);
-            R[((h * LPF_L + (dz + 1) * LPF_C + lz) * LPF_L + (dy + 1) * LPF_C + ly) * LPF_L + (dx + 1) * LPF_C + lx] = v;
+            *reinterpret_cast<float4 *>(R + ((h * LPF_L + (nb / 9) * LPF_C + lz) * LPF_L + ((nb / 3) % 3) * LPF_C + ly) *
+                                                LPF_L +
+                                        (nb % 3) * LPF_C + lx) = v;
         }
         __syncthreads();
+        // Rows of R that lie in bricks of the block with no box are zero and
+        // filter to +0 exactly: those rows (x pass) and z-slabs (y pass) are
+        // skipped.  Each thread keeps four outputs in flight (independent FP64
+        // chains); every output sums over j in increasing order, one FMA per
+        // term.
+        auto row_live = [&](int dz, int dy) {
+            const int k = (dz * 3 + dy) * 3;
+            return s_nbslot[k] >= 0 || s_nbslot[k + 1] >= 0 || s_nbslot[k + 2] >= 0;
+        };
+        static_assert(LPF_C % 4 == 0, "four outputs per thread");
+        constexpr int C4 = LPF_C / 4;
         for (int h = 0; h < 2; ++h) {
-            for (int e = threadIdx.x; e < LPF_L * LPF_L * LPF_C; e += BLOCK) {   // along x
-                const int i = e % LPF_C, zy = e / LPF_C;
-                const float *row = R + ((size_t)h * LPF_L * LPF_L + zy) * LPF_L;
-                double acc = 0.0;
-                for (int j = 0; j < LPF_L; ++j) acc = __dadd_rn(acc, __dmul_rn(A[i * LPF_L + j], (double)row[j]));
-                T1[e] = acc;
+            for (int e = threadIdx.x; e < LPF_L * LPF_L * C4; e += BLOCK) {   // along x
+                const int i = (e % C4) * 4, zy = e / C4;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                if (row_live((zy / LPF_L) / LPF_C, (zy % LPF_L) / LPF_C)) {
+                    const float *row = R + ((size_t)h * LPF_L * LPF_L + zy) * LPF_L;
+#pragma unroll 4
+                    for (int j = 0; j < LPF_L; ++j) {
+                        const double r = (double)row[j];
+                        a0 = __fma_rn(A[(i + 0) * LPF_L + j], r, a0);
+                        a1 = __fma_rn(A[(i + 1) * LPF_L + j], r, a1);
+                        a2 = __fma_rn(A[(i + 2) * LPF_L + j], r, a2);
+                        a3 = __fma_rn(A[(i + 3) * LPF_L + j], r, a3);
+                    }
+                }
+                double *t = T1 + zy * LPF_C + i;
+                t[0] = a0;
+                t[1] = a1;
+                t[2] = a2;
+                t[3] = a3;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < LPF_L * LPF_C * LPF_C; e += BLOCK) {   // along y
-                const int x = e % LPF_C, i = (e / LPF_C) % LPF_C, z = e / (LPF_C * LPF_C);
-                double acc = 0.0;
-                for (int j = 0; j < LPF_L; ++j)
-                    acc = __dadd_rn(acc, __dmul_rn(A[i * LPF_L + j], T1[(z * LPF_L + j) * LPF_C + x]));
-                T2[e] = acc;
+            for (int e = threadIdx.x; e < LPF_L * C4 * LPF_C; e += BLOCK) {   // along y
+                const int x = e % LPF_C, i = ((e / LPF_C) % C4) * 4, z = e / (LPF_C * C4);
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                const int dz = z / LPF_C;
+                if (row_live(dz, 0) || row_live(dz, 1) || row_live(dz, 2)) {
+#pragma unroll 4
+                    for (int j = 0; j < LPF_L; ++j) {
+                        const double v = T1[(z * LPF_L + j) * LPF_C + x];
+                        a0 = __fma_rn(A[(i + 0) * LPF_L + j], v, a0);
+                        a1 = __fma_rn(A[(i + 1) * LPF_L + j], v, a1);
+                        a2 = __fma_rn(A[(i + 2) * LPF_L + j], v, a2);
+                        a3 = __fma_rn(A[(i + 3) * LPF_L + j], v, a3);
+                    }
+                }
+                double *t = T2 + (z * LPF_C + i) * LPF_C + x;
+                t[0] = a0;
+                t[LPF_C] = a1;
+                t[2 * LPF_C] = a2;
+                t[3 * LPF_C] = a3;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < BVOL; e += BLOCK) {                     // along z
-                const int x = e % LPF_C, y = (e / LPF_C) % LPF_C, i = e / (LPF_C * LPF_C);
-                double acc = 0.0;
-                for (int j = 0; j < LPF_L; ++j)
-                    acc = __dadd_rn(acc, __dmul_rn(A[i * LPF_L + j], T2[(j * LPF_C + y) * LPF_C + x]));
-                E.lpf_out[(size_t)c * 2 * BVOL + h * BVOL + e] = (float)acc;
+            for (int e = threadIdx.x; e < C4 * LPF_C * LPF_C; e += BLOCK) {   // along z
+                const int x = e % LPF_C, y = (e / LPF_C) % LPF_C, i = (e / (LPF_C * LPF_C)) * 4;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll 4
+                for (int j = 0; j < LPF_L; ++j) {
+                    const double v = T2[(j * LPF_C + y) * LPF_C + x];
+                    a0 = __fma_rn(A[(i + 0) * LPF_L + j], v, a0);
+                    a1 = __fma_rn(A[(i + 1) * LPF_L + j], v, a1);
+                    a2 = __fma_rn(A[(i + 2) * LPF_L + j], v, a2);
+                    a3 = __fma_rn(A[(i + 3) * LPF_L + j], v, a3);
+                }
+                float *o = E.lpf_out + (size_t)c * 2 * BVOL + h * BVOL + (i * LPF_C + y) * LPF_C + x;
+                o[0] = (float)a0;
+                o[LPF_C * LPF_C] = (float)a1;
+                o[2 * LPF_C * LPF_C] = (float)a2;
+                o[3 * LPF_C * LPF_C] = (float)a3;
             }
             __syncthreads();
         }
