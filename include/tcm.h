@@ -110,9 +110,8 @@ typedef struct {
                            and replayed (same kernels, same results) */
     int no_prefetch;    /* 1: no L2 prefetch in the time stepping; 0: while a warp steps a
                            brick pair it asks L2 for the next pair's field arrays and
-                           per-node k.  Same results either way; measured faster with
-                           per-node k over a compact active region, slower on a thin
-                           shell of scalar-k bricks spread over a 120 GiB pool */
+                           per-node k (bricks with per-node k only).  Same results
+                           either way */
 } tcm_options;
 
 /* Bytes of pool one box takes for this brick shape and storage (binary32:

@@ -1093,15 +1093,16 @@ __device__ void advance_steps(const Engine &E)
     }
 }
 
-// Ask L2 for the field arrays (and per-node k) of the brick this lane's
+// Ask L2 for the field arrays and per-node k of the brick this lane's
 // segment steps next, one 128-byte line per lane and array, so that the
 // stepping's loads of them find L2 instead of HBM; no registers or shared
-// memory stay held.  Only arrays that the stepping will load are named
-// (valid items; per-node k only).
+// memory stay held.  Only bricks with per-node k (three arrays to read) are
+// prefetched: measured, the prefetch pays for those and costs time on
+// bricks with a scalar k.
 template <int ST>
 __device__ __forceinline__ void prefetch_brick(const Engine &E, const WorkItem &w, bool v, int t, int age_flip)
 {
-    if (!v) return;
+    if (!v || (w.kp & KP_SCALAR)) return;
     const int nh = w.nh ^ age_flip;
     constexpr int LINE = 128;
     constexpr int HB = BVOL * (int)sizeof(typename Fld<ST>::T);
@@ -1111,11 +1112,9 @@ __device__ __forceinline__ void prefetch_brick(const Engine &E, const WorkItem &
         asm volatile("prefetch.global.L2 [%0];" ::"l"(a + o) : "memory");
         asm volatile("prefetch.global.L2 [%0];" ::"l"(b + o) : "memory");
     }
-    if (!(w.kp & KP_SCALAR)) {
-        const char *k = reinterpret_cast<const char *>(w.kp);
-        for (int o = t * LINE; o < BVOL * (int)sizeof(float); o += TPB * LINE)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(k + o) : "memory");
-    }
+    const char *k = reinterpret_cast<const char *>(w.kp);
+    for (int o = t * LINE; o < BVOL * (int)sizeof(float); o += TPB * LINE)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(k + o) : "memory");
 }
 
 template <int ST>
