@@ -578,34 +578,38 @@ def serving_leg(torch, W, args, local_rank):
 
 def end_to_end(torch, tcm, W, wl, local_rank):
     """The same metric through the public API with host buffers: velocity model
-    and wavelet from pinned host memory, 1500 steps, final field back to host."""
+    and wavelet from pinned host memory, 1500 steps, final field back to host.
+    Run twice, the faster reported (the first pays one-off costs)."""
     nz, ny, nx = wl.shape
     c_host = torch.empty(wl.shape, dtype=torch.float32, pin_memory=True)
     c_host.numpy()[...] = wl.media.c
     out_host = torch.empty(wl.shape, dtype=torch.float32, pin_memory=True)
     media = W.dense_media(c_host.numpy())
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    s = tcm.Sim(wl.shape, media, wl.dx, wl.dt, threshold=wl.tau, brick=wl.brick,
-                thr_mode=wl.thr_mode, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps,
-                pool_bytes=None, device=local_rank)
-    for x, y, z, w in wl.sources:
-        s.add_source(x, y, z, np.asarray(w, np.float32))
-    s.step(TOTAL_STEPS)
-    rc = tcm.lib().tcm_read_field(s.handle, 0, 0, 0, 0, nx, ny, nz,
-                                  tcm.C.c_void_p(out_host.data_ptr()))
-    if rc != 0:
-        raise tcm.TCMError(rc, "tcm_read_field")
-    dt = time.perf_counter() - t
-    upd = s.updates
-    s.close()
+    dts = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s = tcm.Sim(wl.shape, media, wl.dx, wl.dt, threshold=wl.tau, brick=wl.brick,
+                    thr_mode=wl.thr_mode, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps,
+                    pool_bytes=None, device=local_rank)
+        for x, y, z, w in wl.sources:
+            s.add_source(x, y, z, np.asarray(w, np.float32))
+        s.step(TOTAL_STEPS)
+        rc = tcm.lib().tcm_read_field(s.handle, 0, 0, 0, 0, nx, ny, nz,
+                                      tcm.C.c_void_p(out_host.data_ptr()))
+        if rc != 0:
+            raise tcm.TCMError(rc, "tcm_read_field")
+        dts.append(time.perf_counter() - t)
+        upd = s.updates
+        s.close()
+    dt = min(dts)
     h2d = c_host.numel() * 4 + sum(len(w) * 4 for *_, w in wl.sources)
     d2h = out_host.numel() * 4
     return {"value": upd / dt, "unit": "cell-updates/s",
             "h2d_bytes_per_step": h2d / TOTAL_STEPS, "d2h_bytes_per_step": d2h / TOTAL_STEPS,
-            "seconds": dt, "steps": TOTAL_STEPS, "cell_updates": upd,
+            "seconds": dt, "seconds_each": dts, "steps": TOTAL_STEPS, "cell_updates": upd,
             "what": "tcm_create from host velocity + tcm_add_source + tcm_step(1500) + "
-                    "tcm_read_field of the whole grid to pinned host memory"}
+                    "tcm_read_field of the whole grid to pinned host memory (best of two)"}
 
 
 def cpu_baseline(W, args, budget_s: float = 15.0, wl=None):
