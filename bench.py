@@ -664,7 +664,7 @@ def run_reference(args, rank, world):
     oracle.lib()
     threads = os.cpu_count() or 1
     used = oracle.set_threads(threads)
-    wl = W.layered(steps=TOTAL_STEPS)
+    wl = W.layered(n=args.grid, steps=TOTAL_STEPS)
     o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, brick=wl.brick, thr_mode=wl.thr_mode,
                          tau=wl.tau, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps)
     for x, y, z, w in wl.sources:
