@@ -259,6 +259,19 @@ int64_t tcm_step_index(const tcm_sim *sim);
 
 const char *tcm_status_string(tcm_status s);
 
+/* Self-test of the bounded device-wide barrier that the step and filter
+ * kernels use between their phases (the library's own failure detection;
+ * the paper has no counterpart).  One cooperative launch of one CTA per SM on
+ * device `device`; every CTA arrives once.  skew = 0: the barrier completes,
+ * TCM_OK.  skew = 1: the arrival counter starts one ahead, so the CTA that
+ * arrives last waits for a round no CTA completes; it gives up after
+ * timeout_s seconds (0 < timeout_s <= 1) and records the timeout, every CTA
+ * returns, the device stays usable, and the call returns TCM_ETIMEOUT.
+ * *err_out receives the device error bits (2 = barrier timeout).  Allocates
+ * and frees a few bytes of device memory; blocks until done.  TCM_EINVAL for
+ * bad arguments, TCM_EDEVICE if a CUDA call fails. */
+tcm_status tcm_barrier_selftest(int device, int skew, double timeout_s, unsigned *err_out);
+
 /* Destroy a simulation made by tcm_create (and its device memory).  On a
  * simulation of a batch it is tcm_batch_remove. */
 void tcm_destroy(tcm_sim *sim);

@@ -1014,6 +1014,43 @@ bool tcm_internal_view(const tcm_sim *s, SimView *v)
 
 extern "C" {
 
+tcm_status tcm_barrier_selftest(int device, int skew, double timeout_s, unsigned *err_out)
+{
+    if (!err_out || (skew != 0 && skew != 1) || !(timeout_s > 0.0) || timeout_s > 1.0) return TCM_EINVAL;
+    *err_out = 0;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return TCM_EDEVICE;
+    }
+    DeviceGuard guard(device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return TCM_EDEVICE;
+    EngineState *st = nullptr;
+    unsigned long long *ctr = nullptr;
+    cudaStream_t q = nullptr;
+    tcm_status rc = TCM_OK;
+    const unsigned long long start = (unsigned long long)skew;
+    unsigned err = 0;
+    if (cudaMalloc(&st, sizeof(EngineState)) != cudaSuccess || cudaMalloc(&ctr, sizeof(*ctr)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMemsetAsync(st, 0, sizeof(EngineState), q) != cudaSuccess ||
+        cudaMemcpyAsync(ctr, &start, sizeof(start), cudaMemcpyHostToDevice, q) != cudaSuccess ||
+        launch_barrier_selftest(st, ctr, sms, (unsigned long long)(timeout_s * 1e9), q) != cudaSuccess ||
+        cudaMemcpyAsync(&err, &st->err, sizeof(err), cudaMemcpyDeviceToHost, q) != cudaSuccess ||
+        cudaStreamSynchronize(q) != cudaSuccess)
+        rc = TCM_EDEVICE;
+    if (q) cudaStreamDestroy(q);
+    if (ctr) cudaFree(ctr);
+    if (st) cudaFree(st);
+    if (rc != TCM_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    *err_out = err;
+    return (err & ERR_TIMEOUT) ? TCM_ETIMEOUT : TCM_OK;
+}
+
 tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out)
 {
     if (!out || brick.bx != BX || brick.by != BY || brick.bz != BZ) return TCM_EINVAL;

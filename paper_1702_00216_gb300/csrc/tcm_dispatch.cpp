@@ -55,6 +55,7 @@ DECL3(int64_t, launch_count, (const void *))
 DECL3(int64_t, graph_launch_count, (const void *))
 DECL3(int64_t, step_index, (const void *))
 DECL3(const char *, status_string, (tcm_status))
+DECL3(tcm_status, barrier_selftest, (int, int, double, unsigned *))
 DECL3(void, destroy, (void *))
 DECL3(tcm_status, batch_create, (const tcm_batch_options *, void **))
 DECL3(tcm_status, batch_add, (void *, const tcm_domain *, const tcm_velocity_model *, double, double, double,
@@ -255,6 +256,12 @@ int64_t tcm_graph_launch_count(const tcm_sim *s)
 int64_t tcm_step_index(const tcm_sim *s) { return s ? SHAPE_CALL(s->shape, step_index, s->impl) : -1; }
 
 const char *tcm_status_string(tcm_status st) { return tcm_b888_status_string(st); }
+
+// The barrier does not depend on the brick shape: the 8x8x8 build runs it.
+tcm_status tcm_barrier_selftest(int device, int skew, double timeout_s, unsigned *err_out)
+{
+    return tcm_b888_barrier_selftest(device, skew, timeout_s, err_out);
+}
 
 void tcm_destroy(tcm_sim *s)
 {

@@ -225,6 +225,8 @@ __device__ __forceinline__ float load_prev_phys(const Engine &E, int slot, int n
 
 // ---- launchers (tcm_kernels.cu) -------------------------------------------
 // Every launcher returns the cudaError_t of its launch.
+cudaError_t launch_barrier_selftest(EngineState *st, unsigned long long *ctr, int grid,
+                                    unsigned long long timeout_ns, cudaStream_t s);
 // Bulking of one sim whose bricks start at global index bb.
 cudaError_t launch_bulk_classify(const MediaDev &m, int nx, int ny, int nz, int mx, int my, int mz,
                                  double dt, double dx, long long bb, float *kscal, int *kslab_of_brick,

@@ -61,10 +61,11 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 // barrier, so the barrier ends when the counter reaches the next multiple of
 // gridDim.x); thread 0 arrives with an acquire-release atomic after the
 // block's __syncthreads and waits with acquire loads, then the block
-// synchronises again.  The wait is bounded: after BARRIER_TIMEOUT_NS the
-// block records ERR_TIMEOUT and returns false, and the caller leaves the
-// kernel (the others then time out at their next barrier).
-__device__ bool grid_barrier(EngineState *st, unsigned long long *ctr)
+// synchronises again.  The wait is bounded: after timeout_ns the block
+// records ERR_TIMEOUT and returns false, and the caller leaves the kernel
+// (the others then time out at their next barrier).
+__device__ bool grid_barrier(EngineState *st, unsigned long long *ctr,
+                             unsigned long long timeout_ns = BARRIER_TIMEOUT_NS)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -78,7 +79,7 @@ __device__ bool grid_barrier(EngineState *st, unsigned long long *ctr)
         if (cur < target) {
             const unsigned long long t0 = globaltimer();
             do {
-                if (globaltimer() - t0 > BARRIER_TIMEOUT_NS) {
+                if (globaltimer() - t0 > timeout_ns) {
                     atomicOr(&st->err, ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -1863,6 +1864,25 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
 
 // Cooperative launch (every block resident at once, so the grid barriers
 // are safe) through cudaLaunchKernelEx, which stream capture accepts.
+// Self-test of the bounded barrier: every block arrives once at a counter
+// the host has set to `start`.  start = 0: the barrier completes.  start = 1:
+// the block that arrives last waits for a round no block completes and gives
+// up after timeout_ns with ERR_TIMEOUT; every block returns.
+__global__ void __launch_bounds__(BLOCK, 1) k_barrier_selftest(EngineState *st, unsigned long long *ctr,
+                                                              unsigned long long timeout_ns)
+{
+    grid_barrier(st, ctr, timeout_ns);
+}
+
+cudaError_t launch_cooperative(const void *fn, int grid, size_t smem, void **args, cudaStream_t s);
+
+cudaError_t launch_barrier_selftest(EngineState *st, unsigned long long *ctr, int grid,
+                                    unsigned long long timeout_ns, cudaStream_t s)
+{
+    void *args[] = {&st, &ctr, &timeout_ns};
+    return launch_cooperative((const void *)k_barrier_selftest, grid, 0, args, s);
+}
+
 cudaError_t launch_cooperative(const void *fn, int grid, size_t smem, void **args, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};

@@ -34,7 +34,7 @@ EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "t
            "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_graph_launch_count", "tcm_step_index",
            "tcm_status_string", "tcm_destroy", "tcm_batch_create", "tcm_batch_add",
            "tcm_batch_step", "tcm_batch_step_async", "tcm_batch_sync", "tcm_sim_done",
-           "tcm_batch_remove", "tcm_batch_info", "tcm_batch_destroy"]
+           "tcm_batch_remove", "tcm_batch_info", "tcm_batch_destroy", "tcm_barrier_selftest"]
 
 
 class tcm_domain(C.Structure):
@@ -118,6 +118,7 @@ def lib():
             "tcm_batch_remove": ([_vp, _vp], C.c_int),
             "tcm_batch_info": ([_vp, _vp, _vp, _vp], C.c_int),
             "tcm_batch_destroy": ([_vp], None),
+            "tcm_barrier_selftest": ([C.c_int, C.c_int, C.c_double, _vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -125,6 +126,14 @@ def lib():
             f.restype = res
         _LIB = L
     return _LIB
+
+
+def tcm_barrier_selftest(device: int = 0, skew: int = 0, timeout_s: float = 0.05):
+    """Run the bounded device-wide barrier once (skew 1: one arrival missing);
+    returns (status, device error bits) without raising."""
+    err = C.c_uint(0)
+    rc = lib().tcm_barrier_selftest(int(device), int(skew), float(timeout_s), C.byref(err))
+    return int(rc), int(err.value)
 
 
 def _chk(rc: int, what: str):

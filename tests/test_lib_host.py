@@ -184,3 +184,11 @@ def test_option_struct_layout_matches_header(tmp_path):
         assert got[(c_name, "size")] == ctypes.sizeof(ct)
         for f, _ in ct._fields_:
             assert got[(c_name, f)] == getattr(ct, f).offset, (c_name, f)
+
+
+def test_barrier_selftest_rejects_bad_arguments(lib):
+    """Argument checks of the barrier self-test come before any device call."""
+    for kw in ({"skew": 2}, {"skew": -1}, {"timeout_s": 0.0}, {"timeout_s": 2.0}):
+        args = {"skew": 0, "timeout_s": 0.05}
+        args.update(kw)
+        assert tcm.tcm_barrier_selftest(0, **args)[0] == tcm.TCM_EINVAL
