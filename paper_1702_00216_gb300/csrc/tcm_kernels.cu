@@ -2,7 +2,7 @@
 // (Naeh, arXiv:1702.00216).
 //
 // The hot path is one cooperative, persistent launch per time step (k_step):
-//   P1  Eq. 3 on every active brick ("Time stepping"): a half-warp owns one
+//   P1  Eq. 3 on every active brick (Time stepping section): a half-warp owns one
 //       8x8x8 brick, each lane one float4 column marching in z; the one-node
 //       halo comes from the six face neighbours' boxes (zero where a neighbour
 //       is inactive or outside the domain), the x/y neighbours inside the
@@ -11,7 +11,7 @@
 //       phi^{n+1} over phi^{n-1} (float4, coalesced) and reduces the cell
 //       maximum, six face maxima and the domain maximum with shuffles.
 //   --  device-wide barrier (bounded wait)
-//   P2  "Updating active cells": each active brick decides keep / shut-down /
+//   P2  the update procedure (Simulation section, Fig. 3a): each active brick decides keep / shut-down /
 //       release from its own maximum and its neighbours' touching faces, and
 //       claims the neighbours across faces above the trigger level
 //       (atomicCAS on Cell2box, a box popped from the free stack).
@@ -605,14 +605,16 @@ __device__ __forceinline__ int agg_add_n(int *ctr, int n)
     return base + incl - n;
 }
 
-// Trigger up to N bricks of one sim (Boxes: "Boxing new cells in vacant
-// boxes"): claim each with a CAS on Cell2box (-1 -> -2; another thread may
-// be boxing it), pop one vacant box per claim won, then publish.  All a new
-// box's record needs (the vacant box, coefficients, has-source bit from the
-// shut-down word) loads in one round after the reservation, so a won claim
-// costs three rounds of dependent accesses: the CAS, the reservation, those
-// loads.  The shut-down word of an unboxed brick is written only by the
-// thread that wins its claim.
+// Trigger up to N bricks of one sim (update procedure step 8, Fig. 1): claim
+// each with a CAS on Cell2box (-1 -> -2; another thread may be boxing it),
+// pop one vacant box per claim won, then publish.  All a new box's record
+// needs (the vacant box, coefficients, has-source bit from the shut-down
+// word) loads in one round after the reservation, so a won claim costs three
+// rounds of dependent accesses: the CAS, the reservation, those loads.  The
+// shut-down word of an unboxed brick is written only by the thread that wins
+// its claim.  Only claims that got a box take an entry of newslots (at most
+// one per box on the free stack, so never more than n_slots in a step); a
+// claim that finds the stack empty is undone and flags ERR_NOMEM.
 template <int N>
 __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_local, int n)
 {
@@ -625,27 +627,26 @@ __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_l
         if (i < n && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1) won |= 1u << i;
     if (won == 0) return;
     const int nw = __popc(won);
-    // vacant boxes free_stack[top - nw .. top - 1]
+    // vacant boxes free_stack[top - nw .. top - 1]; the first nv claims get one
     const int top = atomicSub(&E.st->free_top, nw);
-    const int nn = agg_add_n(&E.st->n_new, nw);
+    const int nv = min(max(top, 0), nw);
+    const int nn = agg_add_n(&E.st->n_new, nv);
     int k = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         if (!(won >> i & 1u)) continue;
         const long long g = bb + b_local[i];
-        const int kslab = __ldg(E.kslab_of_brick + g);
-        const float kscal = __ldg(E.kscal + g);
-        const unsigned short sdw = __ldcg(E.sd_of_brick + g);
-        const int idx = top - 1 - k;
-        const int ns = idx >= 0 ? __ldcg(E.free_stack + idx) : -1;
-        if (ns < 0) {   // no vacant box left
+        if (k >= nv) {   // no vacant box left: undo the claim
             atomicExch(E.slot_of_brick + g, -1);
             atomicOr(&E.st->err, ERR_NOMEM);
             atomicOr(&S->poisoned, 1u);
-            E.newslots[nn + k] = -1;
             ++k;
             continue;
         }
+        const int kslab = __ldg(E.kslab_of_brick + g);
+        const float kscal = __ldg(E.kscal + g);
+        const unsigned short sdw = __ldcg(E.sd_of_brick + g);
+        const int ns = __ldcg(E.free_stack + (top - 1 - k));
         E.claim_step[ns] = step;
         SlotMeta m;
         m.brick = b_local[i];
@@ -1247,12 +1248,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
     {
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
-        const int n_new = __ldcg(&st->n_new);
-        for (int i = gwarp; i < n_new; i += nwarps) {
-            const int ns = __ldcg(E.newslots + i);
-            if (ns < 0) continue;   // a claim that found no vacant box
-            zero_box(E, ns, lane);
-        }
+        const int n_new = min(__ldcg(&st->n_new), E.n_slots);
+        for (int i = gwarp; i < n_new; i += nwarps) zero_box(E, __ldcg(E.newslots + i), lane);
         const int n_ret = __ldcg(&st->n_retired);
         const int base = max(__ldcg(&st->free_top), 0);
         for (int i = gtid; i < n_ret; i += nthr) E.free_stack[base + i] = __ldcg(E.retired + i);
