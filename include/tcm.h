@@ -142,7 +142,7 @@ tcm_status tcm_add_source(tcm_sim *sim, int64_t x, int64_t y, int64_t z, const f
  * neighbours of a brick above the level).  Only before the first tcm_step. */
 tcm_status tcm_set_field(tcm_sim *sim, const float *phi_now, const float *phi_prev);
 
-/* Schedule of the update procedure ("Updating active cells", Eq. 5, Fig. 3).
+/* Schedule of the update procedure (Simulation section, Eq. 5, Fig. 3).
  * interval >= 1: the procedure runs after every interval-th step of this
  * simulation (after step n when (n+1) % interval == 0); launches in between
  * only step the active bricks.  interval = 0: Eq. 5, n = dx * L / (2 c_max
@@ -225,14 +225,20 @@ tcm_status tcm_energy(const tcm_sim *sim, double *e);
  * memory belongs to another allocator with a fixed budget, and code on a
  * latency-critical path that must not synchronise the device (freeing memory
  * does).  Its scratch is a static 512 KiB device array (one partial sum per
- * active brick) that every GPU loading the library holds until exit, so at
- * most 65536 active bricks: larger active sets return TCM_EINVAL.  The first
+ * entry of the active list) that every GPU loading the library holds until
+ * exit.  The active list is the batch's: it holds the active bricks of every
+ * simulation of the batch (a simulation made by tcm_create is a batch of
+ * one), so the limit of 65536 entries counts them all -- a longer list
+ * returns TCM_EINVAL, even for a small simulation in a busy batch.  The first
  * call on a device looks up the array's device address; make that first call
  * before any stream capture.  The array is shared by all calls and keeps the
  * last call's partial sums (each call overwrites what it reads), so calls
  * whose work overlaps on the GPU race: serialise them.  Only after the
- * simulation has started (TCM_ESTATE before); blocks for one 4-byte read of
- * the active count; the sum is in a fixed order (deterministic). */
+ * simulation has started, i.e. after its first step or read (TCM_ESTATE
+ * before); if simulations were added to or removed from its batch since the
+ * last step, the active list is rebuilt first (one kernel launch, no
+ * allocation).  Blocks for one 4-byte read of the list length; the sum is in
+ * a fixed order (deterministic). */
 tcm_status tcm_energy_noalloc(const tcm_sim *sim, double *device_out);
 
 /* Heterogenic bulking result of brick b: *kind = 1 homogenic (*k = its

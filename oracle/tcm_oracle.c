@@ -30,7 +30,7 @@ int orc_set_threads(int n)
 #endif
 }
 
-/* Media rules at one node (Media: "describe the media by rules").  Later rules
+/* Media rules at one node (Media section: media given by rules).  Later rules
  * override earlier ones: background, then layers, then spheres. */
 static float media_rule_c(int64_t i, int64_t j, int64_t l, float c_background,
                           int n_layers, const double *layer_z, const float *layer_c,

@@ -998,16 +998,24 @@ tcm_status ready_for_read(tcm_batch *b, int id)
 
 }  // namespace
 
-bool tcm_internal_view(const tcm_sim *s, SimView *v)
+bool tcm_internal_view(const tcm_sim *s, SimView *v, bool refresh_list)
 {
     HostSim *h = sim_of(s);
     if (!h || !v) return false;
-    v->E = &s->b->E;
-    v->device = s->b->device;
-    v->stream = s->b->stream;
-    v->started = h->primed && !s->b->dirty_list;
+    tcm_batch *b = s->b;
+    v->E = &b->E;
+    v->device = b->device;
+    v->stream = b->stream;
+    v->started = h->primed;
+    v->list_ok = !b->dirty_list;
+    if (refresh_list && h->primed && b->dirty_list) {
+        // an admission or removal since the last step: rebuild the active
+        // list (one compaction launch on the batch's stream; no allocation)
+        DeviceGuard g(b->device);
+        v->list_ok = ensure_list(b) == TCM_OK;
+    }
     v->step = h->step;
-    v->list_parity = s->b->list_parity;
+    v->list_parity = b->list_parity;
     v->sim = s->id;
     return true;
 }

@@ -3,7 +3,7 @@
 //
 // HBM layout of one engine (a set of simulations stepped by one launch):
 //   pool      phi[slot][half][z][y][x]   two binary32 halves of one brick per box
-//                                        (Boxes: "a space in memory ... called a box")
+//                                        (Boxes section, Fig. 1)
 //   per brick slot_of_brick[g]  int32    Cell2box (-1 inactive, -2 claim in flight)
 //             kscal[g]          float    homogenic coefficient (HBM)
 //             kslab_of_brick[g] int32    index of the bulked coefficient brick, -1 if homogenic
@@ -269,7 +269,8 @@ struct SimView {
     const Engine *E;
     int device;
     cudaStream_t stream;
-    bool started;
+    bool started;          // the simulation's initial state is on the device
+    bool list_ok;          // the active list matches the current state
     long long step;
     int list_parity;
     int sim;
@@ -278,5 +279,9 @@ struct SimView {
 }  // namespace tcm
 
 struct tcm_sim;
-// Fills *v; false when sim is NULL.  Defined in tcm_api.cu.
-__attribute__((visibility("hidden"))) bool tcm_internal_view(const tcm_sim *sim, tcm::SimView *v);
+// Fills *v; false when sim is NULL.  refresh_list: if the simulation has
+// started and its batch changed since the last step (admission, removal,
+// freeze), rebuild the active list first (one compaction launch, no device
+// allocation).  Defined in tcm_api.cu.
+__attribute__((visibility("hidden"))) bool tcm_internal_view(const tcm_sim *sim, tcm::SimView *v,
+                                                             bool refresh_list);

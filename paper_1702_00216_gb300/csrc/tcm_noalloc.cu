@@ -8,11 +8,14 @@
 // accumulator on every call; this variant keeps its scratch in a file-scope
 // __device__ array instead.
 //
-// Scratch: one FP64 partial sum per active brick, NOALLOC_MAX_BRICKS of them
-// (512 KiB), resident on every GPU that loads the library until the process
-// exits.  Every call overwrites the partials it reads, so nothing has to start
-// at zero; calls whose kernels overlap on the GPU (two streams, two
-// simulations) race on the array and must be serialised by the caller.
+// Scratch: one FP64 partial sum per entry of the batch's active list (the
+// active bricks of every simulation of the batch; a simulation made by
+// tcm_create is a batch of one), NOALLOC_MAX_BRICKS of them (512 KiB),
+// resident on every GPU that loads the library until the process exits.
+// Entries of other simulations get a zero partial.  Every call overwrites the
+// partials it reads, so nothing has to start at zero; calls whose kernels
+// overlap on the GPU (two streams, two simulations) race on the array and
+// must be serialised by the caller.
 #include "../../include/tcm.h"
 #include "tcm_internal.cuh"
 
@@ -101,8 +104,11 @@ __global__ void k_energy_total(const double *part, int n, double *out)
 extern "C" tcm_status tcm_energy_noalloc(const tcm_sim *sim, double *device_out)
 {
     tcm::SimView v;
-    if (!device_out || !tcm_internal_view(sim, &v)) return TCM_EINVAL;
+    // A started simulation whose batch changed since the last step gets its
+    // active list rebuilt first (a compaction launch, which allocates nothing).
+    if (!device_out || !tcm_internal_view(sim, &v, true)) return TCM_EINVAL;
     if (!v.started) return TCM_ESTATE;
+    if (!v.list_ok) return TCM_EDEVICE;
     if (v.device < 0 || v.device >= NOALLOC_MAX_DEVICES) return TCM_EINVAL;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return TCM_EDEVICE;
@@ -127,7 +133,7 @@ extern "C" tcm_status tcm_energy_noalloc(const tcm_sim *sim, double *device_out)
             st = TCM_EDEVICE;
             break;
         }
-        if (n > NOALLOC_MAX_BRICKS) {  // more active bricks than the scratch holds
+        if (n > NOALLOC_MAX_BRICKS) {  // a longer active list than the scratch holds
             st = TCM_EINVAL;
             break;
         }
