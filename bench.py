@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 TOTAL_STEPS = 1500
 BYTES_PER_UPDATE = 16          # read phi^n, phi^{n-1}, k; write phi^{n+1} (FP32, per-node k)
 BYTES_PER_UPDATE_16 = 12       # 16-bit velocity form: read phi^n, v^n (2 B), k (4 B); write phi, v
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_layered256_traffic.txt")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_layered512_traffic.txt")
 
 
 def env_int(name, default):
@@ -46,40 +46,103 @@ def env_int(name, default):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock and clock-event reasons during the timed region.
 
+    NVML queries (read-only) from a thread every ~1 ms, so even a region of a
+    few milliseconds gets samples; nvidia-smi every 50 ms when NVML cannot be
+    loaded.  The region starts once the first sample is in."""
+
+    # clock-event reason bits of NVML (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, pci=None):
         self.index = index
+        self.pci = pci
         self.proc = None
-        self.lines = []
+        self.samples = []          # (sm_mhz, sm_max_mhz, reasons set)
         self.first = 0
+        self.interval_ms = 1.0
+        self._stop = threading.Event()
+        self._nvml = None
+
+    def _nvml_open(self):
+        import ctypes as C
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = C.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return None
+        h = C.c_void_p()
+        ok = False
+        if self.pci:
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(self.pci.encode(), C.byref(h)) == 0
+        if not ok:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(h)) == 0
+        if not ok:
+            return None
+        smax = C.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(smax))
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, float(smax.value), reasons_fn
+
+    def _poll_nvml(self):
+        import ctypes as C
+        lib, h, smax, reasons_fn = self._nvml
+        clk, rs = C.c_uint(0), C.c_ulonglong(0)
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0 and reasons_fn(h, C.byref(rs)) == 0:
+                self.samples.append((float(clk.value), smax,
+                                     {n for b, n in self.REASONS.items() if rs.value & b}))
+            time.sleep(self.interval_ms / 1e3)
+
+    def _read_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.strip().split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm, smax = float(parts[0]), float(parts[1])
+            except ValueError:
+                continue
+            self.samples.append((sm, smax, {n for n, v in zip(names, parts[4:8]) if v.lower() == "active"}))
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+            self._nvml = self._nvml_open()
+        except Exception:
+            self._nvml = None
+        try:
+            if self._nvml is not None:
+                self.t = threading.Thread(target=self._poll_nvml, daemon=True)
+            else:
+                self.interval_ms = 50.0
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits", "-lms", "50"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.t = threading.Thread(target=self._read_smi, daemon=True)
             self.t.start()
-            # the timed region starts once sampling runs
             t0 = time.perf_counter()
-            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
-                time.sleep(0.005)
-            self.first = len(self.lines)
+            while not self.samples and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.001)
+            self.first = len(self.samples)
         except Exception:
             self.proc = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *a):
+        self.last = len(self.samples)
+        self._stop.set()
         if self.proc:
             self.proc.terminate()
             try:
@@ -88,26 +151,18 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        """Samples taken during the region (the one taken just before it when
-        the region was too short for any)."""
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        during = self.lines[self.first:]
-        lines = during if during else self.lines[-1:]
-        for ln in lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax = float(parts[1])
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 50,
+        """Samples taken during the region (the one just before it when the
+        region was too short for any)."""
+        during = self.samples[self.first:getattr(self, "last", len(self.samples))]
+        rows = during if during else self.samples[self.first - 1:self.first]
+        sm = [r[0] for r in rows]
+        reasons = set()
+        for r in rows:
+            reasons |= r[2]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": rows[-1][1] if rows else None,
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": self.interval_ms,
+                "source": "nvml" if self._nvml is not None else "nvidia-smi",
                 "during_region": bool(during)}
 
 
@@ -175,8 +230,32 @@ def run_ours(args, rank, world, local_rank):
     bpu = BYTES_PER_UPDATE if args.storage == "f32" else BYTES_PER_UPDATE_16
     pool_bytes = (args.grid // 8) ** 3 * tcm.tcm_slot_bytes(wl.brick, storage)
     pool = torch.empty(pool_bytes, dtype=torch.uint8, device=dev)
-    sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank, storage=storage)
-    t0 = max(0, TOTAL_STEPS - K - Wm)
+    if args.save_state:
+        # profiling aid: the run's state at a late step, to resume it with few
+        # launches before the ones a profiler captures
+        sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank, storage=storage,
+                                    graphs=not args.no_graphs)
+        sim.step(args.state_step)
+        np.savez(args.save_state, now=sim.read_field(0), prev=sim.read_field(1), step=args.state_step)
+        print(json.dumps({"saved_state": args.save_state, "step": args.state_step,
+                          "active_bricks": sim.active_count()[0]}), flush=True)
+        sim.close()
+        return
+    if args.load_state:
+        # resume from a saved state (its sources have ended): phi^n, phi^{n-1}
+        # become the initial fields; K timed steps after W warm-up steps
+        import dataclasses
+        st = np.load(args.load_state)
+        wl = dataclasses.replace(wl, sources=[], name=f"{wl.name} from step {int(st['step'])}")
+        sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank, storage=storage,
+                                    graphs=not args.no_graphs)
+        sim.set_field(st["now"], st["prev"])
+        del st
+        t0 = 0
+    else:
+        sim = tcm.Sim.from_workload(wl, pool_tensor=pool, device=local_rank, storage=storage,
+                                    graphs=not args.no_graphs)
+        t0 = max(0, TOTAL_STEPS - K - Wm)
     if args.trace:
         # one step at a time, recording the node updates of every launch
         with open(args.trace, "w") as f:
@@ -199,7 +278,9 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
+    props = torch.cuda.get_device_properties(local_rank)
+    pci = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+    with ClockSampler(local_rank, pci) as clk:
         ev[0].record()
         sim.step_async(K)
         ev[1].record()
@@ -238,7 +319,14 @@ def run_ours(args, rank, world, local_rank):
         e2e.update({"value": u_e / (t_e / 1e3), "seconds": t_e / 1e3, "cell_updates": u_e,
                     "h2d_bytes_per_step": e2e["h2d_bytes_per_step"] * world,
                     "d2h_bytes_per_step": e2e["d2h_bytes_per_step"] * world, "replicas": world})
-    cpu = cpu_baseline(W, args, wl=wl) if (rank == 0 and world == 1 and not args.quick) else None
+    cpu, o512 = cpu_baseline(W, args, wl=wl) if (rank == 0 and world == 1 and not args.quick) else (None, None)
+    otimes = None
+    if cpu is not None and args.oracle_timings:
+        otimes = oracle_timings(torch, tcm, W, args, local_rank, cpu, o512,
+                                extra.get("time_to_solution") if extra else None)
+    if o512 is not None:
+        o512.close()
+        del o512
     serving = serving_leg(torch, W, args, local_rank) if (rank == 0 and not args.quick and args.serving > 0) else None
     precision = precision_leg(torch, tcm, W, dev, local_rank) if (rank == 0 and not args.quick) else None
     virtual = virtual_leg(torch, tcm, W, local_rank) if (rank == 0 and not args.quick and args.virtual) else None
@@ -294,6 +382,8 @@ def run_ours(args, rank, world, local_rank):
         line["virtual_4096"] = virtual
     if tuning is not None:
         line["autotune"] = tuning
+    if otimes is not None:
+        line["oracle_time_to_solution"] = otimes
     print(json.dumps(line), flush=True)
 
 
@@ -612,18 +702,24 @@ def end_to_end(torch, tcm, W, wl, local_rank):
                     "tcm_read_field of the whole grid to pinned host memory (best of two)"}
 
 
-def cpu_baseline(W, args, budget_s: float = 15.0, wl=None):
-    """The oracle (plain C, as it stands) on the host cores: the layered 512^3
-    workload from step 0, as many steps as fit in the time budget."""
+def cpu_baseline(W, args, budget_s: float = 45.0, wl=None):
+    """The oracle (plain C, as it stands) on all host cores: the layered 512^3
+    workload from step 0 to the end of the run (its time to solution), unless
+    the time budget runs out first; then two more steps on one core and two
+    on all cores from the final state (the largest active sets), whose rates
+    give the single-core estimate.  Returns the line's cpu_baseline and the
+    final oracle (for the dense-grid windows of the timing leg)."""
     import oracle
     threads = os.cpu_count() or 1
     used = oracle.set_threads(threads)
     if wl is None:
         wl = W.layered(steps=TOTAL_STEPS)
+    t = time.perf_counter()
     o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, brick=wl.brick, thr_mode=wl.thr_mode,
                          tau=wl.tau, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps)
     for x, y, z, w in wl.sources:
         o.add_source(x, y, z, np.asarray(w, np.float32))
+    t_create = time.perf_counter() - t
     t = time.perf_counter()
     steps = 0
     while time.perf_counter() - t < budget_s and steps < TOTAL_STEPS:
@@ -631,32 +727,163 @@ def cpu_baseline(W, args, budget_s: float = 15.0, wl=None):
         steps += 10
     dt = time.perf_counter() - t
     upd = o.updates
-    # the same oracle on one core, on the next steps of the run (all cores
-    # timed on a window of the same length first, so both rates cover
-    # comparable active sets)
-    single = None
-    if steps < TOTAL_STEPS - 20:
+    t1 = time.perf_counter()
+    o.read_field(0)
+    t_read = time.perf_counter() - t1
+    rates = {}
+    for name, th in (("all_cores", threads), ("one_core", 1)):
+        oracle.set_threads(th)
         u0 = o.updates
-        t1 = time.perf_counter()
-        o.step(10)
-        all_rate = (o.updates - u0) / (time.perf_counter() - t1)
-        oracle.set_threads(1)
-        u1 = o.updates
         t2 = time.perf_counter()
-        o.step(10)
-        single = {"value": (o.updates - u1) / (time.perf_counter() - t2), "cores": 1,
-                  "all_cores_same_window": all_rate,
-                  "sample": f"steps {steps + 10}..{steps + 20} on 1 core, {steps}..{steps + 10} on all"}
+        o.step(2)
+        rates[name] = (o.updates - u0) / (time.perf_counter() - t2)
+    oracle.set_threads(threads)
+    out = {"value": upd / dt, "unit": "cell-updates/s", "cores": used, "kind": "oracle",
+           "sample": f"{wl.name}: steps 0..{steps} of {TOTAL_STEPS} ({upd} cell updates, {dt:.1f} s, "
+                     f"all cores)",
+           "time_to_solution_s": t_create + dt + t_read if steps >= TOTAL_STEPS else None,
+           "single_thread": {"value": rates["one_core"], "cores": 1,
+                             "all_cores_same_window": rates["all_cores"],
+                             "sample": f"steps {steps}..{steps + 2} on all cores, then "
+                                       f"{steps + 2}..{steps + 4} on one"}}
+    return out, o
+
+
+def oracle_timings(torch, tcm, W, args, local_rank, cpu, o512, tts):
+    """Time to solution of the oracle as it stands (create + steps + reading
+    the final field) on one host core and on all of them, beside the GPU's
+    (create + steps + device readback), for each workload: the 64^3 pulse
+    (100 steps), the 512^3 layered run (1500 steps), the first 300 steps of
+    the virtual 4096^3 domain and the 256^3 precision workload (800 steps).
+    Runs that would take minutes on the host are estimated from the rate of a
+    short window times the run's node updates, and say so."""
+    import oracle
+    threads = os.cpu_count() or 1
+
+    def gpu_run(wl, steps, dense=False):
+        best = None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            s = tcm.Sim.from_workload(wl, dense=dense, device=local_rank)
+            s.step(steps)
+            buf = torch.empty(wl.shape if wl.shape[0] * wl.shape[1] * wl.shape[2] <= 1 << 28 else (1,),
+                              dtype=torch.float32, device=f"cuda:{local_rank}")
+            if buf.numel() > 1:
+                tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            upd = s.updates
+            s.close()
+            del buf
+            best = dt if best is None else min(best, dt)
+        return best, upd
+
+    def tcm_oracle(wl, steps, th):
+        oracle.set_threads(th)
+        t = time.perf_counter()
+        o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, brick=wl.brick, thr_mode=wl.thr_mode,
+                             tau=wl.tau, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps)
+        for x, y, z, w in wl.sources:
+            o.add_source(x, y, z, np.asarray(w, np.float32))
+        o.step(steps)
+        if wl.shape[0] * wl.shape[1] * wl.shape[2] <= 1 << 28:
+            o.read_field(0)
+        dt = time.perf_counter() - t
+        upd = o.updates
+        o.close()
         oracle.set_threads(threads)
+        return dt, upd
+
+    def dense_window(wl, now, prev, steps, th, dtype=np.float32):
+        oracle.set_threads(th)
+        k = oracle.k_from_c(wl.media.c if wl.media.kind == "dense" else oracle.rules_c(wl.shape, wl.media),
+                            wl.dt, wl.dx, dtype)
+        t = time.perf_counter()
+        oracle.dense_run(k, now.astype(dtype), prev.astype(dtype), steps)
+        dt = time.perf_counter() - t
+        oracle.set_threads(threads)
+        return int(np.prod(wl.shape)) * steps / dt
+
+    out = {"cores": threads}
+    # 64^3 pulse, threshold 0: full runs
+    wl = W.small()
+    r = {"steps": wl.steps}
+    for name, th in (("one_core", 1), ("all_cores", threads)):
+        dt, upd = tcm_oracle(wl, wl.steps, th)
+        r[f"oracle_tcm_{name}_s"] = dt
+        oracle.set_threads(th)
+        k = oracle.k_from_c(np.ones(wl.shape, np.float32), wl.dt, wl.dx, np.float32)
+        z = np.zeros(wl.shape, np.float32)
+        t = time.perf_counter()
+        oracle.dense_run(k, z, z, wl.steps, [(x, y, zz, np.asarray(w, np.float32)) for x, y, zz, w in wl.sources])
+        r[f"oracle_dense_{name}_s"] = time.perf_counter() - t
+        oracle.set_threads(threads)
+    r["gpu_tcm_s"], r["cell_updates"] = gpu_run(wl, wl.steps)
+    r["gpu_dense_s"], _ = gpu_run(wl, wl.steps, dense=True)
+    out["small_64"] = r
+    # 512^3 layered run: the TCM oracle's full run on all cores is the
+    # cpu_baseline; one core and the dense grid from windows
+    upd = tts.get("tcm_cell_updates") if tts else None
+    r = {"steps": TOTAL_STEPS, "oracle_tcm_all_cores_s": cpu.get("time_to_solution_s"),
+         "gpu_tcm_s": tts.get("tcm_s") if tts else None, "gpu_dense_s": tts.get("dense_s") if tts else None}
+    if upd:
+        r["oracle_tcm_one_core_s_estimated"] = upd / cpu["single_thread"]["value"]
+    if o512 is not None:
+        wl = W.layered(steps=TOTAL_STEPS)
+        a, b = o512.read_field(0), o512.read_field(1)
+        dense_upd = int(np.prod(wl.shape)) * TOTAL_STEPS
+        for name, th in (("all_cores", threads), ("one_core", 1)):
+            rate = dense_window(wl, a, b, 1, th)
+            r[f"oracle_dense_{name}_s_estimated"] = dense_upd / rate
+        del a, b
+    r["estimated_from"] = "rate of 2 TCM steps (1500..1502) / 1 dense step from the final state x the run's updates"
+    out["layered_512"] = r
+    # virtual 4096^3, first 300 steps: full runs
+    wl = W.virtual(steps=300, pool_bytes=4 * 1024 ** 3)
+    r = {"steps": 300}
+    for name, th in (("one_core", 1), ("all_cores", threads)):
+        r[f"oracle_tcm_{name}_s"], r["cell_updates"] = tcm_oracle(wl, 300, th)
+    r["gpu_tcm_s"], _ = gpu_run(wl, 300)
+    r["dense"] = "infeasible (4096^3 x 3 x 4 B = 824 GB)"
+    out["virtual_4096_first_300"] = r
+    # 256^3 precision workload: TCM on all cores in full; one core and the
+    # FP64 dense grid (the reference of the error table) from windows
+    wl = W.precision(256, 800)
+    r = {"steps": 800}
+    r["oracle_tcm_all_cores_s"], upd = tcm_oracle(wl, 800, threads)
+    r["cell_updates"] = upd
+    r["gpu_tcm_s"], _ = gpu_run(wl, 800)
+    r["gpu_dense_s"], _ = gpu_run(wl, 800, dense=True)
+    o = oracle.OracleTCM(wl.shape, wl.media, wl.dx, wl.dt, brick=wl.brick, thr_mode=wl.thr_mode, tau=wl.tau,
+                         decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps)
+    for x, y, z, w in wl.sources:
+        o.add_source(x, y, z, np.asarray(w, np.float32))
+    o.step(780)
+    rates = {}
+    for name, th in (("all_cores", threads), ("one_core", 1)):
+        oracle.set_threads(th)
+        u0 = o.updates
+        t = time.perf_counter()
+        o.step(4)
+        rates[name] = (o.updates - u0) / (time.perf_counter() - t)
+    oracle.set_threads(threads)
+    r["oracle_tcm_one_core_s_estimated"] = upd / rates["one_core"]
+    a, b = o.read_field(0), o.read_field(1)
     o.close()
-    return {"value": upd / dt, "unit": "cell-updates/s", "cores": used, "kind": "oracle",
-            "sample": f"{wl.name}: steps 0..{steps} of {TOTAL_STEPS} ({upd} cell updates, "
-                      f"{dt:.1f} s)", "single_thread": single}
+    for name, th in (("all_cores", threads), ("one_core", 1)):
+        rate = dense_window(wl, a, b, 2, th, np.float64)
+        r[f"oracle_dense_f64_{name}_s_estimated"] = int(np.prod(wl.shape)) * 800 / rate
+    r["estimated_from"] = "rates of 4 TCM steps (780..784) and 2 FP64 dense steps x the run's updates"
+    out["precision_256"] = r
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle as the reference arm: K timed steps of the same workload
-    (from step W, after W warm-up steps), on the host cores."""
+    """The CPU oracle as the reference arm: the same K timed steps of the same
+    workload as the GPU arm (ending at step 1500, reached untimed, after W
+    untimed warm-up steps), on all host cores."""
     if rank != 0:
         return
     import oracle
@@ -669,7 +896,12 @@ def run_reference(args, rank, world):
                          tau=wl.tau, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps)
     for x, y, z, w in wl.sources:
         o.add_source(x, y, z, np.asarray(w, np.float32))
+    # the same window as the GPU arm: steps TOTAL_STEPS - K .. TOTAL_STEPS,
+    # reached untimed, after W untimed warm-up steps
+    t0 = max(0, TOTAL_STEPS - args.steps - args.warmup)
+    o.step(t0)
     o.step(args.warmup)
+    first = o.step_index
     u0 = o.updates
     t = time.perf_counter()
     o.step(args.steps)
@@ -682,10 +914,11 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": wl.name, "grid": list(wl.shape[::-1]), "brick": list(wl.brick),
-                       "timed_steps": [args.warmup, args.warmup + args.steps]},
+                       "threshold": "relative 1e-6", "decay": "alpha 0.8, 20 steps", "storage": "f32",
+                       "timed_steps": [first, first + args.steps]},
             "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": used, "kind": "oracle",
-                             "sample": f"steps {args.warmup}..{args.warmup + args.steps} of "
-                                       f"{wl.name} ({upd} cell updates)"},
+                             "sample": f"steps {first}..{first + args.steps} of {wl.name} "
+                                       f"({upd} cell updates, {dt:.1f} s; steps 0..{first} untimed)"},
             "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -705,6 +938,15 @@ def main():
     ap.add_argument("--trace", default=None,
                     help="write per-launch node updates of the untimed steps (JSON lines)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="issue every step launch directly instead of replaying CUDA graphs")
+    ap.add_argument("--save-state", default=None, metavar="FILE.npz",
+                    help="advance the run to --state-step, save phi^n and phi^{n-1}, exit")
+    ap.add_argument("--state-step", type=int, default=TOTAL_STEPS - 20)
+    ap.add_argument("--load-state", default=None, metavar="FILE.npz",
+                    help="start the timed run from a saved state (profiling: few launches before it)")
+    ap.add_argument("--oracle-timings", type=int, default=1,
+                    help="time the oracle's time to solution per workload (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="skip time-to-solution, e2e, CPU baseline and serving")
     ap.add_argument("--serving", type=int, default=120, help="requests in the serving leg (0: skip)")

@@ -249,20 +249,39 @@ def test_layered_512_first_steps_full_size():
     assert g.updates == o.updates
 
 
-def test_virtual_4096_first_steps():
-    """The virtual 4096^3 domain (never allocated densely): 120 steps of the
-    sphere-inclusion burst against the oracle, on the active window."""
-    wl = W.virtual(steps=120, pool_bytes=4 * 1024 ** 3)
-    g, o = pair(wl, pool_bytes=4 * 1024 ** 3)
-    g.step(120)
-    o.step(120)
-    ids = o.active_bricks()
-    assert np.array_equal(g.active_bricks(), ids)
+def test_virtual_4096_until_the_sphere():
+    """The virtual 4096^3 domain (never allocated densely): the sphere-
+    inclusion burst against the oracle (all host cores) at steps 120, 300 and
+    800.  By step 800 the shell has reached the c = 1.8 sphere, so bulked
+    bricks (per-node k on the sphere's surface) are boxed and compared; the
+    fields are compared over the bounding box of the active bricks, in
+    z-slabs."""
+    import os
+    oracle.set_threads(os.cpu_count() or 1)
+    wl = W.virtual(steps=800, pool_bytes=8 * 1024 ** 3)
+    g, o = pair(wl, pool_bytes=8 * 1024 ** 3)
     m = 512
-    bx, by, bz = ids % m, (ids // m) % m, ids // (m * m)
-    lo = [int(v.min()) * 8 for v in (bx, by, bz)]
-    hi = [int(v.max()) * 8 + 8 for v in (bx, by, bz)]
-    assert_same(g, o, window=(lo, [h - l for h, l in zip(hi, lo)]))
+    done = 0
+    for cp in (120, 300, 800):
+        g.step(cp - done)
+        o.step(cp - done)
+        done = cp
+        ids = o.active_bricks()
+        assert np.array_equal(g.active_bricks(), ids), cp
+        bx, by, bz = ids % m, (ids // m) % m, ids // (m * m)
+        lo = [int(v.min()) * 8 for v in (bx, by, bz)]
+        hi = [int(v.max()) * 8 + 8 for v in (bx, by, bz)]
+        for z0 in range(lo[2], hi[2], 64):
+            dz = min(64, hi[2] - z0)
+            kw = {"origin": (lo[0], lo[1], z0), "size": (hi[0] - lo[0], hi[1] - lo[1], dz)}
+            for which in (0, 1):
+                assert np.array_equal(g.read_field(which, **kw), o.read_field(which, **kw)), (cp, z0, which)
+    assert g.updates == o.updates
+    # bulked (heterogeneous) bricks took part
+    sample = ids[:: max(1, len(ids) // 4000)]
+    assert sum(1 for b in sample if g.brick_media(int(b))[0] == 2) > 0
+    g.close()
+    o.close()
 
 
 @pytest.mark.parametrize("prefetch", [True, False])
