@@ -303,8 +303,10 @@ def run_ours(args, rank, world, local_rank):
     traffic = profiled_traffic(updates / max(launches, 1)) if args.storage == "f32" else None
     sim.close()
     marginal, step_ms = None, None
-    if not args.quick and world == 1:
-        marginal, step_ms = per_cell_fit(torch, tcm, W, wl, pool, local_rank, TOTAL_STEPS - K, K,
+    if not args.quick and world == 1 and not args.load_state:
+        # over the whole run (steps 5..1500), whatever the timed window: the
+        # fit needs steps of very different active-set sizes
+        marginal, step_ms = per_cell_fit(torch, tcm, W, wl, pool, local_rank, 5, TOTAL_STEPS - 5,
                                          peaks["hbm_gbs"], storage, bpu)
     del pool
     torch.cuda.empty_cache()
@@ -362,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
         "step_ms": None if step_ms is None else {
             "p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
             "min": float(min(step_ms)), "max": float(max(step_ms)),
-            "how": "untimed replay of the timed steps, one call and one event per step"},
+            "how": "untimed replay of steps 5..1500, one call and one event per step"},
         "per_active_cell": marginal,
         "phase_ms": {"time_stepping": ph[0] / 1e6, "update_active": ph[1] / 1e6,
                      "compaction": ph[2] / 1e6},
@@ -641,28 +643,59 @@ def storage_throughput(torch, tcm, W, local_rank):
 
 
 def serving_leg(torch, W, args, local_rank):
-    """Continuous batching on the serving stream: the first N requests (grid edge
-    log-uniform 64..512, 2-6 layers, Ricker at a random node, 200..3000 steps,
-    relative threshold 1e-6, 20-step decay), Poisson arrivals at the given rate;
-    p50/p99 time to result (arrival -> result read back) and aggregate node
-    updates per second over the whole run."""
+    """Continuous batching on the serving stream (grid edge log-uniform
+    64..512, 2-6 layers, Ricker at a random node, 200..3000 steps, relative
+    threshold 1e-6, 20-step decay; FP32 and BF16 requests in one batch of
+    mixed storage, admitted by active footprint into a 2 GiB pool).  First the
+    capacity is calibrated: a burst of requests all arriving at once, served
+    to completion (requests per second).  Then the next requests of the
+    stream arrive as a Poisson process at 75 % of that capacity: p50/p99 time
+    to result (arrival -> result read back) and aggregate node updates per
+    second.  The burst is also served with admission by whole grids, for the
+    concurrency that admission reaches in the same pool."""
     from paper_1702_00216_gb300 import serve
-    reqs = W.serving_stream(n_requests=args.serving, seed=216, rate_hz=args.serving_rate)
+    n_cal, n_run = args.serving_calibrate, args.serving
+    pool = 2 * 1024 ** 3
+
+    def stream(rate):
+        reqs = W.serving_stream(n_requests=n_cal + n_run, seed=216, rate_hz=rate)
+        for r in reqs:
+            r.workload.thr_mode, r.workload.tau = 1, 1e-6
+            r.workload.decay_alpha, r.workload.decay_steps = 0.8, 20
+        return reqs
+
+    def serve_once(reqs, time_scale, admission):
+        srv = serve.Server(pool_bytes=pool, max_bricks=24 * 1024 ** 2, max_sims=512, steps_per_tick=16,
+                           device=local_rank, storages=("f32", "bf16"), admission=admission)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = srv.run(reqs, time_scale=time_scale)
+        wall = time.perf_counter() - t
+        stats = dict(srv.stats, ticks=srv.ticks, pool_boxes=srv.n_slots)
+        srv.close()
+        return res, wall, stats
+
+    burst = stream(1.0)[:n_cal]
+    res, wall, stats = serve_once(burst, 0.0, "footprint")
+    capacity = len(res) / wall
+    cal = dict(serve.summarize(res, wall), capacity_requests_per_s=capacity, **stats)
+    _, wall_d, stats_d = serve_once(burst, 0.0, "dense")
+    dense = {"wall_s": wall_d, "max_concurrent": stats_d["max_concurrent"],
+             "max_grid_bricks_running": stats_d["max_grid_bricks_running"]}
+    rate = 0.75 * capacity
+    reqs = stream(rate)[n_cal:]
+    t0 = reqs[0].arrival
     for r in reqs:
-        r.workload.thr_mode, r.workload.tau = 1, 1e-6
-        r.workload.decay_alpha, r.workload.decay_steps = 0.8, 20
-    srv = serve.Server(pool_bytes=48 * 1024 ** 3, max_bricks=24 * 1024 ** 2, max_sims=512,
-                       steps_per_tick=16, device=local_rank, storages=("f32", "bf16"))
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    res = srv.run(reqs, time_scale=1.0)
-    wall = time.perf_counter() - t
-    srv.close()
+        r.arrival -= t0
+    res, wall, stats = serve_once(reqs, 1.0, "footprint")
     out = serve.summarize(res, wall)
-    out.update({"stream": f"first {args.serving} requests of the serving stream (seed 216), "
-                          f"Poisson {args.serving_rate}/s, FP32/BF16 mix (one batch each, "
-                          f"half the pool each)",
-                "steps_per_tick": 16})
+    out.update(stats)
+    out.update({"stream": f"requests {n_cal}..{n_cal + n_run} of the serving stream (seed 216), Poisson "
+                          f"arrivals at 75 % of the calibrated capacity ({rate:.2f}/s), FP32/BF16 mix in one "
+                          f"batch of mixed storage, admission by active footprint, 2 GiB pool",
+                "rate_hz": rate, "steps_per_tick": 16, "calibration": cal,
+                "dense_admission_burst": dense})
+    torch.cuda.empty_cache()
     return out
 
 
@@ -949,8 +982,9 @@ def main():
                     help="time the oracle's time to solution per workload (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="skip time-to-solution, e2e, CPU baseline and serving")
-    ap.add_argument("--serving", type=int, default=120, help="requests in the serving leg (0: skip)")
-    ap.add_argument("--serving-rate", type=float, default=8.0, help="serving arrivals per second")
+    ap.add_argument("--serving", type=int, default=100, help="requests in the serving stream (0: skip)")
+    ap.add_argument("--serving-calibrate", type=int, default=48,
+                    help="requests of the burst that calibrates the serving capacity")
     ap.add_argument("--virtual", type=int, default=1, help="run the virtual 4096^3 leg (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -65,6 +65,12 @@ enum { TCM_THR_ABSOLUTE = 0, TCM_THR_RELATIVE = 1 };
  * rounded to nearest-even on store.  With 16-bit storage, reading phi^{n-1}
  * returns phi^n - v^n (binary32). */
 enum { TCM_STORAGE_F32 = 0, TCM_STORAGE_BF16 = 1, TCM_STORAGE_F16 = 2 };
+/* Batches only (tcm_batch_options.storage): every simulation of the batch has
+ * its own storage, chosen with tcm_set_storage (F32 by default), and all of
+ * them step in the same launches.  Boxes are sized for binary32 (the widest:
+ * 8 bytes per node), so a 16-bit simulation leaves a quarter of its boxes
+ * unused. */
+enum { TCM_STORAGE_MIXED = 3 };
 
 typedef struct {
     int64_t nx, ny, nz; /* nodes */
@@ -333,6 +339,39 @@ tcm_status tcm_batch_remove(tcm_batch *batch, tcm_sim *sim);
 
 /* Boxes in the pool and free now; simulations alive. */
 tcm_status tcm_batch_info(const tcm_batch *batch, int64_t *slots, int64_t *free_slots, int *sims);
+
+/* Field storage of a simulation of a TCM_STORAGE_MIXED batch (TCM_STORAGE_F32,
+ * _BF16 or _F16; see the storage enum).  Only before the simulation's first
+ * step (TCM_ESTATE after).  In a batch of one storage only that storage is
+ * accepted (TCM_OK, nothing changes); any other gives TCM_EINVAL.  Not in the
+ * paper: it lets requests of both precisions share one launch per step. */
+tcm_status tcm_set_storage(tcm_sim *sim, int storage);
+
+/* Pause / resume a simulation of a batch (not in the paper; a serving loop
+ * uses it to keep the pool from running out).  A paused simulation keeps its
+ * boxes, fields, shut-down counts and step index but is not stepped, so it
+ * claims no boxes; resumed, it continues exactly where it stopped (its
+ * results equal those of an uninterrupted run bit for bit).  Pausing a
+ * simulation that has done its n_steps, or one already paused, does nothing;
+ * so does resuming one that is not paused.  Takes effect at the next step
+ * call.  TCM_EINVAL for a simulation made by tcm_create; TCM_ESTATE after the
+ * batch failed. */
+tcm_status tcm_batch_pause(tcm_sim *sim);
+tcm_status tcm_batch_resume(tcm_sim *sim);
+
+/* An upper bound on the boxes the batch's stepping (not paused, not done)
+ * simulations can claim during the next `steps` steps: the unboxed cells of
+ * each simulation that lie within ceil(steps / L) + 1 cells (Chebyshev
+ * distance, L the shortest cell edge in nodes) of one of its boxed cells.
+ * It holds because Eq. 3 moves values at most one node per step and the
+ * update procedure only boxes neighbours of cells that hold values (update
+ * steps 4-5, Fig. 3).  Simulations added since the last step are started
+ * first (their initial cells boxed).  If the free boxes (tcm_batch_info) are
+ * at least this bound, the next `steps` steps cannot exhaust the pool.  One
+ * pass over the brick tables on the device; the first call allocates
+ * 2 bytes of scratch per brick of the batch's capacity; blocks until done.
+ * Not in the paper: admission control for the serving form. */
+tcm_status tcm_batch_headroom(tcm_batch *batch, int64_t steps, int64_t *boxes);
 
 void tcm_batch_destroy(tcm_batch *batch);
 

@@ -33,6 +33,7 @@ struct HostSim {
     bool used = false;     // this table entry holds a simulation
     bool primed = false;   // its initial bricks are boxed
     bool live = false;     // steps with the batch
+    bool paused = false;   // kept with its boxes, not stepping (tcm_batch_pause)
     long long nx = 0, ny = 0, nz = 0;
     int mx = 0, my = 0, mz = 0;
     long long n_bricks = 0, range_len = 0, brick_base = 0;
@@ -98,6 +99,9 @@ struct tcm_batch {
     Engine graph_engine{};
     unsigned long long graph_clock = 0;
     long long graph_launches = 0;   // launches issued through graphs
+    // scratch of tcm_batch_headroom (allocated by its first call)
+    unsigned char *reach_a = nullptr, *reach_b = nullptr;
+    unsigned long long *reach_count = nullptr;
 };
 
 namespace {
@@ -353,8 +357,11 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
                      long long max_bricks, int max_sims, tcm_batch **out)
 {
     *out = nullptr;
-    if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16) return TCM_EINVAL;
-    const size_t slot_bytes = (size_t)slot_elems(storage) * storage_bytes(storage);
+    if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16 &&
+        storage != TCM_STORAGE_MIXED)
+        return TCM_EINVAL;
+    const size_t slot_bytes = storage == TCM_STORAGE_MIXED ? (size_t)slot_elems(ST_F32) * storage_bytes(ST_F32)
+                                                           : (size_t)slot_elems(storage) * storage_bytes(storage);
     const long long n_slots_ll = (long long)(pool_bytes / slot_bytes);
     if (n_slots_ll < 1 || max_bricks < 1 || max_sims < 1 || max_sims > 65535) return TCM_EINVAL;
     if (pool_ptr && reinterpret_cast<uintptr_t>(pool_ptr) % 16 != 0) return TCM_EINVAL;
@@ -391,6 +398,7 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
     Engine &E = b->E;
     E.phi = b->pool;
     E.storage = storage;
+    E.slot_bytes = (int)slot_bytes;
     E.n_slots = b->n_slots;
     E.n_words = b->n_words;
     E.words_per_block = (int)std::max<long long>(1, (b->n_words + b->grid - 1) / b->grid);
@@ -573,6 +581,7 @@ tcm_status sim_add(tcm_batch *b, const tcm_domain *domain, const tcm_velocity_mo
     S.inv_scale = 1.f;
     S.interval = 1;
     S.neighbours = 6;
+    S.storage = b->E.storage == ST_MIXED ? ST_F32 : b->E.storage;
     h.c_max = c_max;
     h.dx = dx;
     h.dt = dt;
@@ -673,7 +682,7 @@ tcm_status sim_prime(tcm_batch *b, int id)
     HostSim &h = b->sims[id];
     if (h.primed) return TCM_OK;
     cudaStream_t q = b->stream;
-    if (b->E.storage == ST_F16) {
+    if (h.dev.storage == ST_F16) {
         // binary16 holds phi / scale: the largest initial value or source
         // sample maps to [128, 256), leaving 2^8 of headroom below 65504.
         float peak = 0.f;
@@ -702,6 +711,27 @@ tcm_status sim_prime(tcm_batch *b, int id)
     long long n_init = 0;
     if (h.dense) {
         n_init = h.n_bricks;
+    } else if (!h.have_field) {
+        // Source cells only (and, with the 26-neighbour set, the neighbourhood
+        // of each source fed before the first update): the same set the pass
+        // below finds, without a pass over the whole brick table (the virtual
+        // 4096^3 domain has 1.3e8 bricks).
+        for (const auto &src : h.sources) {
+            if (src.w.empty()) continue;
+            init.push_back(src.brick);
+            if (h.dev.neighbours != 26 || src.start > h.step + h.dev.interval - 1) continue;
+            const int cx = src.brick % h.mx, cy = (src.brick / h.mx) % h.my, cz = src.brick / (h.mx * h.my);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int ax = cx + dx, ay = cy + dy, az = cz + dz;
+                        if (ax < 0 || ay < 0 || az < 0 || ax >= h.mx || ay >= h.my || az >= h.mz) continue;
+                        init.push_back(((long long)az * h.my + ay) * h.mx + ax);
+                    }
+        }
+        std::sort(init.begin(), init.end());
+        init.erase(std::unique(init.begin(), init.end()), init.end());
+        n_init = (long long)init.size();
     } else {
         std::vector<char> mark((size_t)h.n_bricks, 0);
         for (const auto &src : h.sources)
@@ -746,7 +776,7 @@ tcm_status sim_prime(tcm_batch *b, int id)
                 packed[(size_t)(i * 2 * bvol + e)] = h.init_now[i0];
                 // binary32: phi^{-1}; velocity form (16-bit): v^0 = phi^0 - phi^{-1}
                 packed[(size_t)(i * 2 * bvol + bvol + e)] =
-                    b->E.storage == ST_F32 ? h.init_prev[i0] : h.init_now[i0] - h.init_prev[i0];
+                    h.dev.storage == ST_F32 ? h.init_prev[i0] : h.init_now[i0] - h.init_prev[i0];
             }
         }
         float *d_packed = nullptr;
@@ -1062,6 +1092,7 @@ tcm_status tcm_barrier_selftest(int device, int skew, double timeout_s, unsigned
 tcm_status tcm_slot_bytes(tcm_brick brick, int storage, size_t *out)
 {
     if (!out || brick.bx != BX || brick.by != BY || brick.bz != BZ) return TCM_EINVAL;
+    if (storage == TCM_STORAGE_MIXED) storage = TCM_STORAGE_F32;   // boxes sized for the widest
     if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16) return TCM_EINVAL;
     *out = (size_t)slot_elems(storage) * storage_bytes(storage);
     return TCM_OK;
@@ -1072,7 +1103,7 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
 {
     if (!out) return TCM_EINVAL;
     *out = nullptr;
-    if (!options) return TCM_EINVAL;
+    if (!options || options->storage == TCM_STORAGE_MIXED) return TCM_EINVAL;
     float c_max = 0.f;
     TRYS(check_sim_args(domain, velocity, dx, dt, threshold, brick, options->storage, options->threshold_mode,
                         options->decay_steps, &c_max));
@@ -1502,6 +1533,78 @@ tcm_status tcm_batch_remove(tcm_batch *b, tcm_sim *s)
     b->handles[id] = nullptr;
     if (!s->owns_batch) delete s;
     return st;
+}
+
+tcm_status tcm_set_storage(tcm_sim *s, int storage)
+{
+    HostSim *h = sim_of(s);
+    if (!h) return TCM_EINVAL;
+    if (storage != TCM_STORAGE_F32 && storage != TCM_STORAGE_BF16 && storage != TCM_STORAGE_F16) return TCM_EINVAL;
+    if (s->b->E.storage != ST_MIXED) return storage == s->b->E.storage ? TCM_OK : TCM_EINVAL;
+    if (h->primed) return TCM_ESTATE;
+    h->dev.storage = storage;
+    return TCM_OK;
+}
+
+tcm_status tcm_batch_pause(tcm_sim *s)
+{
+    HostSim *h = sim_of(s);
+    if (!h || s->owns_batch) return TCM_EINVAL;
+    tcm_batch *b = s->b;
+    if (b->poisoned) return TCM_ESTATE;
+    if (h->paused || (h->target > 0 && h->step >= h->target)) return TCM_OK;   // nothing to do
+    DeviceGuard g(b->device);
+    TRYS(sim_prime(b, s->id));
+    TRYS(freeze_sim(b, s->id));
+    h->paused = true;
+    return TCM_OK;
+}
+
+tcm_status tcm_batch_resume(tcm_sim *s)
+{
+    HostSim *h = sim_of(s);
+    if (!h || s->owns_batch) return TCM_EINVAL;
+    if (!h->paused) return TCM_OK;
+    tcm_batch *b = s->b;
+    if (b->poisoned) return TCM_ESTATE;
+    DeviceGuard g(b->device);
+    TRY(launch_thaw(b->E, s->id, h->brick_base / 32, h->range_len / 32, h->brick_base, h->n_bricks, b->stream));
+    h->paused = false;
+    h->live = true;
+    h->dev.live = 1;
+    b->dirty_list = true;
+    return TCM_OK;
+}
+
+tcm_status tcm_batch_headroom(tcm_batch *b, int64_t steps, int64_t *boxes)
+{
+    if (!b || !boxes || steps < 0) return TCM_EINVAL;
+    *boxes = 0;
+    if (b->poisoned) return TCM_ESTATE;
+    DeviceGuard g(b->device);
+    TRYS(prime_all(b));
+    bool any = false;
+    for (const auto &h : b->sims) any = any || (h.used && h.live);
+    if (!any || steps == 0) return TCM_OK;
+    if (!b->reach_a) {
+        TRYS(dalloc(b, &b->reach_a, (size_t)b->cap_bricks));
+        TRYS(dalloc(b, &b->reach_b, (size_t)b->cap_bricks));
+        TRYS(dalloc(b, &b->reach_count, 1));
+    }
+    // values move at most one node per step (Eq. 3 couples face neighbours
+    // only), so in `steps` steps they reach cells within ceil(steps / L) cells
+    // of a boxed cell, L the shortest cell edge; the update boxes at most the
+    // neighbours of such cells
+    const int L = std::min(BX, std::min(BY, BZ));
+    const long long r = (steps + L - 1) / L + 1;
+    const int rr = (int)std::min<long long>(r, 1 << 20);
+    unsigned long long count = 0;
+    TRY(cudaMemsetAsync(b->reach_count, 0, sizeof(unsigned long long), b->stream));
+    TRY(launch_reach(b->E, rr, b->reach_a, b->reach_b, b->reach_count, b->stream));
+    TRY(cudaMemcpyAsync(&count, b->reach_count, sizeof(count), cudaMemcpyDeviceToHost, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
+    *boxes = (int64_t)count;
+    return TCM_OK;
 }
 
 tcm_status tcm_batch_info(const tcm_batch *cb, int64_t *slots, int64_t *free_slots, int *sims)

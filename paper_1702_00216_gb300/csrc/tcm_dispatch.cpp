@@ -67,6 +67,10 @@ DECL3(tcm_status, sim_done, (const void *, int *))
 DECL3(tcm_status, batch_remove, (void *, void *))
 DECL3(tcm_status, batch_info, (const void *, int64_t *, int64_t *, int *))
 DECL3(void, batch_destroy, (void *))
+DECL3(tcm_status, set_storage, (void *, int))
+DECL3(tcm_status, batch_pause, (void *))
+DECL3(tcm_status, batch_resume, (void *))
+DECL3(tcm_status, batch_headroom, (void *, int64_t, int64_t *))
 
 // Call the build of `shape`.
 #define SHAPE_CALL(shape, name, ...)                                                        \
@@ -345,6 +349,32 @@ tcm_status tcm_batch_remove(tcm_batch *b, tcm_sim *s)
     const tcm_status st = SHAPE_CALL(b->shape, batch_remove, b->impl, s->impl);
     forget(s);
     return st;
+}
+
+tcm_status tcm_set_storage(tcm_sim *s, int storage)
+{
+    SIM_OK(s);
+    return SHAPE_CALL(s->shape, set_storage, s->impl, storage);
+}
+
+tcm_status tcm_batch_pause(tcm_sim *s)
+{
+    SIM_OK(s);
+    if (!s->owner) return TCM_EINVAL;
+    return SHAPE_CALL(s->shape, batch_pause, s->impl);
+}
+
+tcm_status tcm_batch_resume(tcm_sim *s)
+{
+    SIM_OK(s);
+    if (!s->owner) return TCM_EINVAL;
+    return SHAPE_CALL(s->shape, batch_resume, s->impl);
+}
+
+tcm_status tcm_batch_headroom(tcm_batch *b, int64_t steps, int64_t *boxes)
+{
+    if (!b) return TCM_EINVAL;
+    return SHAPE_CALL(b->shape, batch_headroom, b->impl, steps, boxes);
 }
 
 tcm_status tcm_batch_info(const tcm_batch *b, int64_t *slots, int64_t *free_slots, int *sims)

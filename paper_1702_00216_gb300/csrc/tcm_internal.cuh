@@ -57,6 +57,9 @@ enum { MEDIA_DENSE = 0, MEDIA_RULES = 1 };
 // Field storage of the boxes: binary32, or bfloat16 / binary16 holding
 // phi / scale (scale a power of two per simulation; compute is binary32).
 enum { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
+// A batch whose simulations each choose one of the three storages; its boxes
+// are sized for binary32 (the widest).
+constexpr int ST_MIXED = 3;
 __host__ __device__ constexpr int storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
 // Elements per box: the two field halves (phi^n, phi^{n-1}) in binary32; with
 // a 16-bit storage the velocity form keeps the two phi halves (phi^n and the
@@ -103,6 +106,8 @@ struct SimDev {
     int neighbours;        // 6: activation across hot faces; 26: all neighbours of a hot cell
     int lpf;               // 1: frequency-domain shut-down (Eq. 7) instead of the decay
     const double *lpf_a;   // LPF_C x LPF_L centre rows of the 1-D filter operator (FP64)
+    int storage;           // field storage of this sim's boxes (ST_F32 / ST_BF16 / ST_F16)
+    int pad_storage;
     // mutable (device-owned)
     long long step;        // n of phi^n
     unsigned gmax[2];      // max |phi^{n+1}| of step n in gmax[n & 1] (float bits)
@@ -149,8 +154,9 @@ constexpr int lpf_pow2(int v) { return v <= 1 ? 1 : 2 * lpf_pow2((v + 1) / 2); }
 constexpr int LPF_M = lpf_pow2(2 * LPF_L);   // at least 2x oversampling
 
 struct Engine {
-    void *phi;             // pool: slot_elems(storage) elements of `storage` per box
-    int storage;
+    void *phi;             // pool: slot_bytes per box
+    int storage;           // ST_F32 / ST_BF16 / ST_F16, or ST_MIXED (per simulation)
+    int slot_bytes;        // bytes per box
     int n_slots;
     int *slot_of_brick;
     const float *kscal;
@@ -194,33 +200,49 @@ struct MediaDev {
     const float *sph_c;
 };
 
-// Element e of box array (slot, half) -- half 0/1 a field half, V_HALF the
-// velocity (16-bit storages) -- as a physical value (x scale).
-__device__ __forceinline__ float load_phys(const Engine &E, int slot, int half, int e, float scale)
+// Field storage of simulation S's boxes.
+__host__ __device__ __forceinline__ int sim_storage(const Engine &E, const SimDev *S)
 {
-    const size_t i = (size_t)slot * slot_elems(E.storage) + (size_t)half * BVOL + e;
-    if (E.storage == ST_F32) return static_cast<const float *>(E.phi)[i] * scale;
-    const unsigned short bits = static_cast<const unsigned short *>(E.phi)[i];
-    if (E.storage == ST_BF16) return __uint_as_float((unsigned)bits << 16) * scale;
+    return E.storage == ST_MIXED ? S->storage : E.storage;
+}
+
+// First byte of box `slot`.
+__device__ __forceinline__ unsigned char *box_base(const Engine &E, int slot)
+{
+    return static_cast<unsigned char *>(E.phi) + (size_t)slot * (size_t)E.slot_bytes;
+}
+
+// Element e of box array (slot, half) -- half 0/1 a field half, V_HALF the
+// velocity (16-bit storages) -- of a box in storage st, as a physical value
+// (x scale).
+__device__ __forceinline__ float load_phys(const Engine &E, int st, int slot, int half, int e, float scale)
+{
+    const unsigned char *base = box_base(E, slot);
+    const size_t i = (size_t)half * BVOL + e;
+    if (st == ST_F32) return reinterpret_cast<const float *>(base)[i] * scale;
+    const unsigned short bits = reinterpret_cast<const unsigned short *>(base)[i];
+    if (st == ST_BF16) return __uint_as_float((unsigned)bits << 16) * scale;
     return __half2float(__ushort_as_half(bits)) * scale;
 }
 
 // Store a physical value v into element e of box half (slot, half).
-__device__ __forceinline__ void store_phys(const Engine &E, int slot, int half, int e, float v, float inv_scale)
+__device__ __forceinline__ void store_phys(const Engine &E, int st, int slot, int half, int e, float v,
+                                           float inv_scale)
 {
-    const size_t i = (size_t)slot * slot_elems(E.storage) + (size_t)half * BVOL + e;
+    unsigned char *base = box_base(E, slot);
+    const size_t i = (size_t)half * BVOL + e;
     const float s = v * inv_scale;
-    if (E.storage == ST_F32) static_cast<float *>(E.phi)[i] = s;
-    else if (E.storage == ST_BF16) static_cast<__nv_bfloat16 *>(E.phi)[i] = __float2bfloat16_rn(s);
-    else static_cast<__half *>(E.phi)[i] = __float2half_rn(s);
+    if (st == ST_F32) reinterpret_cast<float *>(base)[i] = s;
+    else if (st == ST_BF16) reinterpret_cast<__nv_bfloat16 *>(base)[i] = __float2bfloat16_rn(s);
+    else reinterpret_cast<__half *>(base)[i] = __float2half_rn(s);
 }
 
 // phi^{n-1} at element e of a box whose phi^n is in half now_half: the other
 // half in binary32; phi^n - v^n (binary32 subtraction) in the velocity form.
-__device__ __forceinline__ float load_prev_phys(const Engine &E, int slot, int now_half, int e, float scale)
+__device__ __forceinline__ float load_prev_phys(const Engine &E, int st, int slot, int now_half, int e, float scale)
 {
-    if (E.storage == ST_F32) return load_phys(E, slot, now_half ^ 1, e, scale);
-    return __fsub_rn(load_phys(E, slot, now_half, e, scale), load_phys(E, slot, V_HALF, e, scale));
+    if (st == ST_F32) return load_phys(E, st, slot, now_half ^ 1, e, scale);
+    return __fsub_rn(load_phys(E, st, slot, now_half, e, scale), load_phys(E, st, slot, V_HALF, e, scale));
 }
 
 // ---- launchers (tcm_kernels.cu) -------------------------------------------
@@ -242,6 +264,15 @@ cudaError_t launch_settle(const Engine &e, cudaStream_t s);
 cudaError_t launch_admit(const Engine &e, int sim, const long long *bricks, long long n, cudaStream_t s);
 // Take every brick of sim out of the active set (boxes stay) / release its boxes.
 cudaError_t launch_freeze(const Engine &e, int sim, long long words_begin, long long n_words, cudaStream_t s);
+// Put every boxed brick of a paused sim back into the active set (its range
+// is bricks [bb, bb + n) in words [words_begin, words_begin + n_words)).
+cudaError_t launch_thaw(const Engine &e, int sim, long long words_begin, long long n_words, long long bb,
+                        long long n, cudaStream_t s);
+// Unboxed bricks of live sims within Chebyshev distance r (in bricks) of a
+// boxed brick of the same sim, added to *count; scratch a/b hold one byte per
+// brick of the brick tables.
+cudaError_t launch_reach(const Engine &e, int r, unsigned char *a, unsigned char *b, unsigned long long *count,
+                         cudaStream_t s);
 cudaError_t launch_release(const Engine &e, int sim, long long bb, long long n, cudaStream_t s);
 // Rebuild the active list `list_parity` from the bitmap (same grid as the step).
 cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStream_t s);

@@ -293,16 +293,19 @@ struct Fld<ST_F16> {
 };
 
 // Array `half` of a box: 0/1 the field halves, V_HALF the velocity (16-bit).
-template <int ST>
+// MIX: a batch of mixed storages, whose boxes are E.slot_bytes apart.
+template <int ST, bool MIX = false>
 __device__ __forceinline__ typename Fld<ST>::T *half_ptr(const Engine &E, int slot, int half)
 {
-    return static_cast<typename Fld<ST>::T *>(E.phi) + (size_t)slot * slot_elems(ST) + (size_t)half * BVOL;
+    using T = typename Fld<ST>::T;
+    if constexpr (MIX) return reinterpret_cast<T *>(box_base(E, slot)) + (size_t)half * BVOL;
+    return static_cast<T *>(E.phi) + (size_t)slot * slot_elems(ST) + (size_t)half * BVOL;
 }
 
 // Zero one box (every array of it) with the lanes of a warp.
 __device__ __forceinline__ void zero_box(const Engine &E, int slot, int lane)
 {
-    const size_t bytes = (size_t)slot_elems(E.storage) * storage_bytes(E.storage);
+    const size_t bytes = (size_t)E.slot_bytes;
     const int n16 = (int)(bytes / 16);
     float4 *p = reinterpret_cast<float4 *>(static_cast<unsigned char *>(E.phi) + (size_t)slot * bytes);
     for (int e = lane; e < n16; e += 32) p[e] = f4zero();
@@ -333,7 +336,7 @@ __device__ __forceinline__ void flush_updates(const Engine &E, unsigned long lon
 // lanes (lane ^ 17) instead of being loaded.  Every lane of the warp calls
 // this (valid = false on a missing brick) so shuffles see full warps.
 // ---------------------------------------------------------------------------
-template <int ST>
+template <int ST, bool MIX = false>
 __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
                                          bool share_xm, bool share_xp, int age_flip, unsigned long long &cells,
                                          unsigned long long &scells, float &gacc, int &gsim, int &gnh)
@@ -362,9 +365,9 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const int xs = !valid ? -1 : (x4 == 0 ? (share_xm ? -1 : w.nb[0]) : (x4 == XQ - 1 ? (share_xp ? -1 : w.nb[1]) : -1));
     const int xs2 = (XQ == 1 && valid && !share_xp) ? w.nb[1] : -1;
     if (valid) {
-        const typename F::T *now = half_ptr<ST>(E, w.slot, nh);
+        const typename F::T *now = half_ptr<ST, MIX>(E, w.slot, nh);
         // phi^{n-1} in binary32; v^n in the velocity form (16-bit storages)
-        const typename F::T *prv = half_ptr<ST>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF);
+        const typename F::T *prv = half_ptr<ST, MIX>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF);
 #pragma unroll
         for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), sc);
 #pragma unroll
@@ -378,8 +381,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 #pragma unroll
             for (int z = 0; z < BZ; ++z) K[z] = make_float4(ks, ks, ks, ks);
         }
-        if (w.nb[4] >= 0) Zm = F::ld(half_ptr<ST>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), sc);
-        if (w.nb[5] >= 0) Zp = F::ld(half_ptr<ST>(E, w.nb[5], nh) + 4 * t, sc);
+        if (w.nb[4] >= 0) Zm = F::ld(half_ptr<ST, MIX>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), sc);
+        if (w.nb[5] >= 0) Zp = F::ld(half_ptr<ST, MIX>(E, w.nb[5], nh) + 4 * t, sc);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) {
@@ -389,7 +392,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         }
     }
     if (ys >= 0) {
-        const typename F::T *yb = half_ptr<ST>(E, ys, nh) + 4 * ((y == 0 ? BY - 1 : 0) * XQ + x4);
+        const typename F::T *yb = half_ptr<ST, MIX>(E, ys, nh) + 4 * ((y == 0 ? BY - 1 : 0) * XQ + x4);
 #pragma unroll
         for (int z = 0; z < BZ; ++z) YH[z] = F::ld(yb + 4 * z * TPB, sc);
     } else {
@@ -397,7 +400,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         for (int z = 0; z < BZ; ++z) YH[z] = f4zero();
     }
     if (xs >= 0) {
-        const typename F::T *xb = half_ptr<ST>(E, xs, nh) + y * BX + (x4 == 0 ? BX - 1 : 0);
+        const typename F::T *xb = half_ptr<ST, MIX>(E, xs, nh) + y * BX + (x4 == 0 ? BX - 1 : 0);
 #pragma unroll
         for (int z = 0; z < BZ; ++z) XH[z] = F::ld1(xb + z * BY * BX, sc);
     } else {
@@ -406,7 +409,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     }
     if constexpr (XQ == 1) {
         if (xs2 >= 0) {
-            const typename F::T *xb = half_ptr<ST>(E, xs2, nh) + y * BX;
+            const typename F::T *xb = half_ptr<ST, MIX>(E, xs2, nh) + y * BX;
 #pragma unroll
             for (int z = 0; z < BZ; ++z) XH2[z] = F::ld1(xb + z * BY * BX, sc);
         } else {
@@ -419,8 +422,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const bool decay = (w.flags & SD_MASK) != 0u;
     const bool ragged = (cx + 1) * BX > nx || (cy + 1) * BY > ny || (cz + 1) * BZ > nz;
     const int gx0 = cx * BX + 4 * x4, gy = cy * BY + y, gz0 = cz * BZ;
-    typename F::T *out = half_ptr<ST>(E, w.slot, nh ^ 1);
-    typename F::T *vout = half_ptr<ST>(E, w.slot, V_HALF);   // used by 16-bit storages only
+    typename F::T *out = half_ptr<ST, MIX>(E, w.slot, nh ^ 1);
+    typename F::T *vout = half_ptr<ST, MIX>(E, w.slot, V_HALF);   // used by 16-bit storages only
     const bool src = valid && (w.flags & FLAG_HAS_SRC);
     const long long step = src ? __ldcg(&S->step) : 0;
     const bool xrecv = (x4 == 0 && share_xm) || (x4 == XQ - 1 && share_xp);
@@ -1101,15 +1104,15 @@ __device__ void advance_steps(const Engine &E)
 // memory stay held.  Only bricks with per-node k (three arrays to read) are
 // prefetched: measured, the prefetch pays for those and costs time on
 // bricks with a scalar k.
-template <int ST>
+template <int ST, bool MIX = false>
 __device__ __forceinline__ void prefetch_brick(const Engine &E, const WorkItem &w, bool v, int t, int age_flip)
 {
     if (!v || (w.kp & KP_SCALAR)) return;
     const int nh = w.nh ^ age_flip;
     constexpr int LINE = 128;
     constexpr int HB = BVOL * (int)sizeof(typename Fld<ST>::T);
-    const char *a = reinterpret_cast<const char *>(half_ptr<ST>(E, w.slot, nh));
-    const char *b = reinterpret_cast<const char *>(half_ptr<ST>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF));
+    const char *a = reinterpret_cast<const char *>(half_ptr<ST, MIX>(E, w.slot, nh));
+    const char *b = reinterpret_cast<const char *>(half_ptr<ST, MIX>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF));
     for (int o = t * LINE; o < HB; o += TPB * LINE) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(a + o) : "memory");
         asm volatile("prefetch.global.L2 [%0];" ::"l"(b + o) : "memory");
@@ -1117,6 +1120,26 @@ __device__ __forceinline__ void prefetch_brick(const Engine &E, const WorkItem &
     const char *k = reinterpret_cast<const char *>(w.kp);
     for (int o = t * LINE; o < BVOL * (int)sizeof(float); o += TPB * LINE)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(k + o) : "memory");
+}
+
+// One pair of bricks of a warp (bricks 2j and 2j+1; one brick per warp for
+// 16-wide bricks): when the second is the x+ neighbour of the first, their
+// touching columns are exchanged instead of loaded.
+template <int ST, bool MIX>
+__device__ __forceinline__ void p1_pair(const Engine &E, const WorkItem &w, bool v, int t, int seg, int age_flip,
+                                        unsigned long long &cells, unsigned long long &scells, float &gacc,
+                                        int &gsim, int &gnh)
+{
+    bool pair_x = false;
+    const bool first = (seg & 1) == 0;
+    if constexpr (BRICKS_PER_WARP >= 2) {
+        const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
+        const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
+        pair_x = v && other_v &&
+                 (first ? (w.nb[1] >= 0 && w.nb[1] == other_slot) : (w.nb[0] >= 0 && w.nb[0] == other_slot));
+    }
+    p1_brick<ST, MIX>(E, w, v, t, seg, !first && pair_x, first && pair_x, age_flip, cells, scells, gacc, gsim,
+                      gnh);
 }
 
 template <int ST>
@@ -1169,19 +1192,28 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
             bool vnn = pnn < npairs && inn < nact;
             const WorkItem wnn = load_item(L, vnn ? inn : 0);
             vnn = vnn && wnn.slot >= 0;
-            if (E.prefetch) prefetch_brick<ST>(E, wn, vn, t, age_flip);
-            // bricks 2j and 2j+1 of the warp form a pair: is the second the x+
-            // neighbour of the first?
-            bool pair_x = false;
-            const bool first = (seg & 1) == 0;
-            if constexpr (BRICKS_PER_WARP >= 2) {
-                const int other_slot = __shfl_xor_sync(FULL, w.slot, TPB);
-                const bool other_v = __shfl_xor_sync(FULL, (int)v, TPB) != 0;
-                pair_x = v && other_v &&
-                         (first ? (w.nb[1] >= 0 && w.nb[1] == other_slot) : (w.nb[0] >= 0 && w.nb[0] == other_slot));
+            if constexpr (ST != ST_MIXED) {
+                if (E.prefetch) prefetch_brick<ST>(E, wn, vn, t, age_flip);
+                p1_pair<ST, false>(E, w, v, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
+            } else {
+                // Simulations of different storages in one launch: the warp
+                // steps the bricks of each storage present among its lanes in
+                // turn (every lane takes part in every call, so the shuffles
+                // see full warps).
+                if (E.prefetch && vn) {
+                    const int sn = __ldg(&E.sims[wn.flags >> 16].storage);
+                    if (sn == ST_F32) prefetch_brick<ST_F32, true>(E, wn, true, t, age_flip);
+                    else if (sn == ST_BF16) prefetch_brick<ST_BF16, true>(E, wn, true, t, age_flip);
+                    else prefetch_brick<ST_F16, true>(E, wn, true, t, age_flip);
+                }
+                const int sw = v ? __ldg(&E.sims[w.flags >> 16].storage) : -1;
+                if (__any_sync(FULL, sw == ST_F32))
+                    p1_pair<ST_F32, true>(E, w, v && sw == ST_F32, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
+                if (__any_sync(FULL, sw == ST_BF16))
+                    p1_pair<ST_BF16, true>(E, w, v && sw == ST_BF16, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
+                if (__any_sync(FULL, sw == ST_F16))
+                    p1_pair<ST_F16, true>(E, w, v && sw == ST_F16, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
             }
-            p1_brick<ST>(E, w, v, t, seg, !first && pair_x, first && pair_x, age_flip, cells, scells, gacc, gsim,
-                         gnh);
             pr = pn;
             w = wn;
             v = vn;
@@ -1481,6 +1513,90 @@ __global__ void k_release(Engine E, int sim, long long bb, long long n)
     if (blockIdx.x == 0 && threadIdx.x == 0) E.sims[sim].live = 0;
 }
 
+// Put a paused sim's boxed bricks back into the active set (the freeze that
+// paused it cleared its bitmap words; its boxes, fields and shut-down counts
+// stayed) and let it step again.
+__global__ void k_thaw(Engine E, int sim, long long w0, long long n_words, long long bb, long long nb)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_words; i += (long long)gridDim.x * blockDim.x) {
+        const long long w = w0 + i;
+        unsigned bits = 0u;
+        for (int j = 0; j < 32; ++j) {
+            const long long g = w * 32 + j;
+            if (g - bb < nb && E.slot_of_brick[g] >= 0) bits |= 1u << j;
+        }
+        E.bitmap[w] = bits;
+        if (bits) atomicAdd(E.blocktot + (int)(w / E.words_per_block), __popc(bits));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) E.sims[sim].live = 1;
+}
+
+// Reach of the live sims' boxed sets: the bricks a sim can box within a few
+// steps lie within Chebyshev distance r (in bricks) of a brick it has boxed
+// now.  Separable dilation of the boxed set along x, y and z over the brick
+// tables (one byte per brick); the z pass counts the unboxed bricks of the
+// dilated set.  A brick g belongs to the sim that owns its bitmap word, if it
+// lies inside that sim's range (ranges never overlap).
+__device__ __forceinline__ const SimDev *reach_sim(const Engine &E, long long g, long long &b)
+{
+    const SimDev *S = E.sims + E.sim_of_word[g >> 5];
+    b = g - S->brick_base;
+    return (S->live && b >= 0 && b < S->n_bricks) ? S : nullptr;
+}
+
+__global__ void k_reach_x(Engine E, int r, unsigned char *out)
+{
+    const long long n = E.n_words * 32;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        long long b;
+        const SimDev *S = reach_sim(E, g, b);
+        unsigned char v = 0;
+        if (S) {
+            const int cx = (int)(b % S->mx);
+            for (int d = max(-r, -cx); d <= r && cx + d < S->mx; ++d)
+                if (__ldg(E.slot_of_brick + g + d) >= 0) v = 1;
+        }
+        out[g] = v;
+    }
+}
+
+__global__ void k_reach_y(Engine E, int r, const unsigned char *in, unsigned char *out)
+{
+    const long long n = E.n_words * 32;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        long long b;
+        const SimDev *S = reach_sim(E, g, b);
+        unsigned char v = 0;
+        if (S) {
+            const int cy = (int)((b / S->mx) % S->my);
+            for (int d = max(-r, -cy); d <= r && cy + d < S->my; ++d)
+                if (in[g + (long long)d * S->mx]) v = 1;
+        }
+        out[g] = v;
+    }
+}
+
+__global__ void k_reach_z(Engine E, int r, const unsigned char *in, unsigned long long *count)
+{
+    const long long n = E.n_words * 32;
+    unsigned long long c = 0;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        long long b;
+        const SimDev *S = reach_sim(E, g, b);
+        if (!S || __ldg(E.slot_of_brick + g) >= 0) continue;
+        const long long plane = (long long)S->mx * S->my;
+        const int cz = (int)(b / plane);
+        for (int d = max(-r, -cz); d <= r && cz + d < S->mz; ++d)
+            if (in[g + (long long)d * plane]) {
+                ++c;
+                break;
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 // packed[i] = {phi^n, phi^{n-1}} of boxed global brick gids[i].
 __global__ void k_scatter_field(Engine E, const float *packed, const long long *gids, long long n, int now_half)
 {
@@ -1490,10 +1606,12 @@ __global__ void k_scatter_field(Engine E, const float *packed, const long long *
         const int r = (int)(i % (2 * BVOL));
         const int which = r / BVOL, e = r % BVOL;
         // the second array is phi^{-1} in binary32, v^0 in the velocity form
-        const int half = which == 0 ? now_half : (E.storage == ST_F32 ? (now_half ^ 1) : V_HALF);
         const long long g = gids[bi];
+        const SimDev *S = E.sims + E.sim_of_word[g >> 5];
+        const int st = sim_storage(E, S);
+        const int half = which == 0 ? now_half : (st == ST_F32 ? (now_half ^ 1) : V_HALF);
         const int slot = E.slot_of_brick[g];
-        if (slot >= 0) store_phys(E, slot, half, e, packed[i], E.sims[E.sim_of_word[g >> 5]].inv_scale);
+        if (slot >= 0) store_phys(E, st, slot, half, e, packed[i], S->inv_scale);
     }
 }
 
@@ -1510,8 +1628,9 @@ __global__ void k_read_window(Engine E, int sim, int now_half, int which, long l
             const int slot = E.slot_of_brick[S->brick_base + b];
             if (slot >= 0) {
                 const int e = (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX));
-                v = which == 0 ? load_phys(E, slot, now_half, e, S->scale)
-                               : load_prev_phys(E, slot, now_half, e, S->scale);
+                const int st = sim_storage(E, S);
+                v = which == 0 ? load_phys(E, st, slot, now_half, e, S->scale)
+                               : load_prev_phys(E, st, slot, now_half, e, S->scale);
             }
         }
         out[i] = v;
@@ -1526,7 +1645,8 @@ __device__ __forceinline__ double prev_at(const Engine &E, const SimDev *S, int 
     const long long b = ((z / BZ) * S->my + (y / BY)) * S->mx + (x / BX);
     const int slot = E.slot_of_brick[S->brick_base + b];
     if (slot < 0) return 0.0;
-    return (double)load_prev_phys(E, slot, now_half, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
+    return (double)load_prev_phys(E, sim_storage(E, S), slot, now_half,
+                                  (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
 }
 
 __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *out)
@@ -1545,8 +1665,9 @@ __global__ void k_energy(Engine E, int sim, int now_half, int parity, double *ou
         const long long y = (long long)((b / S->mx) % S->my) * BY + (e / BX) % BY;
         const long long z = (long long)(b / (S->mx * S->my)) * BZ + e / (BX * BY);
         if (x >= S->nx || y >= S->ny || z >= S->nz) continue;
-        const double a = (double)load_phys(E, slot, now_half, e, S->scale);
-        const double bb = (double)load_prev_phys(E, slot, now_half, e, S->scale);
+        const int st = sim_storage(E, S);
+        const double a = (double)load_phys(E, st, slot, now_half, e, S->scale);
+        const double bb = (double)load_prev_phys(E, st, slot, now_half, e, S->scale);
         const int nh = now_half;
         const double nb = prev_at(E, S, nh, x - 1, y, z) + prev_at(E, S, nh, x + 1, y, z) +
                           prev_at(E, S, nh, x, y - 1, z) + prev_at(E, S, nh, x, y + 1, z) +
@@ -1642,6 +1763,24 @@ cudaError_t launch_release(const Engine &e, int sim, long long bb, long long n, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_thaw(const Engine &e, int sim, long long words_begin, long long n_words, long long bb,
+                        long long n, cudaStream_t s)
+{
+    k_thaw<<<grid_for(n_words, 256), 256, 0, s>>>(e, sim, words_begin, n_words, bb, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reach(const Engine &e, int r, unsigned char *a, unsigned char *b, unsigned long long *count,
+                         cudaStream_t s)
+{
+    const long long n = e.n_words * 32;
+    const int g = grid_for(n, 256);
+    k_reach_x<<<g, 256, 0, s>>>(e, r, a);
+    k_reach_y<<<g, 256, 0, s>>>(e, r, a, b);
+    k_reach_z<<<g, 256, 0, s>>>(e, r, b, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compact(const Engine &e, int grid, int list_parity, cudaStream_t s)
 {
     k_compact<<<grid, BLOCK, 0, s>>>(e, list_parity);
@@ -1664,7 +1803,9 @@ int step_grid_size(int device)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<ST_F32>, BLOCK, 0) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<ST_BF16>, BLOCK, 0) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_step<ST_F16>, BLOCK, 0) != cudaSuccess) return 0;
-    per_sm = min(a, min(b, c));
+    int d = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_step<ST_MIXED>, BLOCK, 0) != cudaSuccess) return 0;
+    per_sm = min(min(a, d), min(b, c));
     return sms * per_sm;
 }
 
@@ -1692,12 +1833,13 @@ __device__ __forceinline__ long long lpf_neighbour(const SimDev *S, long long ba
 
 // Four consecutive elements e..e+3 (e a multiple of 4) of box half (slot,
 // half) as physical binary32 values, in one vector load.
-__device__ __forceinline__ float4 load_phys4(const Engine &E, int slot, int half, int e, float scale)
+__device__ __forceinline__ float4 load_phys4(const Engine &E, int st, int slot, int half, int e, float scale)
 {
-    const size_t i = (size_t)slot * slot_elems(E.storage) + (size_t)half * BVOL + e;
-    if (E.storage == ST_F32) return scale4(__ldcg(reinterpret_cast<const float4 *>(static_cast<const float *>(E.phi) + i)), scale);
-    const uint2 u = __ldcg(reinterpret_cast<const uint2 *>(static_cast<const unsigned short *>(E.phi) + i));
-    if (E.storage == ST_BF16) return Fld<ST_BF16>::cvt(u, scale);
+    const unsigned char *base = box_base(E, slot);
+    const size_t i = (size_t)half * BVOL + e;
+    if (st == ST_F32) return scale4(__ldcg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(base) + i)), scale);
+    const uint2 u = __ldcg(reinterpret_cast<const uint2 *>(reinterpret_cast<const unsigned short *>(base) + i));
+    if (st == ST_BF16) return Fld<ST_BF16>::cvt(u, scale);
     return Fld<ST_F16>::cvt(u, scale);
 }
 
@@ -1739,6 +1881,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
         const long long base = S->brick_base;
         const int b = (int)(g - base);
         const float sc = S->scale;
+        const int st = sim_storage(E, S);
         if (threadIdx.x < 27) {
             const int nb = threadIdx.x;
             const long long gn = lpf_neighbour(S, base, b, nb % 3 - 1, (nb / 3) % 3 - 1, nb / 9 - 1);
@@ -1753,7 +1896,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
         for (int e4 = threadIdx.x; e4 < 27 * 2 * Q; e4 += BLOCK) {
             const int nb = e4 / (2 * Q), h = (e4 / Q) & 1, loc = (e4 % Q) * 4;
             const int slot = s_nbslot[nb];
-            const float4 v = slot >= 0 ? load_phys4(E, slot, h, loc, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 v = slot >= 0 ? load_phys4(E, st, slot, h, loc, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
             const int lx = loc % BX, ly = (loc / BX) % BY, lz = loc / (BX * BY);
             *reinterpret_cast<float4 *>(R + ((h * LPF_L + (nb / 9) * LPF_C + lz) * LPF_L + ((nb / 3) % 3) * LPF_C + ly) *
                                                 LPF_L +
@@ -1848,12 +1991,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
                   z = (b / (mx * my)) * BZ + loc / (BX * BY);
         const bool in = x < S->nx && y < S->ny && z < S->nz;
         const size_t o = (size_t)c * 2 * BVOL + loc;
-        store_phys(E, slot, 0, loc, in ? E.lpf_out[o] : 0.f, S->inv_scale);
-        store_phys(E, slot, 1, loc, in ? E.lpf_out[o + BVOL] : 0.f, S->inv_scale);
-        if (E.storage != ST_F32) {
+        const int st = sim_storage(E, S);
+        store_phys(E, st, slot, 0, loc, in ? E.lpf_out[o] : 0.f, S->inv_scale);
+        store_phys(E, st, slot, 1, loc, in ? E.lpf_out[o + BVOL] : 0.f, S->inv_scale);
+        if (st != ST_F32) {
             const int nh = (int)(__ldcg(&S->step) & 1);   // the half holding phi^{n+1}
-            const float sn = load_phys(E, slot, nh, loc, S->scale), so = load_phys(E, slot, nh ^ 1, loc, S->scale);
-            store_phys(E, slot, V_HALF, loc, __fsub_rn(sn, so), S->inv_scale);
+            const float sn = load_phys(E, st, slot, nh, loc, S->scale), so = load_phys(E, st, slot, nh ^ 1, loc, S->scale);
+            store_phys(E, st, slot, V_HALF, loc, __fsub_rn(sn, so), S->inv_scale);
         }
         if (loc == 0) E.lpf_mark[slot] = 0;
     }
@@ -1917,9 +2061,10 @@ cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaS
     Engine copy = e;
     int p = parity, m = manage;
     void *args[] = {&copy, &p, &m};
-    const void *fn = e.storage == ST_BF16 ? (const void *)k_step<ST_BF16>
-                     : e.storage == ST_F16 ? (const void *)k_step<ST_F16>
-                                           : (const void *)k_step<ST_F32>;
+    const void *fn = e.storage == ST_BF16  ? (const void *)k_step<ST_BF16>
+                     : e.storage == ST_F16   ? (const void *)k_step<ST_F16>
+                     : e.storage == ST_MIXED ? (const void *)k_step<ST_MIXED>
+                                             : (const void *)k_step<ST_F32>;
     return launch_cooperative(fn, grid, 0, args, s);
 }
 

@@ -40,8 +40,8 @@ __device__ __forceinline__ double prev_node(const tcm::Engine &E, const tcm::Sim
     const long long b = ((z / BZ) * S->my + (y / BY)) * S->mx + (x / BX);
     const int slot = E.slot_of_brick[S->brick_base + b];
     if (slot < 0) return 0.0;
-    return (double)load_prev_phys(E, slot, now_half, (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)),
-                                  S->scale);
+    return (double)load_prev_phys(E, sim_storage(E, S), slot, now_half,
+                                  (int)(((z % BZ) * BY + (y % BY)) * BX + (x % BX)), S->scale);
 }
 
 // One warp per active brick: its energy contribution, reduced in a fixed
@@ -63,14 +63,15 @@ __global__ void k_energy_partials(tcm::Engine E, int sim, int now_half, int pari
             if (lane == 0) part[i] = 0.0;
             continue;
         }
+        const int st = sim_storage(E, S);
         const long long bx0 = (long long)(b % S->mx) * BX, by0 = (long long)((b / S->mx) % S->my) * BY,
                         bz0 = (long long)(b / (S->mx * S->my)) * BZ;
         double acc = 0.0;
         for (int e = lane; e < BVOL; e += 32) {
             const long long x = bx0 + e % BX, y = by0 + (e / BX) % BY, z = bz0 + e / (BX * BY);
             if (x >= S->nx || y >= S->ny || z >= S->nz) continue;
-            const double a = (double)load_phys(E, slot, now_half, e, S->scale);
-            const double bb = (double)load_prev_phys(E, slot, now_half, e, S->scale);
+            const double a = (double)load_phys(E, st, slot, now_half, e, S->scale);
+            const double bb = (double)load_prev_phys(E, st, slot, now_half, e, S->scale);
             const double nb = prev_node(E, S, ph, x - 1, y, z) + prev_node(E, S, ph, x + 1, y, z) +
                               prev_node(E, S, ph, x, y - 1, z) + prev_node(E, S, ph, x, y + 1, z) +
                               prev_node(E, S, ph, x, y, z - 1) + prev_node(E, S, ph, x, y, z + 1);

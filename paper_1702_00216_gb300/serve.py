@@ -1,25 +1,38 @@
-"""Continuous-batching request loop over running batches of simulations.
+"""Continuous-batching request loop over one running batch of simulations.
 
 Requests (workloads.Request: a simulation, its arrival time and its field
 storage) are admitted into a running batch as soon as they have arrived and
-the batch has room -- free boxes in the pool for the request's whole brick
-count (so the pool can never run out mid-run), brick-table space and a
-simulation slot.  A server runs one batch per field storage it serves
-("lanes", e.g. FP32 and BF16, each with its own share of the pool); a request
-goes to the lane of its storage and waits only behind earlier requests of
-that lane.  Each tick steps every lane with running simulations by
-`steps_per_tick` launches; a simulation stops stepping when it has done its
-steps, its result is read and it is removed, which frees its boxes and brick
-range for waiting requests.  Everything runs through the C ABI (tcm_batch_*).
+the pool can take them.  Admission is by active footprint, not by grid size:
+a simulation only holds boxes for the cells its wave occupies, so the loop
+asks the library for an upper bound on the boxes the running simulations can
+claim during the next tick (tcm_batch_headroom) and admits a request when the
+free boxes cover that bound plus the request's own (its source cells and
+their neighbourhood within one tick's reach).  Before every tick the bound is
+checked again; if the running simulations could claim more boxes than are
+free, the most recently admitted ones are paused (tcm_batch_pause: they keep
+their boxes and state and later continue unchanged) until it fits, and
+paused ones are resumed, oldest first, as boxes free up.  If nothing can run,
+the newest paused request is evicted (removed, its boxes freed) and queued
+again from the start.  So the pool never runs out in the middle of a step.
+``admission="dense"`` instead reserves a box for every brick of a request's
+grid (the comparison).
 
-Result of a request: the final phi^n on the plane z = nz // 2, its active
-(boxed) brick count and node updates; time to result = completion time -
-arrival time.
+FP32 and BF16 requests share one batch of mixed storage (each simulation its
+own storage), so one persistent launch per step, replayed from captured CUDA
+graphs, steps all of them.  Each tick steps the batch by `steps_per_tick`
+launches; a simulation stops stepping when it has done its steps, its result
+is read and it is removed, which frees its boxes, brick range and table slot.
+Everything runs through the C ABI (tcm_batch_*).
+
+Result of a request: the final phi^n on the plane z = nz // 2 (the whole
+field with keep_fields), its active (boxed) brick count and node updates;
+time to result = completion time - arrival time.
 """
 from __future__ import annotations
 
 import collections
 import dataclasses
+import math
 import time
 from typing import Callable, Dict, List, Optional, Sequence
 
@@ -40,54 +53,39 @@ class Result:
     plane: Optional[np.ndarray] = None
     field: Optional[np.ndarray] = None
     storage: str = "f32"
+    restarts: int = 0
 
     @property
     def time_to_result(self) -> float:
         return self.done - self.arrival
 
 
-class Lane:
-    """One running batch with one field storage and its capacity accounting."""
-
-    def __init__(self, storage: str, pool_bytes: int, max_bricks: int, max_sims: int, device: int):
-        self.storage = storage
-        self.batch = tcm.Batch(pool_bytes=pool_bytes, max_bricks=max_bricks, max_sims=max_sims,
-                               device=device, storage=storage)
-        self.n_slots = self.batch.info()[0]
-        self.max_bricks = max_bricks
-        self.max_sims = max_sims
-        self.reserved_boxes = 0
-        self.reserved_bricks = 0
-        self.running: Dict[int, tuple] = {}
-        self.queue: collections.deque = collections.deque()
-
-    def fits_empty(self, wl) -> bool:
-        nb = Server.bricks_of(wl)
-        return nb <= self.n_slots and (nb + 31) // 32 * 32 <= self.max_bricks
-
-    def fits(self, wl) -> bool:
-        nb = Server.bricks_of(wl)
-        return (len(self.running) < self.max_sims and self.reserved_boxes + nb <= self.n_slots
-                and self.reserved_bricks + (nb + 31) // 32 * 32 <= self.max_bricks)
+@dataclasses.dataclass
+class _Running:
+    req: object
+    sim: object
+    admitted: float
+    bricks: int
+    paused: bool = False
 
 
 class Server:
-    def __init__(self, pool_bytes: int, max_bricks: int, max_sims: int = 256,
-                 steps_per_tick: int = 8, device: int = 0, keep_fields: bool = False,
-                 clock: Optional[Callable[[], float]] = None, storage: str = "f32",
-                 storages: Optional[Sequence[str]] = None,
-                 pool_shares: Optional[Sequence[float]] = None):
-        """storage: the single lane's field storage (every request goes there).
-        storages: serve several storages, one lane each, requests routed by
-        their own storage; pool_shares splits pool_bytes, max_bricks and
-        max_sims between them (equal shares by default)."""
-        names = list(storages) if storages else [storage]
-        shares = list(pool_shares) if pool_shares else [1.0 / len(names)] * len(names)
-        assert len(shares) == len(names) and abs(sum(shares) - 1.0) < 1e-9
-        self.lanes = {n: Lane(n, int(pool_bytes * f), max(32, int(max_bricks * f)),
-                              max(1, int(round(max_sims * f))), device)
-                      for n, f in zip(names, shares)}
-        self.routed = storages is not None and len(names) > 1
+    def __init__(self, pool_bytes: int, max_bricks: int, max_sims: int = 256, steps_per_tick: int = 8,
+                 device: int = 0, keep_fields: bool = False, clock: Optional[Callable[[], float]] = None,
+                 storage: str = "f32", storages: Optional[Sequence[str]] = None, admission: str = "footprint"):
+        """storage: the field storage of every request; storages: serve these
+        storages side by side in one batch of mixed storage (requests carry
+        their own).  admission: "footprint" (default) or "dense"."""
+        names = list(dict.fromkeys(storages)) if storages else [storage]
+        self.mixed = len(names) > 1
+        self.storages = names
+        assert admission in ("footprint", "dense")
+        self.admission = admission
+        self.batch = tcm.Batch(pool_bytes=pool_bytes, max_bricks=max_bricks, max_sims=max_sims, device=device,
+                               storage="mixed" if self.mixed else names[0])
+        self.n_slots = self.batch.info()[0]
+        self.max_bricks = max_bricks
+        self.max_sims = max_sims
         self.steps_per_tick = int(steps_per_tick)
         self.keep_fields = keep_fields
         self._clock = clock or time.perf_counter
@@ -97,110 +95,179 @@ class Server:
         self.ticks = 0
         self._virtual = False
         self._scale = 1.0
+        self.running: Dict[int, _Running] = {}      # in admission order
+        self.queue: collections.deque = collections.deque()
+        self.bricks_used = 0          # brick-table space of the running requests
+        self.reserved_boxes = 0       # dense admission: boxes reserved
+        self.restarts = collections.Counter()
+        self.stats = {"max_concurrent": 0, "max_grid_bricks_running": 0, "pauses": 0, "resumes": 0,
+                      "evictions": 0, "headroom_calls": 0}
 
-    # single-lane views kept for callers that use one storage
-    @property
-    def batch(self):
-        return next(iter(self.lanes.values())).batch
-
-    @property
-    def n_slots(self):
-        return sum(l.n_slots for l in self.lanes.values())
-
-    @property
-    def reserved_boxes(self):
-        return sum(l.reserved_boxes for l in self.lanes.values())
-
-    @property
-    def reserved_bricks(self):
-        return sum(l.reserved_bricks for l in self.lanes.values())
-
-    @property
-    def running(self):
-        out = {}
-        for l in self.lanes.values():
-            out.update(l.running)
-        return out
-
-    def now(self) -> float:
-        """Seconds since the start of run(), or ticks in virtual mode."""
-        if self._virtual:
-            return float(self.ticks)
-        return self._clock() - self._t0
-
+    # ---- geometry -------------------------------------------------------
     @staticmethod
     def bricks_of(wl) -> int:
         nz, ny, nx = wl.shape
         bx, by, bz = wl.brick
         return -(-nx // bx) * -(-ny // by) * -(-nz // bz)
 
-    def lane_of(self, req) -> Lane:
-        if not self.routed:
-            return next(iter(self.lanes.values()))
-        st = getattr(req, "storage", "f32")
-        if st not in self.lanes:
-            raise ValueError(f"request {req.rid}: no lane serves storage {st!r}")
-        return self.lanes[st]
+    def reach_cells(self, brick=(8, 8, 8)) -> int:
+        """Cells within which a simulation can box new cells in one tick
+        (the radius tcm_batch_headroom uses)."""
+        return math.ceil(self.steps_per_tick / min(brick)) + 1
 
-    def fits(self, wl, lane: Optional[Lane] = None) -> bool:
-        return (lane or next(iter(self.lanes.values()))).fits(wl)
+    def new_request_bound(self, wl) -> int:
+        """Boxes a request can hold by the end of its first tick: its source
+        cells and every cell within the tick's reach of them."""
+        nz, ny, nx = wl.shape
+        bx, by, bz = wl.brick
+        m = (-(-nx // bx), -(-ny // by), -(-nz // bz))
+        r = self.reach_cells(wl.brick)
+        cells = set()
+        for x, y, z, _ in wl.sources:
+            c = (x // bx, y // by, z // bz)
+            span = [range(max(0, c[d] - r), min(m[d], c[d] + r + 1)) for d in range(3)]
+            for k in span[2]:
+                for j in span[1]:
+                    for i in span[0]:
+                        cells.add((i, j, k))
+        return min(len(cells), self.bricks_of(wl))
 
-    def admit(self, req, lane: Lane) -> None:
-        wl = req.workload
-        sim = lane.batch.add(wl, n_steps=wl.steps)
+    # ---- state ----------------------------------------------------------
+    def now(self) -> float:
+        """Seconds since the start of run(), or ticks in virtual mode."""
+        if self._virtual:
+            return float(self.ticks)
+        return self._clock() - self._t0
+
+    def free_boxes(self) -> int:
+        return self.batch.info()[1]
+
+    def headroom(self) -> int:
+        self.stats["headroom_calls"] += 1
+        return self.batch.headroom(self.steps_per_tick)
+
+    def fits_empty(self, wl) -> bool:
         nb = self.bricks_of(wl)
-        lane.reserved_boxes += nb
-        lane.reserved_bricks += (nb + 31) // 32 * 32
-        lane.running[req.rid] = (req, sim, self.now(), nb)
+        return nb <= self.n_slots and (nb + 31) // 32 * 32 <= self.max_bricks
 
-    def collect(self, lane: Lane) -> None:
-        for rid in list(lane.running):
-            req, sim, t_adm, nb = lane.running[rid]
-            if not sim.done():
+    def _table_room(self, wl) -> bool:
+        nb = self.bricks_of(wl)
+        return len(self.running) < self.max_sims and self.bricks_used + (nb + 31) // 32 * 32 <= self.max_bricks
+
+    # ---- admission ------------------------------------------------------
+    def admit(self, req) -> None:
+        wl = req.workload
+        storage = getattr(req, "storage", self.storages[0]) if self.mixed else None
+        sim = self.batch.add(wl, n_steps=wl.steps, storage=storage)
+        nb = self.bricks_of(wl)
+        self.bricks_used += (nb + 31) // 32 * 32
+        if self.admission == "dense":
+            self.reserved_boxes += nb
+        self.running[req.rid] = _Running(req, sim, self.now(), nb)
+        self.stats["max_concurrent"] = max(self.stats["max_concurrent"], len(self.running))
+        # boxes that admission by whole grids would have had to reserve
+        self.stats["max_grid_bricks_running"] = max(self.stats["max_grid_bricks_running"],
+                                                    sum(r.bricks for r in self.running.values()))
+
+    def _admit_arrived(self, time_scale: float) -> None:
+        need = None
+        free = None
+        while self.queue and self.queue[0].arrival * time_scale <= self.now() and self._table_room(self.queue[0].workload):
+            wl = self.queue[0].workload
+            if self.admission == "dense":
+                if self.reserved_boxes + self.bricks_of(wl) > self.n_slots:
+                    break
+            else:
+                if need is None:
+                    need, free = self.headroom(), self.free_boxes()
+                est = self.new_request_bound(wl)
+                if any(r.paused for r in self.running.values()) or free - need < est:
+                    break
+                need += est
+            self.admit(self.queue.popleft())
+
+    def _fit(self) -> None:
+        """Pause the newest running simulations until the boxes they can claim
+        in the next tick fit the free boxes; resume paused ones, oldest first,
+        while they still fit; evict the newest paused one if nothing runs."""
+        if self.admission == "dense" or not self.running:
+            return
+        while True:
+            free = self.free_boxes()
+            need = self.headroom()
+            live = [rid for rid, r in self.running.items() if not r.paused]
+            while need > free and len(live) > 0:
+                rid = live.pop()
+                self.batch.pause(self.running[rid].sim)
+                self.running[rid].paused = True
+                self.stats["pauses"] += 1
+                need = self.headroom()
+            for rid, r in self.running.items():
+                if not r.paused:
+                    continue
+                self.batch.resume(r.sim)
+                n2 = self.headroom()
+                if n2 > free:
+                    self.batch.pause(r.sim)
+                    break
+                r.paused = False
+                self.stats["resumes"] += 1
+                need = n2
+            if any(not r.paused for r in self.running.values()):
+                return
+            # nothing can step: give the newest paused request's boxes back and
+            # queue it again from the start
+            rid = next(reversed(self.running))
+            r = self.running.pop(rid)
+            self.batch.remove(r.sim)
+            self.bricks_used -= (r.bricks + 31) // 32 * 32
+            self.queue.appendleft(r.req)
+            self.restarts[rid] += 1
+            self.stats["evictions"] += 1
+
+    def collect(self) -> None:
+        for rid in list(self.running):
+            r = self.running[rid]
+            if not r.sim.done():
                 continue
-            wl = req.workload
+            wl = r.req.workload
             nz, ny, nx = wl.shape
-            plane = sim.read_field(0, origin=(0, 0, nz // 2), size=(nx, ny, 1))[0]
-            field = sim.read_field(0) if self.keep_fields else None
-            upd = sim.updates
-            active = sim.active_count()[0]
-            lane.batch.remove(sim)
-            lane.reserved_boxes -= nb
-            lane.reserved_bricks -= (nb + 31) // 32 * 32
+            plane = r.sim.read_field(0, origin=(0, 0, nz // 2), size=(nx, ny, 1))[0]
+            field = r.sim.read_field(0) if self.keep_fields else None
+            upd = r.sim.updates
+            active = r.sim.active_count()[0]
+            self.batch.remove(r.sim)
+            self.bricks_used -= (r.bricks + 31) // 32 * 32
+            if self.admission == "dense":
+                self.reserved_boxes -= r.bricks
             self.updates += upd
-            self.results.append(Result(rid, req.arrival * self._scale, t_adm, self.now(), wl.steps, upd,
-                                       active, plane, field, lane.storage))
-            del lane.running[rid]
+            storage = getattr(r.req, "storage", self.storages[0]) if self.mixed else self.storages[0]
+            self.results.append(Result(rid, r.req.arrival * self._scale, r.admitted, self.now(), wl.steps, upd,
+                                       active, plane, field, storage, self.restarts[rid]))
+            del self.running[rid]
 
     def run(self, requests, time_scale: float = 1.0, virtual: bool = False) -> List[Result]:
         """Serve requests (sorted by arrival, seconds x time_scale).  virtual=True
         admits by tick count instead of wall-clock time (arrival = tick index)."""
         for r in sorted(requests, key=lambda r: r.arrival):
-            lane = self.lane_of(r)
-            if not lane.fits_empty(r.workload):
+            if not self.fits_empty(r.workload):
                 raise RuntimeError(f"request {r.rid} can never fit this server")
-            lane.queue.append(r)
+            if self.mixed and getattr(r, "storage", "f32") not in self.storages:
+                raise ValueError(f"request {r.rid}: storage {r.storage!r} not served")
+            self.queue.append(r)
         self._t0 = self._clock()
         self._virtual = bool(virtual)
         self._scale = float(time_scale)
-        lanes = list(self.lanes.values())
-        while any(l.queue or l.running for l in lanes):
-            t = self.now()
-            # admit everything that has arrived and fits, in arrival order per lane
-            for l in lanes:
-                while l.queue and l.queue[0].arrival * time_scale <= t and l.fits(l.queue[0].workload):
-                    self.admit(l.queue.popleft(), l)
-            busy = [l for l in lanes if l.running]
-            if busy:
-                for l in busy:
-                    l.batch.step_async(self.steps_per_tick)
-                for l in busy:
-                    l.batch.sync()
+        while self.queue or self.running:
+            self._admit_arrived(time_scale)
+            self._fit()
+            if self.running:
+                self.batch.step_async(self.steps_per_tick)
+                self.batch.sync()
                 self.ticks += 1
-                for l in busy:
-                    self.collect(l)
+                self.collect()
             else:
-                nxt = min(l.queue[0].arrival for l in lanes if l.queue) * time_scale
+                nxt = self.queue[0].arrival * time_scale
                 if virtual:
                     self.ticks = max(self.ticks + 1, int(np.ceil(nxt)))
                 else:
@@ -210,8 +277,7 @@ class Server:
         return self.results
 
     def close(self):
-        for l in self.lanes.values():
-            l.batch.close()
+        self.batch.close()
 
 
 def summarize(results: List[Result], wall_s: float) -> dict:

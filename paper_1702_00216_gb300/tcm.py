@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(HERE, "libtcm.so")
 TCM_OK, TCM_EINVAL, TCM_ECFL, TCM_ENOMEM, TCM_EDEVICE, TCM_ETIMEOUT, TCM_ESTATE = range(7)
 TCM_MEDIA_DENSE, TCM_MEDIA_RULES = 0, 1
 TCM_THR_ABSOLUTE, TCM_THR_RELATIVE = 0, 1
-TCM_STORAGE_F32, TCM_STORAGE_BF16, TCM_STORAGE_F16 = 0, 1, 2
-STORAGES = {"f32": TCM_STORAGE_F32, "bf16": TCM_STORAGE_BF16, "f16": TCM_STORAGE_F16}
+TCM_STORAGE_F32, TCM_STORAGE_BF16, TCM_STORAGE_F16, TCM_STORAGE_MIXED = 0, 1, 2, 3
+STORAGES = {"f32": TCM_STORAGE_F32, "bf16": TCM_STORAGE_BF16, "f16": TCM_STORAGE_F16, "mixed": TCM_STORAGE_MIXED}
 
 
 def storage_code(storage) -> int:
@@ -34,7 +34,8 @@ EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "t
            "tcm_brick_media", "tcm_pool_info", "tcm_phase_ns", "tcm_launch_count", "tcm_graph_launch_count", "tcm_step_index",
            "tcm_status_string", "tcm_destroy", "tcm_batch_create", "tcm_batch_add",
            "tcm_batch_step", "tcm_batch_step_async", "tcm_batch_sync", "tcm_sim_done",
-           "tcm_batch_remove", "tcm_batch_info", "tcm_batch_destroy", "tcm_barrier_selftest"]
+           "tcm_batch_remove", "tcm_batch_info", "tcm_batch_destroy", "tcm_barrier_selftest",
+           "tcm_set_storage", "tcm_batch_pause", "tcm_batch_resume", "tcm_batch_headroom"]
 
 
 class tcm_domain(C.Structure):
@@ -119,6 +120,10 @@ def lib():
             "tcm_batch_info": ([_vp, _vp, _vp, _vp], C.c_int),
             "tcm_batch_destroy": ([_vp], None),
             "tcm_barrier_selftest": ([C.c_int, C.c_int, C.c_double, _vp], C.c_int),
+            "tcm_set_storage": ([_vp, C.c_int], C.c_int),
+            "tcm_batch_pause": ([_vp], C.c_int),
+            "tcm_batch_resume": ([_vp], C.c_int),
+            "tcm_batch_headroom": ([_vp, _i64, _vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -360,6 +365,24 @@ def tcm_batch_destroy(b):
     lib().tcm_batch_destroy(b)
 
 
+def tcm_set_storage(h, storage):
+    _chk(lib().tcm_set_storage(h, storage_code(storage)), "tcm_set_storage")
+
+
+def tcm_batch_pause(h):
+    _chk(lib().tcm_batch_pause(h), "tcm_batch_pause")
+
+
+def tcm_batch_resume(h):
+    _chk(lib().tcm_batch_resume(h), "tcm_batch_resume")
+
+
+def tcm_batch_headroom(b, steps) -> int:
+    n = C.c_int64(0)
+    _chk(lib().tcm_batch_headroom(b, int(steps), C.byref(n)), "tcm_batch_headroom")
+    return n.value
+
+
 # ---- convenience wrapper ----------------------------------------------------
 def _torch():
     try:
@@ -557,11 +580,14 @@ class Batch:
         self._h = tcm_batch_create(o)
         self._sims = []
 
-    def add(self, wl, n_steps=0, dense=False):
-        """Add a workloads.Workload (with its sources); returns a Sim bound to the batch."""
+    def add(self, wl, n_steps=0, dense=False, storage=None):
+        """Add a workloads.Workload (with its sources); returns a Sim bound to the
+        batch.  storage: the simulation's field storage in a mixed batch."""
         h = tcm_batch_add(self._h, wl.shape, wl.media, wl.dx, wl.dt, wl.tau, wl.brick, wl.thr_mode,
                           wl.decay_alpha, wl.decay_steps, dense=dense, n_steps=n_steps)
         sim = Sim._wrap(h, wl.shape, wl.brick)
+        if storage is not None:
+            tcm_set_storage(h, storage)
         for x, y, z, w in wl.sources:
             sim.add_source(x, y, z, np.asarray(w, dtype=np.float32))
         if (getattr(wl, "interval", 1), getattr(wl, "neighbours", 6)) != (1, 6):
@@ -588,6 +614,16 @@ class Batch:
     def info(self):
         """(boxes in the pool, free boxes, simulations alive)."""
         return tcm_batch_info(self._h)
+
+    def pause(self, sim):
+        tcm_batch_pause(sim._h)
+
+    def resume(self, sim):
+        tcm_batch_resume(sim._h)
+
+    def headroom(self, steps) -> int:
+        """Upper bound on the boxes the stepping simulations can claim in `steps` steps."""
+        return tcm_batch_headroom(self._h, steps)
 
     @property
     def handle(self):

@@ -52,8 +52,10 @@ def test_slot_bytes(lib):
     for bad in ((8, 8, 16), (4, 4, 8), (2, 2, 2)):
         with pytest.raises(tcm.TCMError):
             tcm.tcm_slot_bytes(bad)
+        # a batch of mixed storages: boxes sized for binary32
+        assert tcm.tcm_slot_bytes(brick, tcm.TCM_STORAGE_MIXED) == 2 * n * 4
     with pytest.raises(tcm.TCMError):
-        tcm.tcm_slot_bytes((8, 8, 8), 3)
+        tcm.tcm_slot_bytes((8, 8, 8), 4)
     with pytest.raises(tcm.TCMError) as e:
         tcm.tcm_slot_bytes((8, 8, 4))
     assert e.value.status == tcm.TCM_EINVAL

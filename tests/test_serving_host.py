@@ -1,16 +1,28 @@
-"""Host logic of the serving loop (admission, reservations, completion) with
-a fake batch in place of the GPU library."""
+"""Host logic of the serving loop (admission by footprint or by grid,
+pausing, resuming, eviction, completion) with a fake batch in place of the
+GPU library.  The fake boxes cells the way a pulse does -- a few at the start,
+a bounded number more per step -- and fails loudly if the pool would run out,
+so a correct loop never trips it."""
 import numpy as np
+import pytest
 
 from paper_1702_00216_gb300 import serve
 from paper_1702_00216_gb300 import workloads as W
 
+GROWTH = 6          # cells a fake simulation boxes per step
+
 
 class FakeSim:
-    def __init__(self, wl):
+    def __init__(self, wl, batch):
         self.wl = wl
+        self.batch = batch
         self.step_index = 0
         self.updates = 0
+        self.nb = serve.Server.bricks_of(wl)
+        self.boxed = 0
+        self.started = False
+        self.paused = False
+        self.storage = None
 
     def done(self):
         return self.step_index >= self.wl.steps
@@ -21,14 +33,17 @@ class FakeSim:
         return np.zeros((size[2], size[1], size[0]), np.float32)
 
     def active_count(self):
-        return (1, 512)
+        return (self.boxed, self.boxed * 512)
+
+    def live(self):
+        return not self.paused and not self.done()
 
 
 class FakeBatch:
     made = []
 
     def __init__(self, pool_bytes, max_bricks, max_sims, device=0, storage="f32"):
-        self.slots = pool_bytes // (4096 if storage == "f32" else 2048)
+        self.slots = pool_bytes // (2048 * 3 // 2 if storage in ("bf16", "f16") else 4096)
         self.storage = storage
         self.max_sims = max_sims
         FakeBatch.made.append(self)
@@ -36,22 +51,49 @@ class FakeBatch:
         self.peak = 0
         self.events = []
 
-    def info(self):
-        return (self.slots, self.slots, len(self.sims))
+    def used(self):
+        return sum(s.boxed for s in self.sims)
 
-    def add(self, wl, n_steps=0, dense=False):
-        s = FakeSim(wl)
+    def _start(self):
+        for s in self.sims:
+            if not s.started:
+                s.started = True
+                s.boxed = min(s.nb, len(s.wl.sources))
+                assert self.used() <= self.slots, "pool exhausted at admission"
+
+    def info(self):
+        return (self.slots, self.slots - self.used(), len(self.sims))
+
+    def headroom(self, steps):
+        self._start()
+        return sum(min(s.nb - s.boxed, GROWTH * steps) for s in self.sims if s.live())
+
+    def add(self, wl, n_steps=0, dense=False, storage=None):
+        s = FakeSim(wl, self)
+        s.storage = storage
         self.sims.append(s)
         self.peak = max(self.peak, len(self.sims))
         self.events.append(("add", wl.name))
         return s
 
+    def pause(self, sim):
+        sim.paused = True
+        self.events.append(("pause", sim.wl.name))
+
+    def resume(self, sim):
+        sim.paused = False
+        self.events.append(("resume", sim.wl.name))
+
     def step(self, n):
-        for s in self.sims:
-            if not s.done():
-                k = min(n, s.wl.steps - s.step_index)
-                s.step_index += k
-                s.updates += k * 512
+        self._start()
+        for _ in range(n):
+            for s in self.sims:
+                if s.live():
+                    s.step_index += 1
+                    s.updates += s.boxed * 512
+                    s.boxed = min(s.nb, s.boxed + GROWTH)
+            if self.used() > self.slots:
+                raise RuntimeError("pool exhausted in the middle of a step")
 
     def step_async(self, n):
         self.step(n)
@@ -67,23 +109,101 @@ class FakeBatch:
         pass
 
 
-def test_admission_respects_capacity_and_finishes_everything(monkeypatch):
+@pytest.fixture
+def fake(monkeypatch):
+    FakeBatch.made = []
     monkeypatch.setattr(serve.tcm, "Batch", FakeBatch)
-    reqs = W.serving_stream(n_requests=40, seed=3, edge_lo=16, edge_hi=64, steps_lo=10,
-                            steps_hi=60, rate_hz=2.0)
-    # 64^3 grid = 512 bricks; capacity of 1200 boxes holds two large requests at most
-    srv = serve.Server(pool_bytes=1200 * 4096, max_bricks=4096, max_sims=5, steps_per_tick=5)
-    res = srv.run(reqs, time_scale=1.0, virtual=True)
-    assert sorted(r.rid for r in res) == [r.rid for r in reqs]
-    assert srv.batch.peak <= 5
-    assert srv.reserved_boxes == 0 and srv.reserved_bricks == 0 and not srv.running
+
+
+def stream(n, seed, **kw):
+    kw.setdefault("edge_lo", 16)
+    kw.setdefault("edge_hi", 64)
+    kw.setdefault("steps_lo", 10)
+    kw.setdefault("steps_hi", 60)
+    kw.setdefault("rate_hz", 2.0)
+    return W.serving_stream(n_requests=n, seed=seed, **kw)
+
+
+def check_done(srv, res, reqs):
+    assert sorted(r.rid for r in res) == sorted(r.rid for r in reqs)
+    assert not srv.running and srv.bricks_used == 0
     for r in res:
-        q = reqs[r.rid]
-        assert r.steps == q.workload.steps and r.cell_updates == q.workload.steps * 512
-        assert r.admitted >= 0 and r.done >= r.admitted
-    # admission order is arrival order
-    adds = [e[1] for e in srv.batch.events if e[0] == "add"]
-    assert adds == [q.workload.name for q in sorted(reqs, key=lambda q: q.arrival)]
+        q = next(x for x in reqs if x.rid == r.rid)
+        assert r.steps == q.workload.steps and r.admitted >= 0 and r.done >= r.admitted
+
+
+def test_footprint_admission_finishes_everything_and_never_exhausts(fake):
+    reqs = stream(40, 3)
+    # 64^3 grid = 512 cells: admitted by grid, 1200 boxes hold two such requests
+    srv = serve.Server(pool_bytes=1200 * 4096, max_bricks=1 << 16, max_sims=16, steps_per_tick=5)
+    res = srv.run(reqs, time_scale=1.0, virtual=True)
+    check_done(srv, res, reqs)
+    b = FakeBatch.made[-1]
+    assert b.peak <= 16
+    # admission follows arrival order (no request overtakes an earlier one)
+    adds = [e[1] for e in b.events if e[0] == "add"]
+    first = {}
+    for i, name in enumerate(adds):
+        first.setdefault(name, i)
+    order = sorted(first, key=first.get)
+    assert order == [q.workload.name for q in sorted(reqs, key=lambda q: q.arrival)]
+
+
+def test_footprint_holds_more_simulations_than_dense_admission(fake):
+    reqs = stream(30, 5, rate_hz=50.0, edge_lo=48, edge_hi=64, steps_lo=40, steps_hi=80)
+    peaks = {}
+    for adm in ("dense", "footprint"):
+        srv = serve.Server(pool_bytes=1500 * 4096, max_bricks=1 << 16, max_sims=32, steps_per_tick=4,
+                           admission=adm)
+        res = srv.run(reqs, time_scale=1.0, virtual=True)
+        check_done(srv, res, reqs)
+        peaks[adm] = srv.stats["max_concurrent"]
+    assert peaks["dense"] <= 1500 // 216 + 1          # 48^3 = 216 cells at least each
+    assert peaks["footprint"] >= 2 * peaks["dense"], peaks
+
+
+def test_pauses_and_resumes_when_growth_outruns_the_pool(fake):
+    # few boxes, many long requests arriving together: running simulations
+    # outgrow the free boxes and must be paused, then resumed
+    reqs = stream(12, 9, rate_hz=1000.0, edge_lo=40, edge_hi=48, steps_lo=60, steps_hi=90)
+    srv = serve.Server(pool_bytes=400 * 4096, max_bricks=1 << 16, max_sims=12, steps_per_tick=6)
+    res = srv.run(reqs, time_scale=1.0, virtual=True)
+    check_done(srv, res, reqs)
+    assert srv.stats["pauses"] > 0 and srv.stats["resumes"] > 0, srv.stats
+
+
+def test_eviction_when_paused_simulations_hold_the_pool(fake):
+    # each request alone fits (216-343 cells <= 360 boxes), but two grown ones
+    # do not: the loop must evict and restart rather than stall
+    reqs = stream(6, 11, rate_hz=1000.0, edge_lo=48, edge_hi=56, steps_lo=80, steps_hi=90)
+    srv = serve.Server(pool_bytes=360 * 4096, max_bricks=1 << 16, max_sims=6, steps_per_tick=6)
+    res = srv.run(reqs, time_scale=1.0, virtual=True)
+    check_done(srv, res, reqs)
+    assert srv.stats["evictions"] > 0 and any(r.restarts for r in res), srv.stats
+
+
+def test_dense_admission_reserves_whole_grids(fake):
+    reqs = stream(20, 4)
+    srv = serve.Server(pool_bytes=1200 * 4096, max_bricks=4096, max_sims=5, steps_per_tick=5,
+                       admission="dense")
+    res = srv.run(reqs, time_scale=1.0, virtual=True)
+    check_done(srv, res, reqs)
+    assert srv.reserved_boxes == 0 and srv.stats["pauses"] == 0
+    assert FakeBatch.made[-1].peak <= 5
+
+
+def test_mixed_storages_share_one_batch(fake):
+    reqs = stream(30, 8, edge_hi=48, steps_hi=40, rate_hz=3.0)
+    assert {r.storage for r in reqs} == {"f32", "bf16"}
+    srv = serve.Server(pool_bytes=2000 * 4096, max_bricks=8192, max_sims=6, steps_per_tick=4,
+                       storages=("f32", "bf16"))
+    res = srv.run(reqs, virtual=True)
+    check_done(srv, res, reqs)
+    assert len(FakeBatch.made) == 1 and FakeBatch.made[0].storage == "mixed"
+    for r in res:
+        assert r.storage == reqs[r.rid].storage
+    s = serve.summarize(res, 1.0)
+    assert sum(s["by_storage"].values()) == 30
 
 
 def test_summarize():
@@ -93,39 +213,20 @@ def test_summarize():
     assert s["cell_updates_per_s"] == 1000.0
 
 
-def test_lanes_route_by_storage():
-    FakeBatch.made = []
-    import pytest
-    mp = pytest.MonkeyPatch()
-    mp.setattr(serve.tcm, "Batch", FakeBatch)
-    try:
-        reqs = W.serving_stream(n_requests=30, seed=8, edge_lo=16, edge_hi=48, steps_lo=10,
-                                steps_hi=40, rate_hz=3.0)
-        assert {r.storage for r in reqs} == {"f32", "bf16"}
-        srv = serve.Server(pool_bytes=2000 * 4096, max_bricks=8192, max_sims=6, steps_per_tick=4,
-                           storages=("f32", "bf16"), pool_shares=(0.5, 0.5))
-        res = srv.run(reqs, virtual=True)
-        assert sorted(r.rid for r in res) == [r.rid for r in reqs]
-        lanes = {b.storage: b for b in FakeBatch.made}
-        assert set(lanes) == {"f32", "bf16"}
-        # the BF16 lane holds twice the boxes of the FP32 one for the same bytes
-        assert lanes["bf16"].slots == 2 * lanes["f32"].slots
-        for r in res:
-            assert r.storage == reqs[r.rid].storage
-        for st, b in lanes.items():
-            adds = [e[1] for e in b.events if e[0] == "add"]
-            want = [q.workload.name for q in sorted(reqs, key=lambda q: q.arrival) if q.storage == st]
-            assert adds == want and b.peak <= 3
-        s = serve.summarize(res, 1.0)
-        assert sum(s["by_storage"].values()) == 30
-    finally:
-        mp.undo()
-
-
-def test_request_that_never_fits_is_refused(monkeypatch):
-    monkeypatch.setattr(serve.tcm, "Batch", FakeBatch)
+def test_request_that_never_fits_is_refused(fake):
     reqs = W.serving_stream(n_requests=3, seed=1, edge_lo=64, edge_hi=65, steps_lo=5, steps_hi=6)
     srv = serve.Server(pool_bytes=100 * 4096, max_bricks=4096, max_sims=2)
-    import pytest
     with pytest.raises(RuntimeError):
         srv.run(reqs, virtual=True)
+
+
+def test_new_request_bound_covers_its_first_tick():
+    """The bound the loop charges a new request: its source cell and all cells
+    within the tick's reach, clipped to the grid."""
+    wl = W.Workload("r", (40, 48, 56), W.homogeneous(1.0), 1.0, 0.5, [(3, 20, 39, W.ricker(0.1, 0.5))], 10)
+    srv = serve.Server.__new__(serve.Server)
+    srv.steps_per_tick = 16
+    r = srv.reach_cells()
+    assert r == 3
+    # cell (0, 2, 4) of a 7 x 6 x 5 grid: x 0..3, y 0..5, z 1..4 -> 4 * 6 * 4
+    assert srv.new_request_bound(wl) == 4 * 6 * 4
