@@ -444,6 +444,8 @@ tcm_status batch_new(int device, cudaStream_t stream, void *pool_ptr, size_t poo
         cudaMemsetAsync(E.sims, 0, max_sims * sizeof(SimDev), q) != cudaSuccess ||
         cudaMemsetAsync(E.claim_step, 0xff, b->n_slots * sizeof(int), q) != cudaSuccess ||
         cudaMemsetAsync(E.lpf_mark, 0, b->n_slots * sizeof(int), q) != cudaSuccess ||
+        // records stamped with launch 0xffffffff: never taken for a current one
+        cudaMemsetAsync(E.rec, 0xff, (size_t)b->n_slots * 8 * sizeof(float), q) != cudaSuccess ||
         cudaMemcpyAsync(E.st, &es, sizeof(es), cudaMemcpyHostToDevice, q) != cudaSuccess ||
         launch_iota_desc(E.free_stack, b->n_slots, b->n_slots - 1, q) != cudaSuccess ||
         cudaStreamSynchronize(q) != cudaSuccess)

@@ -12,7 +12,7 @@
 //             bitmap[g/32]      bit      active for the next step (drives the compaction)
 //             sim_of_word[g/32] uint16   simulation owning those 32 bricks
 //   per box   meta[slot]        16 B     Box2cell brick id, bulk index, scalar k, sim/sd flags
-//             rec[slot][8]      float    6 face maxima, cell maximum, max |phi^{n+1}|
+//             rec[slot][8]      float    6 face maxima, cell maximum, launch that wrote it
 //   lists     items[2][n_slots] 48 B     active bricks in brick order (double-buffered): box,
 //                                        brick, k, flags and the boxes of the 6 face neighbours
 //             listids, free_stack, retired, newslots  int32 per box

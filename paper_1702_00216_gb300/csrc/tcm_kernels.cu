@@ -338,8 +338,9 @@ __device__ __forceinline__ void flush_updates(const Engine &E, unsigned long lon
 // ---------------------------------------------------------------------------
 template <int ST, bool MIX = false>
 __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, bool valid, int t, int seg,
-                                         bool share_xm, bool share_xp, int age_flip, unsigned long long &cells,
-                                         unsigned long long &scells, float &gacc, int &gsim, int &gnh)
+                                         bool share_xm, bool share_xp, int age_flip, unsigned stamp,
+                                         unsigned long long &cells, unsigned long long &scells, float &gacc,
+                                         int &gsim, int &gnh)
 {
     const int x4 = t % XQ;
     const int y = t / XQ;
@@ -546,9 +547,11 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     f4 = seg_max(f4);
     f5 = seg_max(f5);
     if (valid && t == 0) {
+        // rec[7]: the launch that wrote the record (a box claimed during an
+        // update still holds its previous owner's record, from an older launch)
         float4 *r = reinterpret_cast<float4 *>(E.rec + (size_t)w.slot * 8);
         __stcg(r, make_float4(f0, f1, f2, f3));
-        __stcg(r + 1, make_float4(f4, f5, mc, qm));
+        __stcg(r + 1, make_float4(f4, f5, mc, __uint_as_float(stamp)));
         // running domain maximum of this lane's sim, flushed when the sim
         // (or its step parity) changes
         if (sim != gsim || nh != gnh) {
@@ -697,19 +700,30 @@ __device__ int block_excl_scan(int v, int *total)
     return before + inc - v;
 }
 
-__device__ long long block_sum(long long v)
+// Block sums of two values at once (one pair of barriers).
+__device__ void block_sum2(long long &a, long long &b)
 {
-    __shared__ long long s_w[BLOCK / 32];
+    __shared__ long long s_a[BLOCK / 32], s_b[BLOCK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    if (lane == 0) s_w[wid] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL, a, o);
+        b += __shfl_xor_sync(FULL, b, o);
+    }
+    if (lane == 0) {
+        s_a[wid] = a;
+        s_b[wid] = b;
+    }
     __syncthreads();
-    long long r = 0;
+    long long ra = 0, rb = 0;
 #pragma unroll
-    for (int i = 0; i < BLOCK / 32; ++i) r += s_w[i];
+    for (int i = 0; i < BLOCK / 32; ++i) {
+        ra += s_a[i];
+        rb += s_b[i];
+    }
     __syncthreads();
-    return r;
+    a = ra;
+    b = rb;
 }
 
 // Per-thread copy of one sim's geometry for building work items.
@@ -811,8 +825,7 @@ __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int st
         if (j < (int)blockIdx.x) before += v;
     }
     const int mine = __ldcg(E.blocktot + blockIdx.x);
-    before = block_sum(before);
-    all = block_sum(all);
+    block_sum2(before, all);
     const bool local = mine <= SMEM_IDS;
     int *ids = local ? s_ids : E.listids + before;
     const int cap = local ? SMEM_IDS : (int)max(0ll, (long long)E.n_slots - before);
@@ -907,7 +920,7 @@ __device__ __forceinline__ void keep_or_release(const Engine &E, const WorkItem 
 // feeds it during the steps the update covers; it stays when it or any of
 // its 26 neighbours is triggered; a triggered brick boxes all 26 neighbours.
 __device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool above, bool nonzero, float thr,
-                                       int interval, bool lpf, int sim, SimDev *S)
+                                       int interval, bool lpf, int sim, SimDev *S, unsigned stamp)
 {
     const int b = w.brick;
     const int mx = __ldg(&S->mx), my = __ldg(&S->my), mz = __ldg(&S->mz);
@@ -944,12 +957,17 @@ __device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool 
         }
     }
     if (!hot) {
-        float nm[26];
-#pragma unroll
-        for (int i = 0; i < 26; ++i) nm[i] = nslot[i] >= 0 ? __ldcg(E.rec + (size_t)nslot[i] * 8 + 6) : 0.f;
+        // neighbours stepped in this launch: a neighbour claimed during this
+        // update by another thread reads as boxed here, but its box still
+        // holds its previous owner's record, stamped with an older launch
+        float2 nm[26];
 #pragma unroll
         for (int i = 0; i < 26; ++i)
-            if (nslot[i] >= 0 && nm[i] > thr) hot = true;
+            nm[i] = nslot[i] >= 0 ? __ldcg(reinterpret_cast<const float2 *>(E.rec + (size_t)nslot[i] * 8 + 6))
+                                  : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 26; ++i)
+            if (nslot[i] >= 0 && __float_as_uint(nm[i].y) == stamp && nm[i].x > thr) hot = true;
     }
     unsigned sd = w.flags & SD_MASK;
     const unsigned sd0 = sd;
@@ -1046,14 +1064,14 @@ __device__ __noinline__ void p2_item_general(const Engine &E, const WorkItem w, 
 // for them the update changes nothing, which is decided here without a
 // memory access; the rest take the general path.
 __device__ __forceinline__ void p2_item(const Engine &E, const WorkItem &w, const float4 &r0, const float4 &r1,
-                                        int age_flip, SimCache &c)
+                                        int age_flip, unsigned stamp, SimCache &c)
 {
     const int sim = (int)(w.flags >> 16);
     sim_cache(E, sim, w.nh ^ age_flip, c);
     if (c.dense || !c.manage) return;
     const float thr = c.thr_f;   // see SimCache
     if (c.neighbours == 26) {
-        p2_item26(E, w, r1.z > thr, r1.z > 0.f, thr, c.interval, c.lpf, sim, E.sims + sim);
+        p2_item26(E, w, r1.z > thr, r1.z > 0.f, thr, c.interval, c.lpf, sim, E.sims + sim, stamp);
         return;
     }
     if (r1.z > thr && (w.flags & SD_MASK) == 0) {
@@ -1127,8 +1145,8 @@ __device__ __forceinline__ void prefetch_brick(const Engine &E, const WorkItem &
 // touching columns are exchanged instead of loaded.
 template <int ST, bool MIX>
 __device__ __forceinline__ void p1_pair(const Engine &E, const WorkItem &w, bool v, int t, int seg, int age_flip,
-                                        unsigned long long &cells, unsigned long long &scells, float &gacc,
-                                        int &gsim, int &gnh)
+                                        unsigned stamp, unsigned long long &cells, unsigned long long &scells,
+                                        float &gacc, int &gsim, int &gnh)
 {
     bool pair_x = false;
     const bool first = (seg & 1) == 0;
@@ -1138,8 +1156,8 @@ __device__ __forceinline__ void p1_pair(const Engine &E, const WorkItem &w, bool
         pair_x = v && other_v &&
                  (first ? (w.nb[1] >= 0 && w.nb[1] == other_slot) : (w.nb[0] >= 0 && w.nb[0] == other_slot));
     }
-    p1_brick<ST, MIX>(E, w, v, t, seg, !first && pair_x, first && pair_x, age_flip, cells, scells, gacc, gsim,
-                      gnh);
+    p1_brick<ST, MIX>(E, w, v, t, seg, !first && pair_x, first && pair_x, age_flip, stamp, cells, scells, gacc,
+                      gsim, gnh);
 }
 
 template <int ST>
@@ -1147,6 +1165,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
 {
     EngineState *st = E.st;
     const int age_flip = __ldcg(&st->list_age) & 1;
+    const unsigned stamp = (unsigned)__ldcg(&st->launches);   // this launch, in the maxima records
     const WorkItem *L = cur ? E.items1 : E.items0;
     WorkItem *Lnext = cur ? E.items0 : E.items1;
     const int nact = __ldcg(&st->n_active[cur]);
@@ -1194,7 +1213,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
             vnn = vnn && wnn.slot >= 0;
             if constexpr (ST != ST_MIXED) {
                 if (E.prefetch) prefetch_brick<ST>(E, wn, vn, t, age_flip);
-                p1_pair<ST, false>(E, w, v, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
+                p1_pair<ST, false>(E, w, v, t, seg, age_flip, stamp, cells, scells, gacc, gsim, gnh);
             } else {
                 // Simulations of different storages in one launch: the warp
                 // steps the bricks of each storage present among its lanes in
@@ -1208,11 +1227,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
                 }
                 const int sw = v ? __ldg(&E.sims[w.flags >> 16].storage) : -1;
                 if (__any_sync(FULL, sw == ST_F32))
-                    p1_pair<ST_F32, true>(E, w, v && sw == ST_F32, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
+                    p1_pair<ST_F32, true>(E, w, v && sw == ST_F32, t, seg, age_flip, stamp, cells, scells, gacc, gsim,
+                                          gnh);
                 if (__any_sync(FULL, sw == ST_BF16))
-                    p1_pair<ST_BF16, true>(E, w, v && sw == ST_BF16, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
+                    p1_pair<ST_BF16, true>(E, w, v && sw == ST_BF16, t, seg, age_flip, stamp, cells, scells, gacc,
+                                           gsim, gnh);
                 if (__any_sync(FULL, sw == ST_F16))
-                    p1_pair<ST_F16, true>(E, w, v && sw == ST_F16, t, seg, age_flip, cells, scells, gacc, gsim, gnh);
+                    p1_pair<ST_F16, true>(E, w, v && sw == ST_F16, t, seg, age_flip, stamp, cells, scells, gacc,
+                                          gsim, gnh);
             }
             pr = pn;
             w = wn;
@@ -1267,7 +1289,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (base + u * nthr < nact && w[u].slot >= 0) p2_item(E, w[u], r0[u], r1[u], age_flip, sc);
+                if (base + u * nthr < nact && w[u].slot >= 0) p2_item(E, w[u], r0[u], r1[u], age_flip, stamp, sc);
         }
         // (Source bricks need no activation here: every source starts at its
         // sim's first step, its brick is boxed when the sim starts, and the
