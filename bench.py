@@ -473,14 +473,17 @@ def virtual_leg(torch, tcm, W, local_rank):
 
 
 def tuning_leg(torch, tcm, W, wl, dev, local_rank):
-    """The autotuner on the benchmark workload (brick shapes x update
-    schedules, then the fastest with the L2 prefetch off; steps 600..800
-    timed), then the full create-to-result run with its choice, compared with
-    the dense result."""
+    """The autotuner on the benchmark workload (brick shapes, CTA blocking of
+    the 8x8x8 build, update schedules, then the fastest with the L2 prefetch
+    off; steps 600..800 timed; each candidate's field at step 800 compared
+    with the dense grid's, the choice the fastest within 1e-5 max|phi|), then
+    the full create-to-result run with its choice, compared with the dense
+    result."""
     from paper_1702_00216_gb300 import autotune
-    r = autotune.autotune(wl, start=600, count=200, allow_schedule=True, device=local_rank, allow_prefetch=True)
+    r = autotune.autotune(wl, start=600, count=200, allow_schedule=True, device=local_rank, allow_prefetch=True,
+                          allow_blocking=True, accuracy=True, tolerance=1e-5)
     best = autotune.apply(wl, r["best"])
-    out = {"window": r["window"], "table": r["table"], "best": r["best"].label()}
+    out = {"window": r["window"], "table": r["table"], "best": r["best"].label(), "choice": r["choice"]}
     runs = {}
     for name, w, dense in (("dense", wl, True), ("tuned", best, False)):
         torch.cuda.synchronize()
@@ -560,9 +563,15 @@ def precision_leg(torch, tcm, W, dev, local_rank):
     update, max and RMS error of phi^800 against the FP32 run (which is within
     ~1e-6 of the FP64 dense grid), and the drift of the leapfrog energy from
     step len(wavelet)+50 to step 800 (FP64 reduction on the device)."""
+    from paper_1702_00216_gb300 import autotune
     wl = W.precision(256, 800)
+    # brick shape and CTA blocking from the autotuner (steps 300..400, binary32)
+    tuned = autotune.autotune(wl, start=300, count=100, device=local_rank, allow_blocking=True)
+    wl = autotune.apply(wl, tuned["best"])
     n_src = len(wl.sources[0][3])
-    out = {"workload": f"{wl.name}, 800 steps, relative threshold 1e-6, 20-step decay"}
+    out = {"workload": f"{wl.name}, 800 steps, relative threshold 1e-6, 20-step decay",
+           "tuned": {"best": tuned["best"].label(), "window": tuned["window"],
+                     "table": [{k: t[k] for k in ("config", "window_ms", "updates_per_s")} for t in tuned["table"]]}}
     ref = None
     for st in ("f32", "bf16", "f16"):
         s = tcm.Sim.from_workload(wl, device=local_rank, storage=st)

@@ -118,6 +118,9 @@ typedef struct {
                            brick pair it asks L2 for the next pair's field arrays and
                            per-node k (bricks with per-node k only).  Same results
                            either way */
+    int cta_warps;      /* warps per CTA of the step kernel: 0 or 8 (every brick shape),
+                           4 or 16 (8x8x8 only); same results, different blocking
+                           (TCM_EINVAL otherwise) */
 } tcm_options;
 
 /* Bytes of pool one box takes for this brick shape and storage (binary32:
@@ -313,6 +316,7 @@ typedef struct {
     int no_graphs;      /* as in tcm_options */
     tcm_brick brick;    /* brick shape of every simulation of the batch ({0,0,0}: 8x8x8) */
     int no_prefetch;    /* as in tcm_options */
+    int cta_warps;      /* as in tcm_options */
 } tcm_batch_options;
 
 tcm_status tcm_batch_create(const tcm_batch_options *options, tcm_batch **out);

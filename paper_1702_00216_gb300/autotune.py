@@ -1,22 +1,29 @@
-"""Autotuner: choose the brick shape (and, if allowed, the update schedule)
-for a workload by timing it.
+"""Autotuner: choose the brick shape, the CTA blocking of the step kernel
+and (if allowed) the update schedule for a workload by timing it.
 
 Each candidate runs the workload through the C ABI: the steps before the
 probe window untimed, then the window timed with CUDA events on the
-library's stream.  The choice minimises the device time of the window (the
-time to solution of those steps; node-update counts differ between shapes
-because the cells differ).  Candidates:
+library's stream.  Candidates:
 
   brick shapes     4x4x4, 8x8x8, 16x8x8 (one build of the library each)
+  CTA blocking     with allow_blocking, the 8x8x8 shape also with 4 and 16
+                   warps per CTA of the step kernel (8 is the default of every
+                   shape; separate builds; same results)
   schedules        update every step with face neighbours (always); with
                    allow_schedule, also the Eq. 5 interval with the 26
-                   neighbour set (at threshold 0 both equal the dense grid;
-                   above it the active sets differ slightly)
+                   neighbour set
   L2 prefetch      on (always); with allow_prefetch, the fastest of the
                    above is timed once more with it off (same results)
 
-Results are cached per (workload name, shape, window, candidates) in the
-process, and the chosen configuration can be applied with `apply`.
+Two kinds of knobs: the blocking and the prefetch never change a result
+(checked bit for bit against the default configuration of the same shape
+when a reference is kept), while the brick shape and the schedule change
+which cells are boxed at a level above 0, so they change the result a
+little.  With a reference (`accuracy=True`) every candidate's field at the
+end of the window is compared with the dense grid's, and the choice is the
+fastest candidate within `tolerance` x max|phi| of it; without one, the
+fastest.  Results are cached per (workload, window, candidates) in the
+process; `apply` returns the workload with a chosen configuration.
 """
 from __future__ import annotations
 
@@ -26,6 +33,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 from . import tcm
 
 BRICKS: Tuple[Tuple[int, int, int], ...] = ((4, 4, 4), (8, 8, 8), (16, 8, 8))
+# warps per CTA of the step kernel available per brick shape (8: the default)
+BLOCKINGS = {(8, 8, 8): (4, 16)}
 _CACHE: Dict[tuple, dict] = {}
 
 
@@ -35,40 +44,47 @@ class Candidate:
     interval: int = 1
     neighbours: int = 6
     prefetch: bool = True
+    cta_warps: int = 0
 
     def label(self) -> str:
         b = "x".join(map(str, self.brick))
+        if self.cta_warps not in (0, 8):
+            b = f"{b}/w{self.cta_warps}"
         b = b if (self.interval, self.neighbours) == (1, 6) else f"{b}/eq5-26"
         return b if self.prefetch else f"{b}/no-prefetch"
 
+    def same_results_as(self) -> "Candidate":
+        """The configuration whose results this one reproduces bit for bit
+        (the blocking and the prefetch do not change results)."""
+        return dataclasses.replace(self, prefetch=True, cta_warps=0)
 
-def candidates(allow_schedule: bool = False, bricks: Sequence = BRICKS) -> List[Candidate]:
+
+def candidates(allow_schedule: bool = False, bricks: Sequence = BRICKS,
+               allow_blocking: bool = False) -> List[Candidate]:
     out = [Candidate(tuple(b)) for b in bricks]
+    if allow_blocking:
+        out += [Candidate(tuple(b), cta_warps=w) for b in bricks for w in BLOCKINGS.get(tuple(b), ())]
     if allow_schedule:
         out += [Candidate(tuple(b), 0, 26) for b in bricks]
     return out
 
 
 def apply(wl, c: Candidate):
-    """The workload with the candidate's brick shape, schedule and prefetch."""
+    """The workload with the candidate's brick shape, schedule, prefetch and
+    CTA blocking."""
     return dataclasses.replace(wl, brick=tuple(c.brick), interval=c.interval, neighbours=c.neighbours,
-                               prefetch=c.prefetch)
+                               prefetch=c.prefetch, cta_warps=c.cta_warps)
 
 
-def _pool_bytes(wl, brick) -> Optional[int]:
-    if wl.pool_bytes is None:
-        return None
-    # the same memory budget, whatever the box size
-    return wl.pool_bytes
-
-
-def measure(wl, c: Candidate, start: int, count: int, device: int = 0, storage="f32") -> dict:
+def measure(wl, c: Candidate, start: int, count: int, device: int = 0, storage="f32", ref=None) -> dict:
+    """Time steps [start, start+count) of the workload in configuration c;
+    with a reference (the dense grid's phi at start+count, a device tensor)
+    also the largest difference from it."""
     import torch
     w = apply(wl, c)
     # direct launches: a graph captured inside the timed window would add its
     # host-side capture time to the window
-    s = tcm.Sim.from_workload(w, device=device, pool_bytes=_pool_bytes(w, c.brick), storage=storage,
-                              graphs=False)
+    s = tcm.Sim.from_workload(w, device=device, pool_bytes=wl.pool_bytes, storage=storage, graphs=False)
     try:
         s.step(start)
         u0 = s.updates
@@ -81,14 +97,40 @@ def measure(wl, c: Candidate, start: int, count: int, device: int = 0, storage="
         s.sync()
         ms = e0.elapsed_time(e1)
         upd = s.updates - u0
+        out = {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
+               "prefetch": c.prefetch, "cta_warps": c.cta_warps or 8, "window_ms": ms, "cell_updates": upd,
+               "updates_per_s": upd / (ms / 1e3) if ms > 0 else 0.0}
+        if ref is not None:
+            buf = torch.empty(wl.shape, dtype=torch.float32, device=ref.device)
+            tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
+            torch.cuda.synchronize(device)
+            gmax = float(ref.abs().max().item())
+            d = float((buf - ref).abs().max().item())
+            out["max_abs_diff_vs_dense"] = d
+            out["rel_diff_vs_dense"] = d / gmax if gmax > 0 else 0.0
+            out["_field"] = buf
     finally:
         s.close()
-    return {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
-            "prefetch": c.prefetch, "window_ms": ms, "cell_updates": upd, "updates_per_s": upd / (ms / 1e3) if ms > 0 else 0.0}
+    return out
+
+
+def dense_reference(wl, steps: int, device: int = 0):
+    """phi of the dense grid (the same kernel over every brick) after `steps` steps."""
+    import torch
+    s = tcm.Sim.from_workload(wl, dense=True, device=device, pool_bytes=None)
+    try:
+        s.step(steps)
+        buf = torch.empty(wl.shape, dtype=torch.float32, device=f"cuda:{device}")
+        tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
+        torch.cuda.synchronize(device)
+    finally:
+        s.close()
+    return buf
 
 
 def autotune(wl, start: Optional[int] = None, count: Optional[int] = None, allow_schedule: bool = False,
-             device: int = 0, storage="f32", bricks: Sequence = BRICKS, allow_prefetch: bool = False) -> dict:
+             device: int = 0, storage="f32", bricks: Sequence = BRICKS, allow_prefetch: bool = False,
+             allow_blocking: bool = False, accuracy: bool = False, tolerance: float = 1e-5) -> dict:
     """Time every candidate on steps [start, start+count) of the workload and
     return {"best": Candidate, "table": [...]} (fastest window first)."""
     steps = max(int(wl.steps), 1)
@@ -97,22 +139,36 @@ def autotune(wl, start: Optional[int] = None, count: Optional[int] = None, allow
     if start is None:
         start = max(0, min(steps - count, (steps * 2) // 5))
     key = (wl.name, tuple(wl.shape), start, count, allow_schedule, storage, tuple(map(tuple, bricks)),
-           allow_prefetch)
+           allow_prefetch, allow_blocking, accuracy, tolerance)
     if key in _CACHE:
         return _CACHE[key]
+    ref = dense_reference(wl, start + count, device) if accuracy else None
     table = []
-    for c in candidates(allow_schedule, bricks):
-        r = measure(wl, c, start, count, device, storage)
+    fields = {}
+
+    def run(c):
+        r = measure(wl, c, start, count, device, storage, ref)
         r["candidate"] = c
+        f = r.pop("_field", None)
+        base = c.same_results_as()
+        if f is not None:
+            if base == c:
+                fields[c.label()] = f
+            elif base.label() in fields:
+                r["bit_identical_to"] = base.label() if bool((f == fields[base.label()]).all().item()) else None
         table.append(r)
-    table.sort(key=lambda r: r["window_ms"])
+
+    for c in candidates(allow_schedule, bricks, allow_blocking):
+        run(c)
     if allow_prefetch:
-        c = dataclasses.replace(table[0]["candidate"], prefetch=False)
-        r = measure(wl, c, start, count, device, storage)
-        r["candidate"] = c
-        table.append(r)
-        table.sort(key=lambda r: r["window_ms"])
-    out = {"best": table[0]["candidate"], "window": [start, start + count],
+        fastest = min(table, key=lambda r: r["window_ms"])["candidate"]
+        run(dataclasses.replace(fastest, prefetch=False))
+    table.sort(key=lambda r: r["window_ms"])
+    ok = [r for r in table if not accuracy or r["rel_diff_vs_dense"] <= tolerance]
+    best = (ok or table)[0]["candidate"]
+    out = {"best": best, "window": [start, start + count],
+           "choice": f"fastest within {tolerance:g} max|phi| of the dense grid" if accuracy else "fastest",
            "table": [{k: v for k, v in r.items() if k != "candidate"} for r in table]}
+    del fields, ref
     _CACHE[key] = out
     return out

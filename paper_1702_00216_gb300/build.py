@@ -22,9 +22,13 @@ LIB = os.path.join(HERE, "libtcm.so")
 UNITS = ["tcm_kernels.cu", "tcm_api.cu", "tcm_noalloc.cu"]
 DISPATCH = "tcm_dispatch.cpp"
 DEPS = UNITS + ["tcm_internal.cuh", DISPATCH]
-# One build of the runtime and kernels per brick shape (bx, by, bz, name);
-# tcm_dispatch.cpp routes the public entry points to them.
-SHAPES = [(4, 4, 4, "b444"), (8, 8, 8, "b888"), (16, 8, 8, "b1688")]
+# One build of the runtime and kernels per brick shape and CTA blocking
+# (bx, by, bz, warps per CTA of the step kernel, name); tcm_dispatch.cpp
+# routes the public entry points to them.  8 warps per CTA is the default of
+# every shape; the 8x8x8 shape also has 4- and 16-warp builds for the
+# autotuner.
+SHAPES = [(4, 4, 4, 8, "b444"), (8, 8, 8, 8, "b888"), (16, 8, 8, 8, "b1688"),
+          (8, 8, 8, 4, "b888w4"), (8, 8, 8, 16, "b888w16")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-ftz=false", "-prec-div=true",
          "-prec-sqrt=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -38,8 +42,8 @@ def public_names():
     return sorted(set(re.findall(r"\b(tcm_[a-z_]+)\s*\(", src)))
 
 
-def shape_defines(bx, by, bz, name):
-    d = [f"-DTCM_BX={bx}", f"-DTCM_BY={by}", f"-DTCM_BZ={bz}", f"-Dtcm=tcm_{name}",
+def shape_defines(bx, by, bz, warps, name):
+    d = [f"-DTCM_BX={bx}", f"-DTCM_BY={by}", f"-DTCM_BZ={bz}", f"-DTCM_P1_WARPS={warps}", f"-Dtcm=tcm_{name}",
          f"-Dtcm_sim=tcm_{name}_sim", f"-Dtcm_batch=tcm_{name}_batch",
          f"-Dtcm_internal_view=tcm_{name}_internal_view"]
     d += [f"-D{f}=tcm_{name}_{f[4:]}" for f in public_names()]
@@ -77,7 +81,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    jobs = [(u, extra + shape_defines(*sh), "_" + sh[3]) for sh in SHAPES for u in UNITS]
+    jobs = [(u, extra + shape_defines(*sh), "_" + sh[4]) for sh in SHAPES for u in UNITS]
     jobs.append((DISPATCH, [], ""))
     with cf.ThreadPoolExecutor(min(len(jobs), max(4, os.cpu_count() or 4))) as ex:
         objs = list(ex.map(lambda j: _compile(*j), jobs))

@@ -24,10 +24,12 @@ struct tcm_batch {
     std::vector<tcm_sim *> sims;
 };
 
-#define DECL3(ret, name, params)            \
-    extern "C" ret tcm_b444_##name params;  \
-    extern "C" ret tcm_b888_##name params;  \
-    extern "C" ret tcm_b1688_##name params;
+#define DECL3(ret, name, params)             \
+    extern "C" ret tcm_b444_##name params;   \
+    extern "C" ret tcm_b888_##name params;   \
+    extern "C" ret tcm_b1688_##name params;  \
+    extern "C" ret tcm_b888w4_##name params; \
+    extern "C" ret tcm_b888w16_##name params;
 
 DECL3(tcm_status, slot_bytes, (tcm_brick, int, size_t *))
 DECL3(tcm_status, create, (const tcm_domain *, const tcm_velocity_model *, double, double, double, tcm_brick,
@@ -72,20 +74,34 @@ DECL3(tcm_status, batch_pause, (void *))
 DECL3(tcm_status, batch_resume, (void *))
 DECL3(tcm_status, batch_headroom, (void *, int64_t, int64_t *))
 
-// Call the build of `shape`.
-#define SHAPE_CALL(shape, name, ...)                                                        \
-    ((shape) == 0 ? tcm_b444_##name(__VA_ARGS__)                                             \
-                  : ((shape) == 1 ? tcm_b888_##name(__VA_ARGS__) : tcm_b1688_##name(__VA_ARGS__)))
+// Call the build of `shape` (0 4x4x4, 1 8x8x8, 2 16x8x8, 3 8x8x8 with 4 warps
+// per CTA, 4 8x8x8 with 16 warps per CTA).
+#define SHAPE_CALL(shape, name, ...)                                                           \
+    ((shape) == 0   ? tcm_b444_##name(__VA_ARGS__)                                              \
+     : (shape) == 1 ? tcm_b888_##name(__VA_ARGS__)                                              \
+     : (shape) == 2 ? tcm_b1688_##name(__VA_ARGS__)                                             \
+     : (shape) == 3 ? tcm_b888w4_##name(__VA_ARGS__)                                            \
+                    : tcm_b888w16_##name(__VA_ARGS__))
 
 namespace {
 
-// Shape index of a brick, -1 if unsupported.
-int shape_of(tcm_brick b)
+// Build index of a brick shape and CTA blocking (warps per CTA of the step
+// kernel, 0 = the default 8), -1 if unsupported.
+int shape_of(tcm_brick b, int warps = 0)
 {
-    if (b.bx == 4 && b.by == 4 && b.bz == 4) return 0;
-    if (b.bx == 8 && b.by == 8 && b.bz == 8) return 1;
-    if (b.bx == 16 && b.by == 8 && b.bz == 8) return 2;
+    if (warps == 0) warps = 8;
+    if (b.bx == 4 && b.by == 4 && b.bz == 4) return warps == 8 ? 0 : -1;
+    if (b.bx == 8 && b.by == 8 && b.bz == 8) return warps == 8 ? 1 : warps == 4 ? 3 : warps == 16 ? 4 : -1;
+    if (b.bx == 16 && b.by == 8 && b.bz == 8) return warps == 8 ? 2 : -1;
     return -1;
+}
+
+// The blocking of a build (for adding to a batch: any shape index of the
+// brick is the batch's if the brick matches).
+bool same_brick(int shape, tcm_brick b)
+{
+    const int s = shape_of(b);
+    return s >= 0 && (s == shape || (s == 1 && (shape == 3 || shape == 4)));
 }
 
 tcm_sim *wrap_sim(int shape, void *impl, tcm_batch *owner)
@@ -126,7 +142,8 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
 {
     if (!out) return TCM_EINVAL;
     *out = nullptr;
-    const int sh = shape_of(brick);
+    if (!options) return TCM_EINVAL;
+    const int sh = shape_of(brick, options->cta_warps);
     if (sh < 0) return TCM_EINVAL;
     void *impl = nullptr;
     const tcm_status st = SHAPE_CALL(sh, create, domain, velocity, dx, dt, threshold, brick, options, &impl);
@@ -281,7 +298,7 @@ tcm_status tcm_batch_create(const tcm_batch_options *o, tcm_batch **out)
     if (!o) return TCM_EINVAL;
     tcm_brick br = o->brick;
     if (br.bx == 0 && br.by == 0 && br.bz == 0) br = tcm_brick{8, 8, 8};
-    const int sh = shape_of(br);
+    const int sh = shape_of(br, o->cta_warps);
     if (sh < 0) return TCM_EINVAL;
     void *impl = nullptr;
     const tcm_status st = SHAPE_CALL(sh, batch_create, o, &impl);
@@ -303,7 +320,7 @@ tcm_status tcm_batch_add(tcm_batch *b, const tcm_domain *domain, const tcm_veloc
 {
     if (!b || !out) return TCM_EINVAL;
     *out = nullptr;
-    if (shape_of(brick) != b->shape) return TCM_EINVAL;
+    if (!same_brick(b->shape, brick)) return TCM_EINVAL;
     void *impl = nullptr;
     const tcm_status st = SHAPE_CALL(b->shape, batch_add, b->impl, domain, velocity, dx, dt, threshold, brick,
                                      threshold_mode, decay_alpha, decay_steps, dense, n_steps, &impl);

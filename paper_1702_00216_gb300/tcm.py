@@ -56,13 +56,14 @@ class tcm_options(C.Structure):
     _fields_ = [("threshold_mode", C.c_int), ("decay_alpha", C.c_float), ("decay_steps", C.c_int),
                 ("pool_ptr", C.c_void_p), ("pool_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("storage", C.c_int), ("dense", C.c_int), ("device", C.c_int), ("no_graphs", C.c_int),
-                ("no_prefetch", C.c_int)]
+                ("no_prefetch", C.c_int), ("cta_warps", C.c_int)]
 
 
 class tcm_batch_options(C.Structure):
     _fields_ = [("pool_ptr", C.c_void_p), ("pool_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("device", C.c_int), ("storage", C.c_int), ("max_bricks", C.c_int64),
-                ("max_sims", C.c_int), ("no_graphs", C.c_int), ("brick", tcm_brick), ("no_prefetch", C.c_int)]
+                ("max_sims", C.c_int), ("no_graphs", C.c_int), ("brick", tcm_brick), ("no_prefetch", C.c_int),
+                ("cta_warps", C.c_int)]
 
 
 class TCMError(RuntimeError):
@@ -398,7 +399,7 @@ class Sim:
     def __init__(self, shape, media, dx, dt, threshold=0.0, brick=(8, 8, 8),
                  thr_mode=TCM_THR_ABSOLUTE, decay_alpha=1.0, decay_steps=0, pool_bytes=None,
                  dense=False, device=0, stream=None, pool_tensor=None, storage=TCM_STORAGE_F32,
-                 graphs=True, prefetch=True):
+                 graphs=True, prefetch=True, cta_warps=0):
         self.shape = tuple(int(v) for v in shape)
         self.storage = storage_code(storage)
         nz, ny, nx = self.shape
@@ -418,6 +419,7 @@ class Sim:
         opts.storage = self.storage
         opts.no_graphs = 0 if graphs else 1
         opts.no_prefetch = 0 if prefetch else 1
+        opts.cta_warps = int(cta_warps)
         opts.dense = int(bool(dense))
         opts.device = int(device)
         if pool_tensor is not None:
@@ -450,6 +452,7 @@ class Sim:
     def from_workload(cls, wl, dense=False, **kw):
         pool = kw.pop("pool_bytes", wl.pool_bytes)
         kw.setdefault("prefetch", wl.prefetch)
+        kw.setdefault("cta_warps", getattr(wl, "cta_warps", 0))
         s = cls(wl.shape, wl.media, wl.dx, wl.dt, threshold=wl.tau, brick=wl.brick,
                 thr_mode=wl.thr_mode, decay_alpha=wl.decay_alpha, decay_steps=wl.decay_steps,
                 pool_bytes=pool, dense=dense, **kw)
@@ -552,13 +555,15 @@ class Batch:
     """Many simulations stepped together by one launch per step (tcm_batch_*)."""
 
     def __init__(self, pool_bytes, max_bricks, max_sims=64, device=0, stream=None,
-                 pool_tensor=None, storage=TCM_STORAGE_F32, graphs=True, brick=(8, 8, 8), prefetch=True):
+                 pool_tensor=None, storage=TCM_STORAGE_F32, graphs=True, brick=(8, 8, 8), prefetch=True,
+                 cta_warps=0):
         torch = _torch()
         self.storage = storage_code(storage)
         self.brick = tuple(int(v) for v in brick)
         o = tcm_batch_options()
         o.no_graphs = 0 if graphs else 1
         o.no_prefetch = 0 if prefetch else 1
+        o.cta_warps = int(cta_warps)
         o.brick = tcm_brick(*self.brick)
         o.pool_bytes = int(pool_bytes)
         o.device = int(device)

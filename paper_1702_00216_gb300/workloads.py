@@ -177,6 +177,7 @@ class Workload:
     neighbours: int = 6                              # 6 (faces) or 26
     lpf: Optional[Tuple[float, float]] = None        # Eq. 7 shut-down (pass, stop), else Eq. 6
     prefetch: bool = True                            # L2 prefetch in the time stepping
+    cta_warps: int = 0                               # warps per CTA of the step kernel (0: 8)
 
     @property
     def nx(self):

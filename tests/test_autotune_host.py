@@ -15,7 +15,7 @@ def test_candidates():
 def test_picks_fastest_window_and_caches(monkeypatch):
     calls = []
 
-    def fake(wl, c, start, count, device=0, storage="f32"):
+    def fake(wl, c, start, count, device=0, storage="f32", ref=None):
         calls.append((c.label(), start, count))
         ms = {"4x4x4": 3.0, "8x8x8": 1.0, "16x8x8": 2.0}[c.label()]
         return {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
@@ -38,7 +38,7 @@ def test_prefetch_refinement(monkeypatch):
     the L2 prefetch off, and the faster of the two is chosen."""
     calls = []
 
-    def fake(wl, c, start, count, device=0, storage="f32"):
+    def fake(wl, c, start, count, device=0, storage="f32", ref=None):
         calls.append(c.label())
         ms = {"4x4x4": 3.0, "8x8x8": 1.0, "16x8x8": 2.0, "8x8x8/no-prefetch": 0.5}[c.label()]
         return {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
@@ -51,3 +51,32 @@ def test_prefetch_refinement(monkeypatch):
     assert calls == ["4x4x4", "8x8x8", "16x8x8", "8x8x8/no-prefetch"]
     assert r["best"].brick == (8, 8, 8) and r["best"].prefetch is False
     assert A.apply(wl, r["best"]).prefetch is False and wl.prefetch is True
+
+
+def test_blocking_axis_and_labels():
+    labels = [c.label() for c in A.candidates(allow_blocking=True)]
+    assert labels == ["4x4x4", "8x8x8", "16x8x8", "8x8x8/w4", "8x8x8/w16"]
+    c = A.Candidate((8, 8, 8), cta_warps=16, prefetch=False)
+    assert c.same_results_as() == A.Candidate((8, 8, 8))
+    wl = W.small(n=32, steps=100)
+    assert A.apply(wl, c).cta_warps == 16 and wl.cta_warps == 0
+
+
+def test_choice_respects_the_accuracy_tolerance(monkeypatch):
+    """Schedules and shapes that change results are chosen only if they stay
+    within the tolerance of the dense grid; the fastest within it wins."""
+    def fake(wl, c, start, count, device=0, storage="f32", ref=None):
+        ms = {"4x4x4": 3.0, "8x8x8": 2.0, "16x8x8": 2.5, "8x8x8/w4": 2.2, "8x8x8/w16": 2.1,
+              "4x4x4/eq5-26": 0.5, "8x8x8/eq5-26": 1.5, "16x8x8/eq5-26": 1.8}[c.label()]
+        rel = {"4x4x4/eq5-26": 3e-5}.get(c.label(), 2e-6)
+        return {"config": c.label(), "window_ms": ms, "cell_updates": 1, "updates_per_s": 1.0,
+                "max_abs_diff_vs_dense": rel, "rel_diff_vs_dense": rel}
+
+    monkeypatch.setattr(A, "measure", fake)
+    monkeypatch.setattr(A, "dense_reference", lambda wl, steps, device=0: object())
+    A._CACHE.clear()
+    wl = W.small(n=32, steps=100)
+    r = A.autotune(wl, allow_schedule=True, allow_blocking=True, accuracy=True, tolerance=1e-5)
+    assert r["table"][0]["config"] == "4x4x4/eq5-26"        # fastest, but outside the tolerance
+    assert r["best"].label() == "8x8x8/eq5-26"
+    assert "within" in r["choice"]

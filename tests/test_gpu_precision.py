@@ -2,6 +2,7 @@
 arithmetic): the GPU equals, bit for bit, the oracle's storage form (fields
 and active sets), TCM at threshold 0 equals the dense grid, and the error
 against the binary64 dense grid stays within the stated bounds."""
+import dataclasses
 import os
 
 import numpy as np
@@ -156,9 +157,27 @@ def test_precision_workload_error_against_fp64_dense(capsys):
         d = s.read_field(0).astype(np.float64) - now
         errs[st] = (np.abs(d).max() / gmax, np.sqrt((d ** 2).mean()) / grms)
         s.close()
+    # every configuration the autotuner can choose for it (brick shape and
+    # CTA blocking; the blocking cannot change a result, the shape can)
+    tuned = {}
+    for brick, warps in (((4, 4, 4), 0), ((16, 8, 8), 0), ((8, 8, 8), 4), ((8, 8, 8), 16)):
+        w2 = dataclasses.replace(wl, brick=brick, cta_warps=warps)
+        for st in ("f32", "bf16", "f16"):
+            s = tcm.Sim.from_workload(w2, storage=st)
+            s.step(800)
+            d = s.read_field(0).astype(np.float64) - now
+            tuned[(brick, warps, st)] = (np.abs(d).max() / gmax, np.sqrt((d ** 2).mean()) / grms)
+            s.close()
     with capsys.disabled():
         print("\nprecision 256^3 x 800 vs FP64 dense (max rel, rms rel):",
               {k_: tuple(float(f"{v:.3e}") for v in e) for k_, e in errs.items()})
+        print("other autotuner configurations:",
+              {f"{'x'.join(map(str, b))}/w{w or 8}/{st}": tuple(float(f"{v:.3e}") for v in e)
+               for (b, w, st), e in tuned.items()})
+    for (b, w, st), e in tuned.items():
+        if b == (8, 8, 8):
+            assert e == errs[st]                     # blocking only: identical results
+        assert e[0] < {"f32": 1e-4, "f16": 1.2e-2, "bf16": 8e-2}[st]
     # measured: f32 6.5e-6, f16 5.7e-3, bf16 4.1e-2 (max rel) with the
     # velocity form (phi and v = phi^n - phi^{n-1} stored); storing phi^n and
     # phi^{n-1} in 16 bits gave 1.4e-2 and 0.45, because each rounding of

@@ -134,3 +134,33 @@ def test_set_field_16x8x8():
     o.set_field(v, v * F32(0.99))
     compare(s, o, [5, 20])
     s.close()
+
+
+@pytest.mark.parametrize("warps", [4, 16])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_cta_blocking_builds_equal_the_oracle(warps, storage):
+    """The 8x8x8 builds with 4 and 16 warps per CTA of the step kernel (the
+    autotuner's blocking axis) give the oracle's fields, active sets and
+    updates bit for bit, at a level above 0 with shut-down, in a single
+    simulation and in a batch."""
+    wl = het((8, 8, 8), thr_mode=1, tau=1e-4, alpha=0.7, decay=4)
+    s = tcm.Sim.from_workload(wl, cta_warps=warps, storage=storage)
+    compare(s, oracle_of(wl, storage), [1, 9, 30, 60])
+    s.close()
+    b = tcm.Batch(pool_bytes=4000 * tcm.tcm_slot_bytes(), max_bricks=1 << 14, max_sims=4, cta_warps=warps,
+                  storage=storage)
+    sims = [b.add(wl), b.add(het((8, 8, 8), shape=(21, 30, 17)))]
+    b.step(50)
+    for sm, w in zip(sims, (wl, het((8, 8, 8), shape=(21, 30, 17)))):
+        o = oracle_of(w, storage)
+        o.step(50)
+        assert np.array_equal(sm.read_field(0), o.read_field(0))
+        assert np.array_equal(sm.active_bricks(), o.active_bricks())
+    b.close()
+
+
+def test_cta_blocking_rejects_unbuilt_combinations():
+    wl = het((4, 4, 4))
+    with pytest.raises(tcm.TCMError) as e:
+        tcm.Sim.from_workload(wl, cta_warps=16)
+    assert e.value.status == tcm.TCM_EINVAL
