@@ -6,6 +6,12 @@ root.  The runtime and kernels compile once per supported brick shape (with
 their entry points renamed per shape), plus the dispatcher of the public C
 ABI; all translation units compile in parallel and link into one shared
 library with the CUDA runtime linked statically.
+
+With TCM_CHECKED=1 in the environment the same sources build the checked
+library, libtcm_checked.so (compiled with -DTCM_CHECKED: every box, brick,
+free-stack, list and claim index is bounds-checked on the device, an index
+out of range sets an error bit that the next status read turns into
+TCM_EDEVICE, and the access is skipped), which the binding then loads.
 """
 from __future__ import annotations
 
@@ -18,7 +24,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libtcm.so")
+LIB_NORMAL = os.path.join(HERE, "libtcm.so")
+LIB_CHECKED = os.path.join(HERE, "libtcm_checked.so")
+
+
+def checked() -> bool:
+    """Whether this process builds and loads the bounds-checked library."""
+    return os.environ.get("TCM_CHECKED", "") == "1"
+
+
+LIB = LIB_CHECKED if checked() else LIB_NORMAL
 UNITS = ["tcm_kernels.cu", "tcm_api.cu", "tcm_noalloc.cu"]
 DISPATCH = "tcm_dispatch.cpp"
 DEPS = UNITS + ["tcm_internal.cuh", DISPATCH]
@@ -67,6 +82,9 @@ def _stale() -> bool:
 
 
 def _compile(unit: str, extra, tag: str = "") -> str:
+    if checked():
+        extra = list(extra) + ["-DTCM_CHECKED"]
+        tag += "_checked"
     obj = os.path.join(BUILD, unit.replace(".cu", "").replace(".cpp", "") + tag + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, unit), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)

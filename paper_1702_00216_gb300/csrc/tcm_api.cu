@@ -171,6 +171,7 @@ tcm_status sync_status(tcm_batch *b)
     }
     const unsigned err = *b->h_err;
     if (err & ERR_TIMEOUT) return poison(b, TCM_ETIMEOUT);
+    if (err & ERR_BOUNDS) return poison(b, TCM_EDEVICE);   // checked build only
     if (err & ERR_NOMEM) return poison(b, TCM_ENOMEM);
     return TCM_OK;
 }

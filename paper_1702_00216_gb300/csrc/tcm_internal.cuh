@@ -49,6 +49,7 @@ static_assert(BRICKS_PER_WARP == 1 || XQ <= 2, "pair exchange lane mapping needs
 
 constexpr unsigned ERR_NOMEM = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
+constexpr unsigned ERR_BOUNDS = 4u;   // the checked build found an index out of range
 
 constexpr unsigned FLAG_HAS_SRC = 1u << 15;
 constexpr unsigned SD_MASK = 0x7fffu;
@@ -199,6 +200,25 @@ struct MediaDev {
     const double *sph;
     const float *sph_c;
 };
+
+// Bounds checks of the checked build (compiled with -DTCM_CHECKED): every
+// box, brick, free-stack, list and claim index is checked before the access
+// it guards; an index out of range sets ERR_BOUNDS and the access is
+// skipped (no trap).  In the normal build the checks compile to `true`.
+#ifdef TCM_CHECKED
+__device__ __forceinline__ bool in_range(EngineState *st, long long i, long long n)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(&st->err, ERR_BOUNDS);
+    return false;
+}
+#define TCM_IN(E, i, n) ::tcm::in_range((E).st, (long long)(i), (long long)(n))
+#else
+#define TCM_IN(E, i, n) true
+#endif
+// the brick tables hold n_words * 32 entries
+#define TCM_BRICK_OK(E, g) TCM_IN(E, g, (E).n_words * 32)
+#define TCM_SLOT_OK(E, s) TCM_IN(E, s, (E).n_slots)
 
 // Field storage of simulation S's boxes.
 __host__ __device__ __forceinline__ int sim_storage(const Engine &E, const SimDev *S)

@@ -344,6 +344,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 {
     const int x4 = t % XQ;
     const int y = t / XQ;
+    valid = valid && TCM_SLOT_OK(E, w.slot);
     const int sim = valid ? (int)(w.flags >> 16) : 0;
     SimDev *S = E.sims + sim;
     const int mx = __ldg(&S->mx), my = __ldg(&S->my);
@@ -360,11 +361,14 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     float4 Zm = f4zero(), Zp = f4zero();
     // y-edge lanes read the touching row of y- / y+, x-edge lanes the
     // touching column of x- / x+ (unless exchanged within the pair)
-    const int ys = !valid ? -1 : (y == 0 ? w.nb[2] : (y == BY - 1 ? w.nb[3] : -1));
+    int ys = !valid ? -1 : (y == 0 ? w.nb[2] : (y == BY - 1 ? w.nb[3] : -1));
+    if (ys >= 0 && !TCM_SLOT_OK(E, ys)) ys = -1;
     // x-edge lanes: the column of x- (x4 == 0) or x+ (x4 == XQ-1); with one
     // float4 per row (XQ == 1) a lane is both, and xs2 is the x+ one
-    const int xs = !valid ? -1 : (x4 == 0 ? (share_xm ? -1 : w.nb[0]) : (x4 == XQ - 1 ? (share_xp ? -1 : w.nb[1]) : -1));
-    const int xs2 = (XQ == 1 && valid && !share_xp) ? w.nb[1] : -1;
+    int xs = !valid ? -1 : (x4 == 0 ? (share_xm ? -1 : w.nb[0]) : (x4 == XQ - 1 ? (share_xp ? -1 : w.nb[1]) : -1));
+    int xs2 = (XQ == 1 && valid && !share_xp) ? w.nb[1] : -1;
+    if (xs >= 0 && !TCM_SLOT_OK(E, xs)) xs = -1;
+    if (xs2 >= 0 && !TCM_SLOT_OK(E, xs2)) xs2 = -1;
     if (valid) {
         const typename F::T *now = half_ptr<ST, MIX>(E, w.slot, nh);
         // phi^{n-1} in binary32; v^n in the velocity form (16-bit storages)
@@ -382,8 +386,9 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 #pragma unroll
             for (int z = 0; z < BZ; ++z) K[z] = make_float4(ks, ks, ks, ks);
         }
-        if (w.nb[4] >= 0) Zm = F::ld(half_ptr<ST, MIX>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), sc);
-        if (w.nb[5] >= 0) Zp = F::ld(half_ptr<ST, MIX>(E, w.nb[5], nh) + 4 * t, sc);
+        if (w.nb[4] >= 0 && TCM_SLOT_OK(E, w.nb[4]))
+            Zm = F::ld(half_ptr<ST, MIX>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), sc);
+        if (w.nb[5] >= 0 && TCM_SLOT_OK(E, w.nb[5])) Zp = F::ld(half_ptr<ST, MIX>(E, w.nb[5], nh) + 4 * t, sc);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) {
@@ -630,7 +635,8 @@ __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_l
     unsigned won = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i)
-        if (i < n && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1) won |= 1u << i;
+        if (i < n && TCM_BRICK_OK(E, bb + b_local[i]) && atomicCAS(E.slot_of_brick + bb + b_local[i], -1, -2) == -1)
+            won |= 1u << i;
     if (won == 0) return;
     const int nw = __popc(won);
     // vacant boxes free_stack[top - nw .. top - 1]; the first nv claims get one
@@ -652,7 +658,12 @@ __device__ void claim_bricks(const Engine &E, int sim, SimDev *S, const int *b_l
         const int kslab = __ldg(E.kslab_of_brick + g);
         const float kscal = __ldg(E.kscal + g);
         const unsigned short sdw = __ldcg(E.sd_of_brick + g);
-        const int ns = __ldcg(E.free_stack + (top - 1 - k));
+        const int ns = TCM_SLOT_OK(E, top - 1 - k) ? __ldcg(E.free_stack + (top - 1 - k)) : -1;
+        if (!TCM_SLOT_OK(E, ns) || !TCM_SLOT_OK(E, nn + k)) {   // checked build: give the claim up
+            atomicExch(E.slot_of_brick + g, -1);
+            ++k;
+            continue;
+        }
         E.claim_step[ns] = step;
         SlotMeta m;
         m.brick = b_local[i];
@@ -777,7 +788,7 @@ __device__ __forceinline__ void build_items(const Engine &E, const long long (&g
         b[k] = (int)(g[k] - q.bb);
         const int cx = b[k] % q.mx, cy = (b[k] / q.mx) % q.my, cz = b[k] / (q.mx * q.my);
         // a brick outside its sim's grid (never listed) gets no box
-        slot[k] = (b[k] >= 0 && cz < q.mz) ? __ldcg(E.slot_of_brick + g[k]) : -1;
+        slot[k] = (b[k] >= 0 && cz < q.mz && TCM_BRICK_OK(E, g[k])) ? __ldcg(E.slot_of_brick + g[k]) : -1;
         kslab[k] = __ldg(E.kslab_of_brick + g[k]);
         kscal[k] = __ldg(E.kscal + g[k]);
         sd[k] = __ldcg(E.sd_of_brick + g[k]);
@@ -907,11 +918,13 @@ __device__ __forceinline__ void keep_or_release(const Engine &E, const WorkItem 
     if (keep) {
         if (sd != sd0) E.sd_of_brick[g] = (unsigned short)((w.flags & FLAG_HAS_SRC) | sd);
     } else {
+        if (!TCM_BRICK_OK(E, g)) return;
         if (sd0 != 0) E.sd_of_brick[g] = (unsigned short)(w.flags & FLAG_HAS_SRC);
         atomicExch(E.slot_of_brick + g, -1);
         atomicAnd(E.bitmap + (g >> 5), ~(1u << (unsigned)(g & 31)));
         atomicSub(E.blocktot + (int)((g >> 5) / E.words_per_block), 1);
-        E.retired[agg_add(&E.st->n_retired, 1)] = slot;
+        const int r = agg_add(&E.st->n_retired, 1);
+        if (TCM_SLOT_OK(E, r)) E.retired[r] = slot;
     }
 }
 
@@ -963,8 +976,9 @@ __device__ __noinline__ void p2_item26(const Engine &E, const WorkItem &w, bool 
         float2 nm[26];
 #pragma unroll
         for (int i = 0; i < 26; ++i)
-            nm[i] = nslot[i] >= 0 ? __ldcg(reinterpret_cast<const float2 *>(E.rec + (size_t)nslot[i] * 8 + 6))
-                                  : make_float2(0.f, 0.f);
+            nm[i] = (nslot[i] >= 0 && TCM_SLOT_OK(E, nslot[i]))
+                        ? __ldcg(reinterpret_cast<const float2 *>(E.rec + (size_t)nslot[i] * 8 + 6))
+                        : make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < 26; ++i)
             if (nslot[i] >= 0 && __float_as_uint(nm[i].y) == stamp && nm[i].x > thr) hot = true;
@@ -1014,7 +1028,8 @@ __device__ __noinline__ void p2_item_general(const Engine &E, const WorkItem w, 
         // the touching faces of the boxed neighbours (loads in parallel)
         float nf[6];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) nf[f] = w.nb[f] >= 0 ? __ldcg(E.rec + (size_t)w.nb[f] * 8 + (f ^ 1)) : 0.f;
+        for (int f = 0; f < 6; ++f)
+            nf[f] = (w.nb[f] >= 0 && TCM_SLOT_OK(E, w.nb[f])) ? __ldcg(E.rec + (size_t)w.nb[f] * 8 + (f ^ 1)) : 0.f;
 #pragma unroll
         for (int f = 0; f < 6; ++f)
             if (w.nb[f] >= 0 && nf[f] > thr) hot = true;
@@ -1289,7 +1304,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (base + u * nthr < nact && w[u].slot >= 0) p2_item(E, w[u], r0[u], r1[u], age_flip, stamp, sc);
+                if (base + u * nthr < nact && w[u].slot >= 0 && TCM_SLOT_OK(E, w[u].slot))
+                    p2_item(E, w[u], r0[u], r1[u], age_flip, stamp, sc);
         }
         // (Source bricks need no activation here: every source starts at its
         // sim's first step, its brick is boxed when the sim starts, and the
@@ -1303,10 +1319,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
         const int n_new = min(__ldcg(&st->n_new), E.n_slots);
-        for (int i = gwarp; i < n_new; i += nwarps) zero_box(E, __ldcg(E.newslots + i), lane);
+        for (int i = gwarp; i < n_new; i += nwarps) {
+            const int ns = __ldcg(E.newslots + i);
+            if (TCM_SLOT_OK(E, ns)) zero_box(E, ns, lane);
+        }
         const int n_ret = __ldcg(&st->n_retired);
         const int base = max(__ldcg(&st->free_top), 0);
-        for (int i = gtid; i < n_ret; i += nthr) E.free_stack[base + i] = __ldcg(E.retired + i);
+        for (int i = gtid; i < n_ret; i += nthr)
+            if (TCM_SLOT_OK(E, base + i) && TCM_SLOT_OK(E, i)) E.free_stack[base + i] = __ldcg(E.retired + i);
         compact_list(E, Lnext, &st->n_active[cur ^ 1], 1);
         // The last block to finish advances the step: every block has read
         // the step counters by then.
@@ -1482,7 +1502,7 @@ __global__ void k_admit(Engine E, int sim, const long long *bricks, long long n)
                 atomicAdd(&E.st->free_top, 1);
                 atomicOr(&E.st->err, ERR_NOMEM);
                 atomicOr(&S->poisoned, 1u);
-            } else {
+            } else if (TCM_SLOT_OK(E, idx) && TCM_BRICK_OK(E, g) && TCM_SLOT_OK(E, E.free_stack[idx])) {
                 slot = E.free_stack[idx];
                 E.slot_of_brick[g] = slot;
                 E.claim_step[slot] = -1;
@@ -1525,6 +1545,7 @@ __global__ void k_release(Engine E, int sim, long long bb, long long n)
         const int slot = E.slot_of_brick[g];
         if (slot < 0) continue;
         const int idx = atomicAdd(&E.st->free_top, 1);
+        if (!TCM_SLOT_OK(E, idx)) continue;
         E.free_stack[idx] = slot;
         E.slot_of_brick[g] = -1;
         E.sd_of_brick[g] = 0;

@@ -7,7 +7,11 @@ a simulation only holds boxes for the cells its wave occupies, so the loop
 asks the library for an upper bound on the boxes the running simulations can
 claim during the next tick (tcm_batch_headroom) and admits a request when the
 free boxes cover that bound plus the request's own (its source cells and
-their neighbourhood within one tick's reach).  Before every tick the bound is
+their neighbourhood within one tick's reach), and while the peak footprints
+of the running requests -- each the cells its wave can reach over its whole
+run at a little above the Courant speed, clipped to its grid: an estimate,
+not a bound -- fit the pool, so that running requests seldom have to wait
+for each other.  Before every tick the bound is
 checked again; if the running simulations could claim more boxes than are
 free, the most recently admitted ones are paused (tcm_batch_pause: they keep
 their boxes and state and later continue unchanged) until it fits, and
@@ -67,20 +71,25 @@ class _Running:
     admitted: float
     bricks: int
     paused: bool = False
+    reserve: int = 0
 
 
 class Server:
     def __init__(self, pool_bytes: int, max_bricks: int, max_sims: int = 256, steps_per_tick: int = 8,
                  device: int = 0, keep_fields: bool = False, clock: Optional[Callable[[], float]] = None,
-                 storage: str = "f32", storages: Optional[Sequence[str]] = None, admission: str = "footprint"):
+                 storage: str = "f32", storages: Optional[Sequence[str]] = None, admission: str = "footprint",
+                 peak_margin: float = 1.25):
         """storage: the field storage of every request; storages: serve these
         storages side by side in one batch of mixed storage (requests carry
-        their own).  admission: "footprint" (default) or "dense"."""
+        their own).  admission: "footprint" (default) or "dense".  peak_margin:
+        factor over the Courant speed in the estimate of a request's peak
+        footprint (smaller admits more at once and pauses more)."""
         names = list(dict.fromkeys(storages)) if storages else [storage]
         self.mixed = len(names) > 1
         self.storages = names
         assert admission in ("footprint", "dense")
         self.admission = admission
+        self.peak_margin = float(peak_margin)
         self.batch = tcm.Batch(pool_bytes=pool_bytes, max_bricks=max_bricks, max_sims=max_sims, device=device,
                                storage="mixed" if self.mixed else names[0])
         self.n_slots = self.batch.info()[0]
@@ -98,7 +107,7 @@ class Server:
         self.running: Dict[int, _Running] = {}      # in admission order
         self.queue: collections.deque = collections.deque()
         self.bricks_used = 0          # brick-table space of the running requests
-        self.reserved_boxes = 0       # dense admission: boxes reserved
+        self.reserved_boxes = 0       # boxes reserved: grids (dense admission) or peak footprints
         self.restarts = collections.Counter()
         self.stats = {"max_concurrent": 0, "max_grid_bricks_running": 0, "pauses": 0, "resumes": 0,
                       "evictions": 0, "headroom_calls": 0}
@@ -132,6 +141,24 @@ class Server:
                         cells.add((i, j, k))
         return min(len(cells), self.bricks_of(wl))
 
+    @staticmethod
+    def peak_footprint(wl, margin: float = 1.25) -> int:
+        """Cells a request's wave can reach over its whole run: those within
+        margin x (c_max dt / dx) x steps nodes of a source (values above the
+        level travel at the wave speed; the margin covers the dispersion of
+        Eq. 3 near the front), clipped to the grid."""
+        nz, ny, nx = wl.shape
+        bx, by, bz = wl.brick
+        courant = wl.media.c_max() * wl.dt / wl.dx
+        R = int(math.ceil(margin * courant * wl.steps)) + 1
+        total = 0
+        for x, y, z, _ in wl.sources:
+            n = 1
+            for c, size, b in ((x, nx, bx), (y, ny, by), (z, nz, bz)):
+                n *= min(size - 1, c + R) // b - max(0, c - R) // b + 1
+            total += n
+        return min(total, Server.bricks_of(wl))
+
     # ---- state ----------------------------------------------------------
     def now(self) -> float:
         """Seconds since the start of run(), or ticks in virtual mode."""
@@ -161,9 +188,9 @@ class Server:
         sim = self.batch.add(wl, n_steps=wl.steps, storage=storage)
         nb = self.bricks_of(wl)
         self.bricks_used += (nb + 31) // 32 * 32
-        if self.admission == "dense":
-            self.reserved_boxes += nb
-        self.running[req.rid] = _Running(req, sim, self.now(), nb)
+        reserve = nb if self.admission == "dense" else self.peak_footprint(wl, self.peak_margin)
+        self.reserved_boxes += reserve
+        self.running[req.rid] = _Running(req, sim, self.now(), nb, reserve=reserve)
         self.stats["max_concurrent"] = max(self.stats["max_concurrent"], len(self.running))
         # boxes that admission by whole grids would have had to reserve
         self.stats["max_grid_bricks_running"] = max(self.stats["max_grid_bricks_running"],
@@ -178,6 +205,8 @@ class Server:
                 if self.reserved_boxes + self.bricks_of(wl) > self.n_slots:
                     break
             else:
+                if self.running and self.reserved_boxes + self.peak_footprint(wl, self.peak_margin) > self.n_slots:
+                    break
                 if need is None:
                     need, free = self.headroom(), self.free_boxes()
                 est = self.new_request_bound(wl)
@@ -221,6 +250,7 @@ class Server:
             r = self.running.pop(rid)
             self.batch.remove(r.sim)
             self.bricks_used -= (r.bricks + 31) // 32 * 32
+            self.reserved_boxes -= r.reserve
             self.queue.appendleft(r.req)
             self.restarts[rid] += 1
             self.stats["evictions"] += 1
@@ -238,8 +268,7 @@ class Server:
             active = r.sim.active_count()[0]
             self.batch.remove(r.sim)
             self.bricks_used -= (r.bricks + 31) // 32 * 32
-            if self.admission == "dense":
-                self.reserved_boxes -= r.bricks
+            self.reserved_boxes -= r.reserve
             self.updates += upd
             storage = getattr(r.req, "storage", self.storages[0]) if self.mixed else self.storages[0]
             self.results.append(Result(rid, r.req.arrival * self._scale, r.admitted, self.now(), wl.steps, upd,

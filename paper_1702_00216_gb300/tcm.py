@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtcm.so")
+# TCM_CHECKED=1: the bounds-checked build of the same sources (see build.py)
+LIB_PATH = os.path.join(HERE, "libtcm_checked.so" if os.environ.get("TCM_CHECKED", "") == "1" else "libtcm.so")
 
 TCM_OK, TCM_EINVAL, TCM_ECFL, TCM_ENOMEM, TCM_EDEVICE, TCM_ETIMEOUT, TCM_ESTATE = range(7)
 TCM_MEDIA_DENSE, TCM_MEDIA_RULES = 0, 1

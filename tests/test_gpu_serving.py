@@ -56,16 +56,18 @@ def test_served_results_equal_the_oracle_and_solo_runs():
     reqs = small_stream(n=12, seed=77)
     assert {r.storage for r in reqs} == {"f32", "bf16"}
     # a pool far smaller than the requests' grids: admission by footprint,
-    # with pauses when the running waves outgrow the free boxes
+    # with peak footprints deliberately underestimated so that the running
+    # waves outgrow the free boxes and get paused and resumed
     total = sum(serve.Server.bricks_of(q.workload) for q in reqs)
     srv = serve.Server(pool_bytes=700 * tcm.tcm_slot_bytes(), max_bricks=1 << 16, max_sims=8, steps_per_tick=7,
-                       keep_fields=True, storages=("f32", "bf16"))
+                       keep_fields=True, storages=("f32", "bf16"), peak_margin=0.1)
     res = srv.run(reqs, time_scale=1.0, virtual=True)
     srv.close()
     assert len(res) == len(reqs)
     # more grid bricks running at once than the pool has boxes: admission by
     # whole grids could not have run them together
     assert srv.stats["max_grid_bricks_running"] > srv.n_slots, srv.stats
+    assert srv.stats["pauses"] > 0, srv.stats
     overlapped = sum(any(q.rid != r.rid and q.admitted < r.done and r.admitted < q.done for q in res) for r in res)
     assert overlapped >= len(res) // 2, "requests should share the GPU"
     assert total > 700

@@ -150,7 +150,8 @@ def test_footprint_admission_finishes_everything_and_never_exhausts(fake):
 
 
 def test_footprint_holds_more_simulations_than_dense_admission(fake):
-    reqs = stream(30, 5, rate_hz=50.0, edge_lo=48, edge_hi=64, steps_lo=40, steps_hi=80)
+    # short runs in large grids: the waves stay far smaller than the grids
+    reqs = stream(30, 5, rate_hz=50.0, edge_lo=48, edge_hi=64, steps_lo=12, steps_hi=20)
     peaks = {}
     for adm in ("dense", "footprint"):
         srv = serve.Server(pool_bytes=1500 * 4096, max_bricks=1 << 16, max_sims=32, steps_per_tick=4,
@@ -163,10 +164,12 @@ def test_footprint_holds_more_simulations_than_dense_admission(fake):
 
 
 def test_pauses_and_resumes_when_growth_outruns_the_pool(fake):
-    # few boxes, many long requests arriving together: running simulations
-    # outgrow the free boxes and must be paused, then resumed
+    # few boxes, many long requests arriving together, and peak footprints
+    # estimated far too small: running simulations outgrow the free boxes and
+    # must be paused, then resumed
     reqs = stream(12, 9, rate_hz=1000.0, edge_lo=40, edge_hi=48, steps_lo=60, steps_hi=90)
-    srv = serve.Server(pool_bytes=400 * 4096, max_bricks=1 << 16, max_sims=12, steps_per_tick=6)
+    srv = serve.Server(pool_bytes=400 * 4096, max_bricks=1 << 16, max_sims=12, steps_per_tick=6,
+                       peak_margin=0.02)
     res = srv.run(reqs, time_scale=1.0, virtual=True)
     check_done(srv, res, reqs)
     assert srv.stats["pauses"] > 0 and srv.stats["resumes"] > 0, srv.stats
@@ -176,7 +179,8 @@ def test_eviction_when_paused_simulations_hold_the_pool(fake):
     # each request alone fits (216-343 cells <= 360 boxes), but two grown ones
     # do not: the loop must evict and restart rather than stall
     reqs = stream(6, 11, rate_hz=1000.0, edge_lo=48, edge_hi=56, steps_lo=80, steps_hi=90)
-    srv = serve.Server(pool_bytes=360 * 4096, max_bricks=1 << 16, max_sims=6, steps_per_tick=6)
+    srv = serve.Server(pool_bytes=360 * 4096, max_bricks=1 << 16, max_sims=6, steps_per_tick=6,
+                       peak_margin=0.02)
     res = srv.run(reqs, time_scale=1.0, virtual=True)
     check_done(srv, res, reqs)
     assert srv.stats["evictions"] > 0 and any(r.restarts for r in res), srv.stats
@@ -230,3 +234,24 @@ def test_new_request_bound_covers_its_first_tick():
     assert r == 3
     # cell (0, 2, 4) of a 7 x 6 x 5 grid: x 0..3, y 0..5, z 1..4 -> 4 * 6 * 4
     assert srv.new_request_bound(wl) == 4 * 6 * 4
+
+
+def test_peak_footprint_estimate():
+    """The cells a wave can reach over a run at 1.25 x the Courant speed,
+    clipped to the grid: 20 steps at Courant 0.5 reach 13.5 -> 14 nodes."""
+    wl = W.Workload("p", (64, 64, 64), W.homogeneous(1.0), 1.0, 0.5, [(30, 5, 60, W.ricker(0.1, 0.5))], 20)
+    # x 16..44 -> cells 2..5 (4), y 0..19 -> 0..2 (3), z 46..63 -> 5..7 (3)
+    assert serve.Server.peak_footprint(wl) == 4 * 3 * 3
+    long_run = W.Workload("q", (64, 64, 64), W.homogeneous(1.0), 1.0, 0.5, [(30, 5, 60, W.ricker(0.1, 0.5))], 900)
+    assert serve.Server.peak_footprint(long_run) == 512
+
+
+def test_peak_estimates_keep_the_loop_from_thrashing(fake):
+    """With the default estimate of each request's peak footprint, a burst of
+    long requests is admitted only as far as their peaks fit: no pauses or
+    evictions are needed."""
+    reqs = stream(12, 9, rate_hz=1000.0, edge_lo=40, edge_hi=48, steps_lo=60, steps_hi=90)
+    srv = serve.Server(pool_bytes=400 * 4096, max_bricks=1 << 16, max_sims=12, steps_per_tick=6)
+    res = srv.run(reqs, time_scale=1.0, virtual=True)
+    check_done(srv, res, reqs)
+    assert srv.stats["pauses"] == 0 and srv.stats["evictions"] == 0, srv.stats
