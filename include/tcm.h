@@ -264,6 +264,13 @@ tcm_status tcm_pool_info(const tcm_sim *sim, int64_t *slots, int64_t *free_slots
  * for its step (Results, Fig. 11). */
 tcm_status tcm_phase_ns(const tcm_sim *sim, int64_t *stepping, int64_t *update, int64_t *compaction);
 
+/* The Eq. 7 filter's work so far: device time of its working launches (ns,
+ * from the GPU's global timer), bricks filtered, and FP64 multiply-adds per
+ * filtered brick (two time levels through the separable operator: 319488 for
+ * 8^3 cells; 0 for shapes the filter does not support).  Not in the paper:
+ * the numbers behind the filter's FP64 roofline. */
+tcm_status tcm_lpf_info(const tcm_sim *sim, int64_t *ns, int64_t *bricks, int64_t *fma_per_brick);
+
 /* Kernel launches issued so far (one per step). */
 int64_t tcm_launch_count(const tcm_sim *sim);
 /* How many of those launches were replayed from captured CUDA graphs. */

@@ -1422,6 +1422,20 @@ tcm_status tcm_phase_ns(const tcm_sim *cs, int64_t *stepping, int64_t *update, i
     return TCM_OK;
 }
 
+tcm_status tcm_lpf_info(const tcm_sim *cs, int64_t *ns, int64_t *bricks, int64_t *fma_per_brick)
+{
+    if (!sim_of(cs)) return TCM_EINVAL;
+    tcm_batch *b = cs->b;
+    DeviceGuard g(b->device);
+    EngineState es{};
+    TRY(cudaMemcpyAsync(&es, b->E.st, sizeof(es), cudaMemcpyDeviceToHost, b->stream));
+    TRY(cudaStreamSynchronize(b->stream));
+    if (ns) *ns = (int64_t)es.lpf_ns;
+    if (bricks) *bricks = (int64_t)es.lpf_bricks;
+    if (fma_per_brick) *fma_per_brick = (BX == BY && BX == BZ) ? LPF_FMA_PER_BRICK : 0;
+    return TCM_OK;
+}
+
 int64_t tcm_launch_count(const tcm_sim *s) { return sim_of(s) ? s->b->launches : -1; }
 
 int64_t tcm_graph_launch_count(const tcm_sim *s) { return sim_of(s) ? s->b->graph_launches : -1; }

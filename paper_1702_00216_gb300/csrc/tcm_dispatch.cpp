@@ -73,6 +73,7 @@ DECL3(tcm_status, set_storage, (void *, int))
 DECL3(tcm_status, batch_pause, (void *))
 DECL3(tcm_status, batch_resume, (void *))
 DECL3(tcm_status, batch_headroom, (void *, int64_t, int64_t *))
+DECL3(tcm_status, lpf_info, (const void *, int64_t *, int64_t *, int64_t *))
 
 // Call the build of `shape` (0 4x4x4, 1 8x8x8, 2 16x8x8, 3 8x8x8 with 4 warps
 // per CTA, 4 8x8x8 with 16 warps per CTA).
@@ -265,6 +266,12 @@ tcm_status tcm_phase_ns(const tcm_sim *s, int64_t *a, int64_t *b, int64_t *c)
 {
     SIM_OK(s);
     return SHAPE_CALL(s->shape, phase_ns, s->impl, a, b, c);
+}
+
+tcm_status tcm_lpf_info(const tcm_sim *s, int64_t *ns, int64_t *bricks, int64_t *fma_per_brick)
+{
+    SIM_OK(s);
+    return SHAPE_CALL(s->shape, lpf_info, s->impl, ns, bricks, fma_per_brick);
 }
 
 int64_t tcm_launch_count(const tcm_sim *s) { return s ? SHAPE_CALL(s->shape, launch_count, s->impl) : -1; }

@@ -144,7 +144,10 @@ struct EngineState {
     int list_age;          // launches since the active list was built (phase of its nh)
     int n_lpf_q;           // bricks released this update that held values (Eq. 7 sources)
     int n_lpf_aff;         // boxed bricks the Eq. 7 filter rewrites this update
-    int pad_lpf;
+    unsigned lpf_done;     // blocks finished with the Eq. 7 kernel this launch
+    unsigned long long t_lpf;          // globaltimer at the start of the Eq. 7 kernel
+    unsigned long long lpf_ns;         // cumulative: time of the Eq. 7 kernel's working launches
+    unsigned long long lpf_bricks;     // cumulative: bricks it filtered
 };
 
 // Eq. 7 region: the 3x3x3-brick block around a brick (LPF_L nodes per axis),
@@ -305,6 +308,12 @@ cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaS
 // Eq. 7 filtering after a launch whose update released bricks of LPF sims.
 cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s);
 int lpf_grid_size(int device);
+// Multiply-adds of the Eq. 7 filter per filtered brick: two time levels, each
+// through the separable operator along x (L^2 rows of C outputs from L
+// inputs), y (L C rows) and z (C^2 rows).
+constexpr long long LPF_FMA_PER_BRICK =
+    2LL * ((long long)LPF_L * LPF_L * LPF_C * LPF_L + (long long)LPF_L * LPF_C * LPF_C * LPF_L +
+           (long long)LPF_C * LPF_C * LPF_C * LPF_L);
 int step_grid_size(int device);
 cudaError_t launch_read_window(const Engine &e, int sim, int now_half, int which, long long x0, long long y0,
                                long long z0, long long wx, long long wy, long long wz, float *out,

@@ -1893,6 +1893,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
     const int nq = __ldcg(&st->n_lpf_q);
     if (nq == 0) return;   // the same value for every block: nobody waits
     const int gtid = blockIdx.x * BLOCK + threadIdx.x, nthr = gridDim.x * BLOCK;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_lpf = globaltimer();
     // (A) the affected bricks
     for (long long i = gtid; i < (long long)nq * 26; i += nthr) {
         const long long q = E.lpf_q[i / 26];
@@ -2043,6 +2044,20 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
             store_phys(E, st, slot, V_HALF, loc, __fsub_rn(sn, so), S->inv_scale);
         }
         if (loc == 0) E.lpf_mark[slot] = 0;
+    }
+    // the last block accounts the launch (time and filtered bricks)
+    __shared__ int s_last_lpf;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last_lpf = atomicAdd(&st->lpf_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last_lpf && threadIdx.x == 0) {
+        __threadfence();
+        st->lpf_ns += globaltimer() - __ldcg(&st->t_lpf);
+        st->lpf_bricks += (unsigned long long)naff;
+        st->lpf_done = 0u;
     }
 }
 

@@ -36,7 +36,7 @@ EXPORTS = ["tcm_slot_bytes", "tcm_create", "tcm_add_source", "tcm_set_field", "t
            "tcm_status_string", "tcm_destroy", "tcm_batch_create", "tcm_batch_add",
            "tcm_batch_step", "tcm_batch_step_async", "tcm_batch_sync", "tcm_sim_done",
            "tcm_batch_remove", "tcm_batch_info", "tcm_batch_destroy", "tcm_barrier_selftest",
-           "tcm_set_storage", "tcm_batch_pause", "tcm_batch_resume", "tcm_batch_headroom"]
+           "tcm_set_storage", "tcm_batch_pause", "tcm_batch_resume", "tcm_batch_headroom", "tcm_lpf_info"]
 
 
 class tcm_domain(C.Structure):
@@ -126,6 +126,7 @@ def lib():
             "tcm_batch_pause": ([_vp], C.c_int),
             "tcm_batch_resume": ([_vp], C.c_int),
             "tcm_batch_headroom": ([_vp, _i64, _vp], C.c_int),
+            "tcm_lpf_info": ([_vp, _vp, _vp, _vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -300,6 +301,13 @@ def tcm_phase_ns(h):
     """(time stepping, updating active cells, compaction) cumulative device ns."""
     a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
     _chk(lib().tcm_phase_ns(h, C.byref(a), C.byref(b), C.byref(c)), "tcm_phase_ns")
+    return a.value, b.value, c.value
+
+
+def tcm_lpf_info(h):
+    """(ns, bricks filtered, FP64 multiply-adds per brick) of the Eq. 7 filter so far."""
+    a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _chk(lib().tcm_lpf_info(h, C.byref(a), C.byref(b), C.byref(c)), "tcm_lpf_info")
     return a.value, b.value, c.value
 
 
