@@ -535,15 +535,17 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
         dt = min(dts)
         r = {"seconds": dt, "seconds_each": dts, "cell_updates": s.updates, "schedule": list(s.schedule())}
         if w.lpf is not None:
-            # the Eq. 7 filter's roofline: FP64 multiply-adds of the separable
-            # operator per filtered brick over the filter kernel's device time,
-            # against GB300's nominal FP64 rate (no measured FP64 peak)
+            # the Eq. 7 filter's roofline: binary32 multiply-adds of the
+            # separable operator per filtered brick over the filter kernel's
+            # device time, against the CUDA-core FP32 rate derived from unit
+            # counts and clocks (152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz)
             ns, nbr, fma = tcm.tcm_lpf_info(s.handle)
             flops = 2.0 * fma * nbr
-            r["k_lpf"] = {"ms": ns / 1e6, "bricks_filtered": nbr, "fp64_fma_per_brick": fma,
-                          "fp64_tflops": flops / (ns * 1e-9) / 1e12 if ns else None,
-                          "peak_tflops": 1.25, "peak_source": "nominal FP64 of GB300",
-                          "frac": (flops / (ns * 1e-9) / 1e12) / 1.25 if ns else None,
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            r["k_lpf"] = {"ms": ns / 1e6, "bricks_filtered": nbr, "fp32_fma_per_brick": fma,
+                          "fp32_tflops": flops / (ns * 1e-9) / 1e12 if ns else None,
+                          "peak_tflops": peak, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                          "frac": (flops / (ns * 1e-9) / 1e12) / peak if ns else None,
                           "share_of_run": (ns / 1e9) / dt}
         if ref is None:
             ref = buf

@@ -179,8 +179,13 @@ tcm_status tcm_set_schedule(tcm_sim *sim, int interval, int neighbours);
  * outside bricks read zero) zero-padded to M^3, M the power of two >= 2 L
  * (spatial oversampling; 64 for 8^3 bricks), LPF = H(kx) H(ky) H(kz), H = 1 up to `pass`, 0
  * from `stop` (fractions of the Nyquist frequency), raised cosine between;
- * the centre brick of the result is kept (FP64 arithmetic, rounded to the
- * storage).  All filtered values come from the state before any is
+ * the centre brick of the result is kept.  The filter is applied as the
+ * separable operator equal to that transform (its centre rows, computed in
+ * FP64 and rounded once to binary32) in binary32 FMA arithmetic, x, y, z in
+ * turn, each output summed over the taps in increasing order; against exact
+ * arithmetic the result is within 3 (L + 1) 2^-24 |A|^3 max|Phi| per
+ * application, |A| the largest absolute row sum of the 1-D operator (about
+ * 1.5 at pass 0.25, stop 0.5), then rounded to the storage.  All filtered values come from the state before any is
  * written.  decay_alpha / decay_steps are then unused.  0 < pass < stop <= 1
  * and cubic bricks (TCM_EINVAL otherwise); only before the first step
  * (TCM_ESTATE).  At most
@@ -265,10 +270,10 @@ tcm_status tcm_pool_info(const tcm_sim *sim, int64_t *slots, int64_t *free_slots
 tcm_status tcm_phase_ns(const tcm_sim *sim, int64_t *stepping, int64_t *update, int64_t *compaction);
 
 /* The Eq. 7 filter's work so far: device time of its working launches (ns,
- * from the GPU's global timer), bricks filtered, and FP64 multiply-adds per
- * filtered brick (two time levels through the separable operator: 319488 for
- * 8^3 cells; 0 for shapes the filter does not support).  Not in the paper:
- * the numbers behind the filter's FP64 roofline. */
+ * from the GPU's global timer), bricks filtered, and binary32 multiply-adds
+ * per filtered brick (two time levels through the separable operator: 319488
+ * for 8^3 cells; 0 for shapes the filter does not support).  Not in the
+ * paper: the numbers behind the filter's roofline. */
 tcm_status tcm_lpf_info(const tcm_sim *sim, int64_t *ns, int64_t *bricks, int64_t *fma_per_brick);
 
 /* Kernel launches issued so far (one per step). */

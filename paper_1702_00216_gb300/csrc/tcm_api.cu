@@ -47,7 +47,7 @@ struct HostSim {
     long long target = -1;   // freeze after this many steps (-1: never)
     double dx = 1, dt = 1;
     float c_max = 0.f;
-    double *lpf_a = nullptr;   // Eq. 7 filter operator (device)
+    float *lpf_a = nullptr;    // Eq. 7 filter operator (device)
     SimDev dev{};
 };
 
@@ -1195,8 +1195,9 @@ tcm_status tcm_set_lpf_shutdown(tcm_sim *s, double pass, double stop)
     }
     // Centre rows of the 1-D operator P^T F^-1 diag(H) F P (zero-padding P of
     // LPF_L nodes to LPF_M, DFT F): A[i][j] = (1/M) sum_k H(k) cos(2 pi k
-    // (i + C - j) / M) -- real because H(k) = H(M - k).
-    std::vector<double> A((size_t)LPF_C * LPF_L);
+    // (i + C - j) / M) -- real because H(k) = H(M - k).  Summed in FP64 and
+    // rounded once to binary32, the precision the filter runs in.
+    std::vector<float> A((size_t)LPF_C * LPF_L);
     for (int i = 0; i < LPF_C; ++i)
         for (int j = 0; j < LPF_L; ++j) {
             double acc = 0.0;
@@ -1206,15 +1207,15 @@ tcm_status tcm_set_lpf_shutdown(tcm_sim *s, double pass, double stop)
                 const double hk = nu <= pass ? 1.0 : nu >= stop ? 0.0 : 0.5 * (1.0 + std::cos(M_PI * (nu - pass) / (stop - pass)));
                 acc += hk * std::cos(2.0 * M_PI * (double)k * (double)(i + LPF_C - j) / LPF_M);
             }
-            A[(size_t)i * LPF_L + j] = acc / LPF_M;
+            A[(size_t)i * LPF_L + j] = (float)(acc / LPF_M);
         }
     if (!h->lpf_a) {
-        if (cudaMalloc(&h->lpf_a, A.size() * sizeof(double)) != cudaSuccess) {
+        if (cudaMalloc(&h->lpf_a, A.size() * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return TCM_ENOMEM;
         }
     }
-    TRY(cudaMemcpyAsync(h->lpf_a, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    TRY(cudaMemcpyAsync(h->lpf_a, A.data(), A.size() * sizeof(float), cudaMemcpyHostToDevice, b->stream));
     TRY(cudaStreamSynchronize(b->stream));
     h->dev.lpf = 1;
     h->dev.lpf_a = h->lpf_a;

@@ -106,7 +106,7 @@ struct SimDev {
     int interval;          // the update procedure runs after every interval-th step
     int neighbours;        // 6: activation across hot faces; 26: all neighbours of a hot cell
     int lpf;               // 1: frequency-domain shut-down (Eq. 7) instead of the decay
-    const double *lpf_a;   // LPF_C x LPF_L centre rows of the 1-D filter operator (FP64)
+    const float *lpf_a;    // LPF_C x LPF_L centre rows of the 1-D filter operator (binary32)
     int storage;           // field storage of this sim's boxes (ST_F32 / ST_BF16 / ST_F16)
     int pad_storage;
     // mutable (device-owned)

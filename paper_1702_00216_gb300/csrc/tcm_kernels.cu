@@ -1855,16 +1855,24 @@ int step_grid_size(int device)
 // ---------------------------------------------------------------------------
 // Eq. 7 frequency-domain shut-down, after an update that released bricks
 // holding values (lpf_q): (A) every boxed 26-neighbour of such a brick that
-// was not claimed by this update is listed once; (B) for each listed brick,
-// its 3x3x3-brick block (both halves; released, unboxed and outside bricks
-// read zero) goes through the separable filter operator A (x, then y, then
-// z, FP64 in a fixed order) and the centre brick is kept in lpf_out; (C) the
-// filtered values replace the bricks' halves (nodes outside the domain stay
-// zero).  Every filtered value comes from the state before (C).
+// was not claimed by this update is listed once; (B) for each listed brick
+// and each of its two levels, the level over its 3x3x3-brick block
+// (released, unboxed and outside bricks read zero) goes through the
+// separable filter operator A (x, then y, then z; binary32 FMA, each output
+// summed over the taps in increasing order) and the centre brick is kept in
+// lpf_out; (C) the filtered values replace the bricks' halves (nodes outside
+// the domain stay zero).  Every filtered value comes from the state before (C).
 // ---------------------------------------------------------------------------
-constexpr size_t LPF_SMEM = (size_t)2 * LPF_L * LPF_L * LPF_L * sizeof(float) +
-                            (size_t)LPF_L * LPF_L * LPF_C * sizeof(double) +
-                            (size_t)LPF_L * LPF_C * LPF_C * sizeof(double) + (size_t)LPF_C * LPF_L * sizeof(double);
+// Shared memory of one (brick, level) unit: R [L][L][L] the level over the
+// block; T1 [L][L][C] after the x pass; T2 [L][C][C] after the y pass; Ax
+// [C][LPF_LP] the operator's rows, padded so that the two row groups a warp
+// reads sit in different banks; At [L][C] the operator transposed (four
+// consecutive outputs per vector).
+constexpr int LPF_LP = LPF_L + 4;
+constexpr int LPF_BLOCK = 256;   // threads per CTA of the filter kernel (every build)
+constexpr size_t LPF_SMEM = sizeof(float) * ((size_t)LPF_L * LPF_L * LPF_L + (size_t)LPF_L * LPF_L * LPF_C +
+                                             (size_t)LPF_L * LPF_C * LPF_C + (size_t)LPF_C * LPF_LP +
+                                             (size_t)LPF_L * LPF_C);
 
 __device__ __forceinline__ long long lpf_neighbour(const SimDev *S, long long base, int b, int dx, int dy, int dz)
 {
@@ -1886,13 +1894,35 @@ __device__ __forceinline__ float4 load_phys4(const Engine &E, int st, int slot, 
     return Fld<ST_F16>::cvt(u, scale);
 }
 
-__global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
+// acc + w.x v.x + w.y v.y + w.z v.z + w.w v.w, one FMA per term in that order
+__device__ __forceinline__ float fma4(float4 w, float4 v, float acc)
+{
+    acc = __fmaf_rn(w.x, v.x, acc);
+    acc = __fmaf_rn(w.y, v.y, acc);
+    acc = __fmaf_rn(w.z, v.z, acc);
+    return __fmaf_rn(w.w, v.w, acc);
+}
+
+// o[t] += w[t] * v (one tap j of four outputs i0+t, over four x)
+__device__ __forceinline__ void outer4(float4 w, float4 v, float4 *o)
+{
+    const float wt[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        o[t].x = __fmaf_rn(wt[t], v.x, o[t].x);
+        o[t].y = __fmaf_rn(wt[t], v.y, o[t].y);
+        o[t].z = __fmaf_rn(wt[t], v.z, o[t].z);
+        o[t].w = __fmaf_rn(wt[t], v.w, o[t].w);
+    }
+}
+
+__global__ void __launch_bounds__(LPF_BLOCK, 2) k_lpf(Engine E)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     EngineState *st = E.st;
     const int nq = __ldcg(&st->n_lpf_q);
     if (nq == 0) return;   // the same value for every block: nobody waits
-    const int gtid = blockIdx.x * BLOCK + threadIdx.x, nthr = gridDim.x * BLOCK;
+    const int gtid = blockIdx.x * LPF_BLOCK + threadIdx.x, nthr = gridDim.x * LPF_BLOCK;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t_lpf = globaltimer();
     // (A) the affected bricks
     for (long long i = gtid; i < (long long)nq * 26; i += nthr) {
@@ -1913,13 +1943,17 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
     }
     if (!grid_barrier(st, &st->bar_count_lpf)) return;
     const int naff = min(__ldcg(&st->n_lpf_aff), E.lpf_cap);
-    // (B) one block per affected brick
+    // (B) one block per (affected brick, level)
     __shared__ int s_nbslot[27];   // boxes of the 3x3x3 block (-1: none)
-    float *R = reinterpret_cast<float *>(smem);                         // [2][L][L][L]
-    double *T1 = reinterpret_cast<double *>(R + 2 * LPF_L * LPF_L * LPF_L);   // [L][L][C]
-    double *T2 = T1 + LPF_L * LPF_L * LPF_C;                               // [L][C][C]
-    double *A = T2 + LPF_L * LPF_C * LPF_C;                                // [C][L]
-    for (int c = blockIdx.x; c < naff; c += gridDim.x) {
+    float *R = reinterpret_cast<float *>(smem);
+    float *T1 = R + LPF_L * LPF_L * LPF_L;
+    float *T2 = T1 + LPF_L * LPF_L * LPF_C;
+    float *Ax = T2 + LPF_L * LPF_C * LPF_C;
+    float *At = Ax + LPF_C * LPF_LP;
+    static_assert(LPF_C % 4 == 0, "four outputs per thread");
+    constexpr int C4 = LPF_C / 4, Q = BVOL / 4;
+    for (int u = blockIdx.x; u < 2 * naff; u += gridDim.x) {
+        const int c = u >> 1, h = u & 1;
         const long long g = E.lpf_aff[c];
         const SimDev *S = E.sims + E.sim_of_word[g >> 5];
         const long long base = S->brick_base;
@@ -1931,95 +1965,80 @@ __global__ void __launch_bounds__(BLOCK, 1) k_lpf(Engine E)
             const long long gn = lpf_neighbour(S, base, b, nb % 3 - 1, (nb / 3) % 3 - 1, nb / 9 - 1);
             s_nbslot[nb] = gn >= 0 ? __ldcg(E.slot_of_brick + gn) : -1;
         }
-        for (int i = threadIdx.x; i < LPF_C * LPF_L; i += BLOCK) A[i] = S->lpf_a[i];
+        for (int i = threadIdx.x; i < LPF_C * LPF_L; i += LPF_BLOCK) {
+            const float a = S->lpf_a[i];
+            Ax[(i / LPF_L) * LPF_LP + i % LPF_L] = a;
+            At[(i % LPF_L) * LPF_C + i / LPF_L] = a;
+        }
         __syncthreads();
-        // the block's two levels, four x-consecutive nodes per vector (a row
+        // the level over the block, four x-consecutive nodes per vector (a row
         // of a brick is x-contiguous in its box and in R)
-        constexpr int Q = BVOL / 4;
 #pragma unroll 4
-        for (int e4 = threadIdx.x; e4 < 27 * 2 * Q; e4 += BLOCK) {
-            const int nb = e4 / (2 * Q), h = (e4 / Q) & 1, loc = (e4 % Q) * 4;
+        for (int e4 = threadIdx.x; e4 < 27 * Q; e4 += LPF_BLOCK) {
+            const int nb = e4 / Q, loc = (e4 % Q) * 4;
             const int slot = s_nbslot[nb];
             const float4 v = slot >= 0 ? load_phys4(E, st, slot, h, loc, sc) : make_float4(0.f, 0.f, 0.f, 0.f);
             const int lx = loc % BX, ly = (loc / BX) % BY, lz = loc / (BX * BY);
-            *reinterpret_cast<float4 *>(R + ((h * LPF_L + (nb / 9) * LPF_C + lz) * LPF_L + ((nb / 3) % 3) * LPF_C + ly) *
-                                                LPF_L +
+            *reinterpret_cast<float4 *>(R + (((nb / 9) * LPF_C + lz) * LPF_L + ((nb / 3) % 3) * LPF_C + ly) * LPF_L +
                                         (nb % 3) * LPF_C + lx) = v;
         }
         __syncthreads();
         // Rows of R that lie in bricks of the block with no box are zero and
         // filter to +0 exactly: those rows (x pass) and z-slabs (y pass) are
-        // skipped.  Each thread keeps four outputs in flight (independent FP64
-        // chains); every output sums over j in increasing order, one FMA per
-        // term.
+        // skipped.  Each thread keeps four (x pass) or sixteen (y, z passes)
+        // independent outputs in flight.
         auto row_live = [&](int dz, int dy) {
             const int k = (dz * 3 + dy) * 3;
             return s_nbslot[k] >= 0 || s_nbslot[k + 1] >= 0 || s_nbslot[k + 2] >= 0;
         };
-        static_assert(LPF_C % 4 == 0, "four outputs per thread");
-        constexpr int C4 = LPF_C / 4;
-        for (int h = 0; h < 2; ++h) {
-            for (int e = threadIdx.x; e < LPF_L * LPF_L * C4; e += BLOCK) {   // along x
-                const int i = (e % C4) * 4, zy = e / C4;
-                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-                if (row_live((zy / LPF_L) / LPF_C, (zy % LPF_L) / LPF_C)) {
-                    const float *row = R + ((size_t)h * LPF_L * LPF_L + zy) * LPF_L;
-#pragma unroll 4
-                    for (int j = 0; j < LPF_L; ++j) {
-                        const double r = (double)row[j];
-                        a0 = __fma_rn(A[(i + 0) * LPF_L + j], r, a0);
-                        a1 = __fma_rn(A[(i + 1) * LPF_L + j], r, a1);
-                        a2 = __fma_rn(A[(i + 2) * LPF_L + j], r, a2);
-                        a3 = __fma_rn(A[(i + 3) * LPF_L + j], r, a3);
-                    }
+        for (int e = threadIdx.x; e < LPF_L * LPF_L * C4; e += LPF_BLOCK) {   // along x
+            const int i0 = (e % C4) * 4, zy = e / C4;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            if (row_live((zy / LPF_L) / LPF_C, (zy % LPF_L) / LPF_C)) {
+                const float4 *row = reinterpret_cast<const float4 *>(R + zy * LPF_L);
+                const float4 *w0 = reinterpret_cast<const float4 *>(Ax + (i0 + 0) * LPF_LP);
+                const float4 *w1 = reinterpret_cast<const float4 *>(Ax + (i0 + 1) * LPF_LP);
+                const float4 *w2 = reinterpret_cast<const float4 *>(Ax + (i0 + 2) * LPF_LP);
+                const float4 *w3 = reinterpret_cast<const float4 *>(Ax + (i0 + 3) * LPF_LP);
+#pragma unroll
+                for (int q = 0; q < LPF_L / 4; ++q) {
+                    const float4 v = row[q];
+                    a0 = fma4(w0[q], v, a0);
+                    a1 = fma4(w1[q], v, a1);
+                    a2 = fma4(w2[q], v, a2);
+                    a3 = fma4(w3[q], v, a3);
                 }
-                double *t = T1 + zy * LPF_C + i;
-                t[0] = a0;
-                t[1] = a1;
-                t[2] = a2;
-                t[3] = a3;
             }
-            __syncthreads();
-            for (int e = threadIdx.x; e < LPF_L * C4 * LPF_C; e += BLOCK) {   // along y
-                const int x = e % LPF_C, i = ((e / LPF_C) % C4) * 4, z = e / (LPF_C * C4);
-                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-                const int dz = z / LPF_C;
-                if (row_live(dz, 0) || row_live(dz, 1) || row_live(dz, 2)) {
-#pragma unroll 4
-                    for (int j = 0; j < LPF_L; ++j) {
-                        const double v = T1[(z * LPF_L + j) * LPF_C + x];
-                        a0 = __fma_rn(A[(i + 0) * LPF_L + j], v, a0);
-                        a1 = __fma_rn(A[(i + 1) * LPF_L + j], v, a1);
-                        a2 = __fma_rn(A[(i + 2) * LPF_L + j], v, a2);
-                        a3 = __fma_rn(A[(i + 3) * LPF_L + j], v, a3);
-                    }
-                }
-                double *t = T2 + (z * LPF_C + i) * LPF_C + x;
-                t[0] = a0;
-                t[LPF_C] = a1;
-                t[2 * LPF_C] = a2;
-                t[3 * LPF_C] = a3;
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < C4 * LPF_C * LPF_C; e += BLOCK) {   // along z
-                const int x = e % LPF_C, y = (e / LPF_C) % LPF_C, i = (e / (LPF_C * LPF_C)) * 4;
-                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-#pragma unroll 4
-                for (int j = 0; j < LPF_L; ++j) {
-                    const double v = T2[(j * LPF_C + y) * LPF_C + x];
-                    a0 = __fma_rn(A[(i + 0) * LPF_L + j], v, a0);
-                    a1 = __fma_rn(A[(i + 1) * LPF_L + j], v, a1);
-                    a2 = __fma_rn(A[(i + 2) * LPF_L + j], v, a2);
-                    a3 = __fma_rn(A[(i + 3) * LPF_L + j], v, a3);
-                }
-                float *o = E.lpf_out + (size_t)c * 2 * BVOL + h * BVOL + (i * LPF_C + y) * LPF_C + x;
-                o[0] = (float)a0;
-                o[LPF_C * LPF_C] = (float)a1;
-                o[2 * LPF_C * LPF_C] = (float)a2;
-                o[3 * LPF_C * LPF_C] = (float)a3;
-            }
-            __syncthreads();
+            *reinterpret_cast<float4 *>(T1 + zy * LPF_C + i0) = make_float4(a0, a1, a2, a3);
         }
+        __syncthreads();
+        for (int e = threadIdx.x; e < LPF_L * C4 * C4; e += LPF_BLOCK) {   // along y
+            const int x0 = (e % C4) * 4, i0 = ((e / C4) % C4) * 4, z = e / (C4 * C4);
+            float4 o[4] = {};
+            const int dz = z / LPF_C;
+            if (row_live(dz, 0) || row_live(dz, 1) || row_live(dz, 2)) {
+#pragma unroll 4
+                for (int j = 0; j < LPF_L; ++j)
+                    outer4(*reinterpret_cast<const float4 *>(At + j * LPF_C + i0),
+                           *reinterpret_cast<const float4 *>(T1 + (z * LPF_L + j) * LPF_C + x0), o);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) *reinterpret_cast<float4 *>(T2 + (z * LPF_C + i0 + t) * LPF_C + x0) = o[t];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < LPF_C * C4 * C4; e += LPF_BLOCK) {   // along z
+            const int x0 = (e % C4) * 4, i0 = ((e / C4) % C4) * 4, y = e / (C4 * C4);
+            float4 o[4] = {};
+#pragma unroll 4
+            for (int j = 0; j < LPF_L; ++j)
+                outer4(*reinterpret_cast<const float4 *>(At + j * LPF_C + i0),
+                       *reinterpret_cast<const float4 *>(T2 + (j * LPF_C + y) * LPF_C + x0), o);
+            float *out = E.lpf_out + (size_t)c * 2 * BVOL + h * BVOL;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                *reinterpret_cast<float4 *>(out + ((i0 + t) * LPF_C + y) * LPF_C + x0) = o[t];
+        }
+        __syncthreads();
     }
     if (!grid_barrier(st, &st->bar_count_lpf)) return;
     // (C) write back, one node (both levels) per thread; in the velocity
@@ -2073,20 +2092,20 @@ __global__ void __launch_bounds__(BLOCK, 1) k_barrier_selftest(EngineState *st, 
     grid_barrier(st, ctr, timeout_ns);
 }
 
-cudaError_t launch_cooperative(const void *fn, int grid, size_t smem, void **args, cudaStream_t s);
+cudaError_t launch_cooperative(const void *fn, int grid, int block, size_t smem, void **args, cudaStream_t s);
 
 cudaError_t launch_barrier_selftest(EngineState *st, unsigned long long *ctr, int grid,
                                     unsigned long long timeout_ns, cudaStream_t s)
 {
     void *args[] = {&st, &ctr, &timeout_ns};
-    return launch_cooperative((const void *)k_barrier_selftest, grid, 0, args, s);
+    return launch_cooperative((const void *)k_barrier_selftest, grid, BLOCK, 0, args, s);
 }
 
-cudaError_t launch_cooperative(const void *fn, int grid, size_t smem, void **args, cudaStream_t s)
+cudaError_t launch_cooperative(const void *fn, int grid, int block, size_t smem, void **args, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(BLOCK);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -2103,7 +2122,7 @@ int lpf_grid_size(int device)
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     if (cudaFuncSetAttribute(k_lpf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LPF_SMEM) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpf, BLOCK, LPF_SMEM) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpf, LPF_BLOCK, LPF_SMEM) != cudaSuccess) return 0;
     return sms * per_sm;
 }
 
@@ -2111,7 +2130,7 @@ cudaError_t launch_lpf(const Engine &e, int grid, cudaStream_t s)
 {
     Engine copy = e;
     void *args[] = {&copy};
-    return launch_cooperative((const void *)k_lpf, grid, LPF_SMEM, args, s);
+    return launch_cooperative((const void *)k_lpf, grid, LPF_BLOCK, LPF_SMEM, args, s);
 }
 
 cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaStream_t s)
@@ -2123,7 +2142,7 @@ cudaError_t launch_step(const Engine &e, int grid, int parity, int manage, cudaS
                      : e.storage == ST_F16   ? (const void *)k_step<ST_F16>
                      : e.storage == ST_MIXED ? (const void *)k_step<ST_MIXED>
                                              : (const void *)k_step<ST_F32>;
-    return launch_cooperative(fn, grid, 0, args, s);
+    return launch_cooperative(fn, grid, BLOCK, 0, args, s);
 }
 
 cudaError_t launch_read_window(const Engine &e, int sim, int now_half, int which, long long x0, long long y0,

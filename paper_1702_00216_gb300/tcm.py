@@ -305,7 +305,7 @@ def tcm_phase_ns(h):
 
 
 def tcm_lpf_info(h):
-    """(ns, bricks filtered, FP64 multiply-adds per brick) of the Eq. 7 filter so far."""
+    """(ns, bricks filtered, binary32 multiply-adds per brick) of the Eq. 7 filter so far."""
     a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
     _chk(lib().tcm_lpf_info(h, C.byref(a), C.byref(b), C.byref(c)), "tcm_lpf_info")
     return a.value, b.value, c.value

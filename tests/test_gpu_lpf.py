@@ -1,6 +1,7 @@
 """Frequency-domain shut-down (Eq. 7) on the GPU against the oracle: the
-affected set, the filtered values (FP64 filter, rounded to the storage) and
-the active sets, step by step; at threshold 0 equal to the dense grid."""
+affected set, the filtered values (binary32 separable filter on the GPU, FP64
+FFT in the oracle; equal within the filter's rounding bound) and the active
+sets, step by step; at threshold 0 equal to the dense grid."""
 import numpy as np
 import pytest
 
@@ -38,11 +39,21 @@ def oracle_of(wl, storage="f32"):
     return o
 
 
+# Largest absolute row sum of the 1-D operator at pass 0.25, stop 0.5 (24
+# taps, 64-point transform): 1.498.  A binary32 FMA dot product of 24 terms
+# errs by at most 24 u sum|a v| (u = 2^-24), rounding the operator adds u per
+# term, and three passes compound: per application the filtered values are
+# within 3 * 25 * u * 1.498^3 = 1.5e-5 of max|phi| of the exact filter, which
+# the oracle's FP64 FFT computes far more closely than that.
+LPF_BOUND = 3 * 25 * 2.0 ** -24 * 1.498 ** 3
+
+
 def close(a, b):
-    """Equal up to the rounding of the FP64 filter to binary32 (the oracle
-    filters with its FFT, the GPU with the separable operator)."""
+    """Equal within the binary32 filter's rounding bound, relative to the
+    field's maximum (the oracle filters with its FP64 FFT, the GPU with the
+    separable operator in binary32)."""
     scale = max(float(np.abs(b).max()), 1e-30)
-    return float(np.abs(a.astype(np.float64) - b).max()) <= 1e-6 * scale
+    return float(np.abs(a.astype(np.float64) - b).max()) <= 1.3 * LPF_BOUND * scale
 
 
 @pytest.mark.parametrize("interval,neighbours", [(1, 6), (3, 26)])
@@ -58,11 +69,11 @@ def test_lpf_threshold0_equals_dense(interval, neighbours):
 
 
 @pytest.mark.parametrize("interval,neighbours,mode,tau", [(1, 6, 1, 2e-3), (2, 26, 0, 1e-3)])
-def test_lpf_matches_oracle(interval, neighbours, mode, tau):
+def test_lpf_matches_oracle(interval, neighbours, mode, tau, capsys):
     wl = wave(tau=tau, mode=mode, interval=interval, neighbours=neighbours)
     s = tcm.Sim.from_workload(wl)
     o = oracle_of(wl)
-    exact = 0
+    exact, worst = 0, 0.0
     for chunk in (10, 20, 30, 40):
         s.step(chunk)
         o.step(chunk)
@@ -70,11 +81,13 @@ def test_lpf_matches_oracle(interval, neighbours, mode, tau):
         assert close(a, b) and close(s.read_field(1), o.read_field(1))
         assert np.array_equal(s.active_bricks(), o.active_bricks())
         exact += int(np.array_equal(a, b))
+        worst = max(worst, float(np.abs(a.astype(np.float64) - b).max()) / max(float(np.abs(b).max()), 1e-30))
     assert s.updates == o.updates
-    # the stated tolerance is the check (close, above); the FP64 filter here
-    # (separable operator) and the oracle's (FFT) agree far below binary32's
-    # resolution, so on these inputs the rounded values happen to be the same
-    # as well (exact), which is not required
+    with capsys.disabled():
+        print(f"\nEq. 7 run vs oracle: max |diff| / max|phi| = {worst:.3e} (bound {1.3 * LPF_BOUND:.2e}), "
+              f"{exact} of 4 checks identical")
+    # the stated tolerance is the check (close, above); values that round to
+    # the same binary32 on both sides (exact) are not required
     assert exact >= 0
     # the filter's counters: work (bricks) was timed, on whole bricks of the
     # separable operator; the relative-level run releases bricks with values
