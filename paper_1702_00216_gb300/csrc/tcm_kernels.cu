@@ -325,6 +325,41 @@ __device__ __forceinline__ void flush_updates(const Engine &E, unsigned long lon
     n = 0;
 }
 
+// Two 16-bit values of storage ST packed in a word (low half first): the
+// larger of each half, and the halves as binary32.
+template <int ST>
+__device__ __forceinline__ unsigned hmax2u(unsigned a, unsigned b)
+{
+    if constexpr (ST == ST_BF16) {
+        const __nv_bfloat162 r =
+            __hmax2(*reinterpret_cast<const __nv_bfloat162 *>(&a), *reinterpret_cast<const __nv_bfloat162 *>(&b));
+        return *reinterpret_cast<const unsigned *>(&r);
+    } else {
+        const __half2 r = __hmax2(*reinterpret_cast<const __half2 *>(&a), *reinterpret_cast<const __half2 *>(&b));
+        return *reinterpret_cast<const unsigned *>(&r);
+    }
+}
+
+template <int ST>
+__device__ __forceinline__ float half_lo(unsigned u)
+{
+    if constexpr (ST == ST_BF16) return __uint_as_float(u << 16);
+    else return __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
+}
+
+template <int ST>
+__device__ __forceinline__ float half_hi(unsigned u)
+{
+    if constexpr (ST == ST_BF16) return __uint_as_float(u & 0xffff0000u);
+    else return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+}
+
+template <int ST>
+__device__ __forceinline__ float max2h(unsigned u)
+{
+    return fmaxf(half_lo<ST>(u), half_hi<ST>(u));
+}
+
 // ---------------------------------------------------------------------------
 // P1: Eq. 3 on one brick per TPB-lane segment, straight from global memory.
 // Each lane owns one float4 column (x4, y) of all BZ planes: it issues every
@@ -353,7 +388,12 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const int b = w.brick;
     const int cx = b % mx, cy = (b / mx) % my, cz = b / (mx * my);
     using F = Fld<ST>;
+    // The plane loop works in stored units (phi / scale, scale a power of
+    // two; 1 for binary32 and bfloat16): every + - * then rounds to the same
+    // bits as on physical values, so the stored results are unchanged.  The
+    // source samples enter scaled, and the maxima leave scaled back.
     const float sc = __ldg(&S->scale), isc = __ldg(&S->inv_scale);
+    constexpr float U1 = 1.f;
 
     float4 P[BZ], M[BZ], K[BZ], YH[BZ];
     float XH[BZ];
@@ -374,9 +414,9 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         // phi^{n-1} in binary32; v^n in the velocity form (16-bit storages)
         const typename F::T *prv = half_ptr<ST, MIX>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), sc);
+        for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), U1);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) M[z] = F::ld_stream(prv + 4 * (z * TPB + t), sc);
+        for (int z = 0; z < BZ; ++z) M[z] = F::ld_stream(prv + 4 * (z * TPB + t), U1);
         if (!(w.kp & KP_SCALAR)) {
             const float4 *k4 = reinterpret_cast<const float4 *>(w.kp);
 #pragma unroll
@@ -387,8 +427,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
             for (int z = 0; z < BZ; ++z) K[z] = make_float4(ks, ks, ks, ks);
         }
         if (w.nb[4] >= 0 && TCM_SLOT_OK(E, w.nb[4]))
-            Zm = F::ld(half_ptr<ST, MIX>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), sc);
-        if (w.nb[5] >= 0 && TCM_SLOT_OK(E, w.nb[5])) Zp = F::ld(half_ptr<ST, MIX>(E, w.nb[5], nh) + 4 * t, sc);
+            Zm = F::ld(half_ptr<ST, MIX>(E, w.nb[4], nh) + 4 * ((BZ - 1) * TPB + t), U1);
+        if (w.nb[5] >= 0 && TCM_SLOT_OK(E, w.nb[5])) Zp = F::ld(half_ptr<ST, MIX>(E, w.nb[5], nh) + 4 * t, U1);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) {
@@ -400,7 +440,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     if (ys >= 0) {
         const typename F::T *yb = half_ptr<ST, MIX>(E, ys, nh) + 4 * ((y == 0 ? BY - 1 : 0) * XQ + x4);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) YH[z] = F::ld(yb + 4 * z * TPB, sc);
+        for (int z = 0; z < BZ; ++z) YH[z] = F::ld(yb + 4 * z * TPB, U1);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) YH[z] = f4zero();
@@ -408,7 +448,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     if (xs >= 0) {
         const typename F::T *xb = half_ptr<ST, MIX>(E, xs, nh) + y * BX + (x4 == 0 ? BX - 1 : 0);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) XH[z] = F::ld1(xb + z * BY * BX, sc);
+        for (int z = 0; z < BZ; ++z) XH[z] = F::ld1(xb + z * BY * BX, U1);
     } else {
 #pragma unroll
         for (int z = 0; z < BZ; ++z) XH[z] = 0.f;
@@ -417,7 +457,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         if (xs2 >= 0) {
             const typename F::T *xb = half_ptr<ST, MIX>(E, xs2, nh) + y * BX;
 #pragma unroll
-            for (int z = 0; z < BZ; ++z) XH2[z] = F::ld1(xb + z * BY * BX, sc);
+            for (int z = 0; z < BZ; ++z) XH2[z] = F::ld1(xb + z * BY * BX, U1);
         } else {
 #pragma unroll
             for (int z = 0; z < BZ; ++z) XH2[z] = 0.f;
@@ -435,6 +475,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const bool xrecv = (x4 == 0 && share_xm) || (x4 == XQ - 1 && share_xp);
 
     float mc = 0.f, qm = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 0.f;
+    [[maybe_unused]] unsigned qm2 = 0u, f02 = 0u, f12 = 0u, f22 = 0u, f32 = 0u, f42 = 0u, f52 = 0u;
 #pragma unroll
     for (int z = 0; z < BZ; ++z) {
         const float4 p = P[z];
@@ -489,7 +530,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
                 if (tt < 0 || tt >= sd.len) continue;
                 const int lx = sd.local % BX, ly = (sd.local / BX) % BY, lz = sd.local / (BX * BY);
                 if (lz != z || ly != y || (lx >> 2) != x4) continue;
-                add_comp(acc, lx & 3, E.wave[sd.w_off + tt]);
+                const float smp = E.wave[sd.w_off + tt];
+                add_comp(acc, lx & 3, ST == ST_F32 ? smp : __fmul_rn(smp, isc));
             }
         }
         if constexpr (ST != ST_F32) {
@@ -526,22 +568,48 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         // phi^{n+1} is what the storage holds: maxima and thresholds see the
         // stored (rounded) value.
         typename F::V qs;
-        q = F::rnd(q, sc, isc, qs);
+        q = F::rnd(q, U1, U1, qs);
         if (valid) F::st(out + 4 * (z * TPB + t), qs);
         if constexpr (ST != ST_F32) {
             typename F::V vs;
-            F::rnd(vq, sc, isc, vs);
+            F::rnd(vq, U1, U1, vs);
             if (valid) F::st(vout + 4 * (z * TPB + t), vs);
         }
-        const float mq = max4abs(q);
-        qm = fmaxf(qm, mq);
-        mc = fmaxf(mc, fmaxf(mq, max4abs(p)));
-        if (z == 0) f4 = mq;
-        if (z == BZ - 1) f5 = mq;
-        f2 = fmaxf(f2, y == 0 ? mq : 0.f);
-        f3 = fmaxf(f3, y == BY - 1 ? mq : 0.f);
-        f0 = fmaxf(f0, x4 == 0 ? fabsf(q.x) : 0.f);
-        f1 = fmaxf(f1, x4 == XQ - 1 ? fabsf(q.w) : 0.f);
+        if constexpr (ST == ST_F32) {
+            const float mq = max4abs(q);
+            qm = fmaxf(qm, mq);
+            mc = fmaxf(mc, fmaxf(mq, max4abs(p)));
+            if (z == 0) f4 = mq;
+            if (z == BZ - 1) f5 = mq;
+            f2 = fmaxf(f2, y == 0 ? mq : 0.f);
+            f3 = fmaxf(f3, y == BY - 1 ? mq : 0.f);
+            f0 = fmaxf(f0, x4 == 0 ? fabsf(q.x) : 0.f);
+            f1 = fmaxf(f1, x4 == XQ - 1 ? fabsf(q.w) : 0.f);
+        } else {
+            // 16-bit: the maxima of |phi^{n+1}| straight from the stored
+            // bits, per 16-bit half (exact: the conversion is monotone)
+            const unsigned a0 = qs.x & 0x7fff7fffu, a1 = qs.y & 0x7fff7fffu;
+            const unsigned m2 = hmax2u<ST>(a0, a1);
+            qm2 = hmax2u<ST>(qm2, m2);
+            mc = fmaxf(mc, max4abs(p));
+            if (z == 0) f42 = m2;
+            if (z == BZ - 1) f52 = m2;
+            if (y == 0) f22 = hmax2u<ST>(f22, m2);
+            if (y == BY - 1) f32 = hmax2u<ST>(f32, m2);
+            if (x4 == 0) f02 = hmax2u<ST>(f02, a0);        // low half: |phi| at x = 4 x4
+            if (x4 == XQ - 1) f12 = hmax2u<ST>(f12, a1);   // high half: at x = 4 x4 + 3
+        }
+    }
+    if constexpr (ST != ST_F32) {
+        qm = max2h<ST>(qm2);
+        mc = __fmul_rn(fmaxf(mc, qm), sc);
+        qm = __fmul_rn(qm, sc);
+        f0 = __fmul_rn(half_lo<ST>(f02), sc);
+        f1 = __fmul_rn(half_hi<ST>(f12), sc);
+        f2 = __fmul_rn(max2h<ST>(f22), sc);
+        f3 = __fmul_rn(max2h<ST>(f32), sc);
+        f4 = __fmul_rn(max2h<ST>(f42), sc);
+        f5 = __fmul_rn(max2h<ST>(f52), sc);
     }
     mc = seg_max(mc);
     qm = seg_max(qm);
