@@ -475,7 +475,7 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const bool xrecv = (x4 == 0 && share_xm) || (x4 == XQ - 1 && share_xp);
 
     float mc = 0.f, qm = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 0.f;
-    [[maybe_unused]] unsigned qm2 = 0u, f02 = 0u, f12 = 0u, f22 = 0u, f32 = 0u, f42 = 0u, f52 = 0u;
+    [[maybe_unused]] unsigned qm2 = 0u, f02 = 0u, f12 = 0u, f42 = 0u, f52 = 0u;
 #pragma unroll
     for (int z = 0; z < BZ; ++z) {
         const float4 p = P[z];
@@ -490,6 +490,16 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
             if constexpr (BRICKS_PER_WARP >= 2) recv = __shfl_xor_sync(FULL, share_xp ? p.w : p.x, TPB);
             xm0 = share_xm ? recv : XH[z];
             xp3 = share_xp ? recv : XH2[z];
+        } else if constexpr (XQ == 2) {
+            // the two columns of a row trade their touching values in one
+            // shuffle: x4 = 0 gets p.x of x4 = 1, x4 = 1 gets p.w of x4 = 0
+            const float nbr = __shfl_xor_sync(FULL, x4 == 0 ? p.w : p.x, 1);
+            float recv = 0.f;
+            if constexpr (BRICKS_PER_WARP >= 2)
+                recv = __shfl_xor_sync(FULL, (x4 == XQ - 1) ? p.w : p.x, TPB + XQ - 1);
+            const float xe = xrecv ? recv : XH[z];
+            xm0 = (x4 == 0) ? xe : nbr;
+            xp3 = (x4 == 0) ? nbr : xe;
         } else {
             const float lw = __shfl_up_sync(FULL, p.w, 1, TPB);
             const float rx = __shfl_down_sync(FULL, p.x, 1, TPB);
@@ -575,16 +585,17 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
             F::rnd(vq, U1, U1, vs);
             if (valid) F::st(vout + 4 * (z * TPB + t), vs);
         }
+        // per lane: the column maximum (qm) and the maxima of its x = 4 x4 and
+        // x = 4 x4 + 3 nodes (f0, f1) over the planes; the y faces are the
+        // column maxima of the y-edge lanes, so they are taken after the loop
         if constexpr (ST == ST_F32) {
             const float mq = max4abs(q);
             qm = fmaxf(qm, mq);
             mc = fmaxf(mc, fmaxf(mq, max4abs(p)));
             if (z == 0) f4 = mq;
             if (z == BZ - 1) f5 = mq;
-            f2 = fmaxf(f2, y == 0 ? mq : 0.f);
-            f3 = fmaxf(f3, y == BY - 1 ? mq : 0.f);
-            f0 = fmaxf(f0, x4 == 0 ? fabsf(q.x) : 0.f);
-            f1 = fmaxf(f1, x4 == XQ - 1 ? fabsf(q.w) : 0.f);
+            f0 = fmaxf(f0, fabsf(q.x));
+            f1 = fmaxf(f1, fabsf(q.w));
         } else {
             // 16-bit: the maxima of |phi^{n+1}| straight from the stored
             // bits, per 16-bit half (exact: the conversion is monotone)
@@ -594,10 +605,8 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
             mc = fmaxf(mc, max4abs(p));
             if (z == 0) f42 = m2;
             if (z == BZ - 1) f52 = m2;
-            if (y == 0) f22 = hmax2u<ST>(f22, m2);
-            if (y == BY - 1) f32 = hmax2u<ST>(f32, m2);
-            if (x4 == 0) f02 = hmax2u<ST>(f02, a0);        // low half: |phi| at x = 4 x4
-            if (x4 == XQ - 1) f12 = hmax2u<ST>(f12, a1);   // high half: at x = 4 x4 + 3
+            f02 = hmax2u<ST>(f02, a0);   // low half: |phi| at x = 4 x4
+            f12 = hmax2u<ST>(f12, a1);   // high half: at x = 4 x4 + 3
         }
     }
     if constexpr (ST != ST_F32) {
@@ -606,11 +615,13 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         qm = __fmul_rn(qm, sc);
         f0 = __fmul_rn(half_lo<ST>(f02), sc);
         f1 = __fmul_rn(half_hi<ST>(f12), sc);
-        f2 = __fmul_rn(max2h<ST>(f22), sc);
-        f3 = __fmul_rn(max2h<ST>(f32), sc);
         f4 = __fmul_rn(max2h<ST>(f42), sc);
         f5 = __fmul_rn(max2h<ST>(f52), sc);
     }
+    f2 = y == 0 ? qm : 0.f;
+    f3 = y == BY - 1 ? qm : 0.f;
+    f0 = x4 == 0 ? f0 : 0.f;
+    f1 = x4 == XQ - 1 ? f1 : 0.f;
     mc = seg_max(mc);
     qm = seg_max(qm);
     f0 = seg_max(f0);
