@@ -3,15 +3,19 @@
 Requests (workloads.Request: a simulation, its arrival time and its field
 storage) are admitted into a running batch as soon as they have arrived and
 the pool can take them.  Admission is by active footprint, not by grid size:
-a simulation only holds boxes for the cells its wave occupies, so the loop
-asks the library for an upper bound on the boxes the running simulations can
-claim during the next tick (tcm_batch_headroom) and admits a request when the
-free boxes cover that bound plus the request's own (its source cells and
-their neighbourhood within one tick's reach), and while the peak footprints
-of the running requests -- each the cells its wave can reach over its whole
-run at a little above the Courant speed, clipped to its grid: an estimate,
-not a bound -- fit the pool, so that running requests seldom have to wait
-for each other.  Before every tick the bound is
+a simulation only holds boxes for the cells its wave occupies, and that
+footprint grows with the simulation's step count while the requests admitted
+earlier run towards their end and free their boxes.  The loop estimates each
+request's footprint after s steps -- the cells within a little more than
+the distance the wave travels in s steps (the Courant number times s, times
+a margin) of a source, clipped to its grid: an estimate, not a bound -- and,
+since every running simulation advances the same steps per tick, the
+footprint of every running request at every future tick until it ends.  A
+request is admitted when, added to those, its own predicted footprint fits
+the pool at every future tick, and when the free boxes cover the upper bound
+the library gives on the boxes the running simulations can claim during the
+next tick (tcm_batch_headroom) plus the request's own (its source cells and
+their neighbourhood within one tick's reach).  Before every tick the bound is
 checked again; if the running simulations could claim more boxes than are
 free, the most recently admitted ones are paused (tcm_batch_pause: they keep
 their boxes and state and later continue unchanged) until it fits, and
@@ -82,8 +86,8 @@ class Server:
         """storage: the field storage of every request; storages: serve these
         storages side by side in one batch of mixed storage (requests carry
         their own).  admission: "footprint" (default) or "dense".  peak_margin:
-        factor over the Courant speed in the estimate of a request's peak
-        footprint (smaller admits more at once and pauses more)."""
+        factor over the Courant speed in the estimate of a request's footprint
+        (smaller admits more at once and pauses more)."""
         names = list(dict.fromkeys(storages)) if storages else [storage]
         self.mixed = len(names) > 1
         self.storages = names
@@ -107,7 +111,7 @@ class Server:
         self.running: Dict[int, _Running] = {}      # in admission order
         self.queue: collections.deque = collections.deque()
         self.bricks_used = 0          # brick-table space of the running requests
-        self.reserved_boxes = 0       # boxes reserved: grids (dense admission) or peak footprints
+        self.reserved_boxes = 0       # boxes reserved for whole grids (dense admission)
         self.restarts = collections.Counter()
         self.stats = {"max_concurrent": 0, "max_grid_bricks_running": 0, "pauses": 0, "resumes": 0,
                       "evictions": 0, "headroom_calls": 0}
@@ -142,22 +146,44 @@ class Server:
         return min(len(cells), self.bricks_of(wl))
 
     @staticmethod
-    def peak_footprint(wl, margin: float = 1.25) -> int:
-        """Cells a request's wave can reach over its whole run: those within
-        margin x (c_max dt / dx) x steps nodes of a source (values above the
-        level travel at the wave speed; the margin covers the dispersion of
-        Eq. 3 near the front), clipped to the grid."""
+    def footprint_at(wl, steps_done, margin: float = 1.25) -> np.ndarray:
+        """Estimated boxed cells of a request after each of `steps_done` steps:
+        the cells within margin x (c_max dt / dx) x steps nodes of a source
+        (values above the level travel at the wave speed; the margin covers
+        the dispersion of Eq. 3 near the front), counted over the bounding box
+        of that ball and clipped to the grid."""
         nz, ny, nx = wl.shape
         bx, by, bz = wl.brick
         courant = wl.media.c_max() * wl.dt / wl.dx
-        R = int(math.ceil(margin * courant * wl.steps)) + 1
-        total = 0
+        R = np.ceil(margin * courant * np.asarray(steps_done, np.float64)).astype(np.int64) + 1
+        total = np.zeros_like(R)
         for x, y, z, _ in wl.sources:
-            n = 1
+            n = np.ones_like(R)
             for c, size, b in ((x, nx, bx), (y, ny, by), (z, nz, bz)):
-                n *= min(size - 1, c + R) // b - max(0, c - R) // b + 1
-            total += n
-        return min(total, Server.bricks_of(wl))
+                n = n * (np.minimum(size - 1, c + R) // b - np.maximum(0, c - R) // b + 1)
+            total = total + n
+        return np.minimum(total, Server.bricks_of(wl))
+
+    @staticmethod
+    def peak_footprint(wl, margin: float = 1.25) -> int:
+        """The estimate after the request's last step."""
+        return int(Server.footprint_at(wl, [wl.steps], margin)[0])
+
+    def trajectory(self, wl, step_now: int) -> np.ndarray:
+        """Estimated boxed cells of a request at the end of each coming tick
+        (index 0: the next tick) until the tick in which it ends."""
+        rem = wl.steps - int(step_now)
+        n = -(-rem // self.steps_per_tick) if rem > 0 else 0
+        ends = np.minimum(int(step_now) + self.steps_per_tick * np.arange(1, n + 1), wl.steps)
+        return self.footprint_at(wl, ends, self.peak_margin)
+
+    def predicted_load(self) -> np.ndarray:
+        """Sum over the running requests of their trajectories."""
+        trajs = [self.trajectory(r.req.workload, r.sim.step_index) for r in self.running.values()]
+        out = np.zeros(max([len(t) for t in trajs] + [0]), np.int64)
+        for t in trajs:
+            out[:len(t)] += t
+        return out
 
     # ---- state ----------------------------------------------------------
     def now(self) -> float:
@@ -188,7 +214,7 @@ class Server:
         sim = self.batch.add(wl, n_steps=wl.steps, storage=storage)
         nb = self.bricks_of(wl)
         self.bricks_used += (nb + 31) // 32 * 32
-        reserve = nb if self.admission == "dense" else self.peak_footprint(wl, self.peak_margin)
+        reserve = nb if self.admission == "dense" else 0
         self.reserved_boxes += reserve
         self.running[req.rid] = _Running(req, sim, self.now(), nb, reserve=reserve)
         self.stats["max_concurrent"] = max(self.stats["max_concurrent"], len(self.running))
@@ -199,20 +225,30 @@ class Server:
     def _admit_arrived(self, time_scale: float) -> None:
         need = None
         free = None
+        load = None
         while self.queue and self.queue[0].arrival * time_scale <= self.now() and self._table_room(self.queue[0].workload):
             wl = self.queue[0].workload
             if self.admission == "dense":
                 if self.reserved_boxes + self.bricks_of(wl) > self.n_slots:
                     break
             else:
-                if self.running and self.reserved_boxes + self.peak_footprint(wl, self.peak_margin) > self.n_slots:
+                if any(r.paused for r in self.running.values()):
+                    break
+                if load is None:
+                    load = self.predicted_load()
+                traj = self.trajectory(wl, 0)
+                both = np.zeros(max(len(load), len(traj)), np.int64)
+                both[:len(load)] += load
+                both[:len(traj)] += traj
+                if self.running and len(both) and int(both.max()) > self.n_slots:
                     break
                 if need is None:
                     need, free = self.headroom(), self.free_boxes()
                 est = self.new_request_bound(wl)
-                if any(r.paused for r in self.running.values()) or free - need < est:
+                if free - need < est:
                     break
                 need += est
+                load = both
             self.admit(self.queue.popleft())
 
     def _fit(self) -> None:

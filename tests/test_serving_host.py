@@ -1,15 +1,20 @@
 """Host logic of the serving loop (admission by footprint or by grid,
 pausing, resuming, eviction, completion) with a fake batch in place of the
-GPU library.  The fake boxes cells the way a pulse does -- a few at the start,
-a bounded number more per step -- and fails loudly if the pool would run out,
-so a correct loop never trips it."""
+GPU library.  The fake boxes cells the way a pulse does -- the source cell at
+the start, then the cells the loop's own estimate at the default margin
+predicts for each step -- and fails loudly if the pool would run out, so a
+correct loop never trips it."""
 import numpy as np
 import pytest
 
 from paper_1702_00216_gb300 import serve
 from paper_1702_00216_gb300 import workloads as W
 
-GROWTH = 6          # cells a fake simulation boxes per step
+
+
+def grown(wl, steps):
+    """Cells a fake simulation has boxed after `steps` steps."""
+    return int(serve.Server.footprint_at(wl, [steps])[0])
 
 
 class FakeSim:
@@ -66,7 +71,7 @@ class FakeBatch:
 
     def headroom(self, steps):
         self._start()
-        return sum(min(s.nb - s.boxed, GROWTH * steps) for s in self.sims if s.live())
+        return sum(max(0, grown(s.wl, s.step_index + steps) - s.boxed) for s in self.sims if s.live())
 
     def add(self, wl, n_steps=0, dense=False, storage=None):
         s = FakeSim(wl, self)
@@ -91,7 +96,7 @@ class FakeBatch:
                 if s.live():
                     s.step_index += 1
                     s.updates += s.boxed * 512
-                    s.boxed = min(s.nb, s.boxed + GROWTH)
+                    s.boxed = max(s.boxed, grown(s.wl, s.step_index))
             if self.used() > self.slots:
                 raise RuntimeError("pool exhausted in the middle of a step")
 
@@ -255,3 +260,28 @@ def test_peak_estimates_keep_the_loop_from_thrashing(fake):
     res = srv.run(reqs, time_scale=1.0, virtual=True)
     check_done(srv, res, reqs)
     assert srv.stats["pauses"] == 0 and srv.stats["evictions"] == 0, srv.stats
+
+
+def test_long_requests_are_staggered_beyond_dense_admission(fake):
+    """A burst of identical requests whose waves end up filling their grids
+    (216 cells each) in a pool of 600 boxes: dense admission runs two at a
+    time; admission by predicted footprint starts a third while the first two
+    are still running, because it stays small until they end (and the 125
+    cells within its first tick's reach are free)."""
+    def req(i):
+        wl = W.Workload(f"long{i}", (48, 48, 48), W.homogeneous(1.0), 1.0, 0.5, [(24, 24, 24, W.ricker(1 / 8, 0.5))],
+                        120)
+        return W.Request(i, 0.0, wl, "f32")
+    assert serve.Server.peak_footprint(req(0).workload) == 216
+    peaks = {}
+    for adm in ("dense", "footprint"):
+        srv = serve.Server(pool_bytes=600 * 4096, max_bricks=1 << 16, max_sims=16, steps_per_tick=6,
+                           admission=adm)
+        reqs = [req(i) for i in range(8)]
+        res = srv.run(reqs, time_scale=1.0, virtual=True)
+        check_done(srv, res, reqs)
+        peaks[adm] = srv.stats["max_concurrent"]
+        if adm == "footprint":
+            assert srv.stats["pauses"] == 0 and srv.stats["evictions"] == 0, srv.stats
+    assert peaks["dense"] == 2
+    assert peaks["footprint"] >= 3, peaks
