@@ -686,8 +686,8 @@ def serving_leg(torch, W, args, local_rank):
             r.workload.decay_alpha, r.workload.decay_steps = 0.8, 20
         return reqs
 
-    def serve_once(reqs, time_scale, admission):
-        srv = serve.Server(pool_bytes=pool, max_bricks=24 * 1024 ** 2, max_sims=512, steps_per_tick=16,
+    def serve_once(reqs, time_scale, admission, pool_bytes=pool):
+        srv = serve.Server(pool_bytes=pool_bytes, max_bricks=24 * 1024 ** 2, max_sims=512, steps_per_tick=16,
                            device=local_rank, storages=("f32", "bf16"), admission=admission)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -704,6 +704,14 @@ def serving_leg(torch, W, args, local_rank):
     _, wall_d, stats_d = serve_once(burst, 0.0, "dense")
     dense = {"wall_s": wall_d, "max_concurrent": stats_d["max_concurrent"],
              "max_grid_bricks_running": stats_d["max_grid_bricks_running"]}
+    # the same burst in a 1 GiB pool (the smallest that holds a whole 512^3
+    # grid), where the pool rather than the GPU limits how many run at once
+    small = {}
+    for adm in ("footprint", "dense"):
+        _, wall_s, st_s = serve_once(burst, 0.0, adm, pool_bytes=1024 ** 3)
+        small[adm] = {"wall_s": wall_s, "max_concurrent": st_s["max_concurrent"],
+                      "max_grid_bricks_running": st_s["max_grid_bricks_running"], "pauses": st_s["pauses"],
+                      "evictions": st_s["evictions"], "pool_boxes": st_s["pool_boxes"]}
     rate = 0.75 * capacity
     reqs = stream(rate)[n_cal:]
     t0 = reqs[0].arrival
@@ -716,7 +724,7 @@ def serving_leg(torch, W, args, local_rank):
                           f"arrivals at 75 % of the calibrated capacity ({rate:.2f}/s), FP32/BF16 mix in one "
                           f"batch of mixed storage, admission by active footprint, 2 GiB pool",
                 "rate_hz": rate, "steps_per_tick": 16, "calibration": cal,
-                "dense_admission_burst": dense})
+                "dense_admission_burst": dense, "burst_in_1gib_pool": small})
     torch.cuda.empty_cache()
     return out
 
