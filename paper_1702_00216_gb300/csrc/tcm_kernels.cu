@@ -35,25 +35,11 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 4000000000ull;  // 4 s
 
-
-
 __device__ __forceinline__ unsigned long long globaltimer()
 {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Device-wide barrier for a cooperative launch: one arrival per block on a
@@ -149,11 +135,6 @@ __device__ __forceinline__ float4 eq3v(float4 p, float4 pm, float4 k, float xm0,
     q.z = eq3(p.z, pm.z, k.z, p.y, p.w, ym.z, yp.z, zm.z, zp.z);
     q.w = eq3(p.w, pm.w, k.w, p.z, xp3, ym.w, yp.w, zm.w, zp.w);
     return q;
-}
-
-__device__ __forceinline__ float comp(const float4 &v, int j)
-{
-    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
 }
 
 __device__ __forceinline__ void add_comp(float4 &v, int j, float w)
