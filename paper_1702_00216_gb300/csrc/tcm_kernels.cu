@@ -21,6 +21,7 @@
 //       block prefix scan), in brick order, for the next launch.
 // Arithmetic: binary32, every + - * an explicit round-to-nearest intrinsic
 // (no FMA contraction), no flush-to-zero.
+#include <cmath>
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
 
@@ -1418,10 +1419,25 @@ __global__ void __launch_bounds__(BLOCK, 1) k_compact(Engine E, int parity)
 // ---------------------------------------------------------------------------
 // Heterogenic Bulking (create time)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float k_of_c(float c, double dt, double dx)
+// Eq. 3 coefficient (c dt / dx)^2: the product and the quotient in FP64,
+// squared, rounded to binary32.  idx = 1 / dx when dx is a power of two
+// (0 otherwise): the quotient is then an exact scaling and is taken as a
+// product, unless it would fall below the normal range -- the same bits
+// without the FP64 division, which is slow on this part.
+__device__ __forceinline__ float k_of_c(float c, double dt, double dx, double idx)
 {
-    const double r = (double)c * dt / dx;
+    const double q = (double)c * dt;
+    double r = q * idx;
+    if (idx == 0.0 || (r != 0.0 && fabs(r) < 2.2250738585072014e-308)) r = q / dx;
     return (float)(r * r);
+}
+
+// 1 / dx when dx is a power of two, else 0 (see k_of_c).
+double exact_inverse(double dx)
+{
+    int e = 0;
+    const double m = std::frexp(dx, &e);   // dx = m 2^e, m in [0.5, 1)
+    return (m == 0.5 && e > -1000 && e < 1000) ? std::ldexp(1.0, 1 - e) : 0.0;
 }
 
 __device__ float media_c(const MediaDev &M, int nx, int ny, long long i, long long j, long long l)
@@ -1472,7 +1488,8 @@ __device__ bool rules_uniform(const MediaDev &M, long long x0, long long x1, lon
 }
 
 __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
-                                double dx, long long bb, float *kscal, int *kslab_of_brick, int *n_kslabs)
+                                double dx, double idx, long long bb, float *kscal, int *kslab_of_brick,
+                                int *n_kslabs)
 {
     const long long nb = (long long)mx * my * mz;
     const int lane = threadIdx.x & 31;
@@ -1482,14 +1499,14 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
         const long long x0 = cx * BX, y0 = cy * BY, z0 = cz * BZ;
         const long long x1 = min(x0 + BX, (long long)nx) - 1, y1 = min(y0 + BY, (long long)ny) - 1,
                         z1 = min(z0 + BZ, (long long)nz) - 1;
-        const float k0 = k_of_c(media_c(M, nx, ny, x0, y0, z0), dt, dx);
+        const float k0 = k_of_c(media_c(M, nx, ny, x0, y0, z0), dt, dx, idx);
         bool uniform = M.kind == MEDIA_RULES && rules_uniform(M, x0, x1, y0, y1, z0, z1);
         bool diff = false;
         if (!uniform) {
             for (int e = lane; e < BVOL; e += 32) {
                 const long long gx = x0 + e % BX, gy = y0 + (e / BX) % BY, gz = z0 + e / (BX * BY);
                 if (gx > x1 || gy > y1 || gz > z1) continue;
-                const float k = k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx);
+                const float k = k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, idx);
                 if (__float_as_uint(k) != __float_as_uint(k0)) diff = true;
             }
             diff = __any_sync(FULL, diff);
@@ -1507,7 +1524,7 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
 }
 
 __global__ void k_bulk_fill(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
-                            double dx, long long bb, const int *kslab_of_brick, float *kslabs)
+                            double dx, double idx, long long bb, const int *kslab_of_brick, float *kslabs)
 {
     const long long nb = (long long)mx * my * mz;
     const int lane = threadIdx.x & 31;
@@ -1519,7 +1536,7 @@ __global__ void k_bulk_fill(MediaDev M, int nx, int ny, int nz, int mx, int my, 
         for (int e = lane; e < BVOL; e += 32) {
             const long long gx = cx * BX + e % BX, gy = cy * BY + (e / BX) % BY, gz = cz * BZ + e / (BX * BY);
             float k = 0.f;
-            if (gx < nx && gy < ny && gz < nz) k = k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx);
+            if (gx < nx && gy < ny && gz < nz) k = k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, idx);
             kslabs[(size_t)ks * BVOL + e] = k;
         }
     }
@@ -1819,8 +1836,8 @@ cudaError_t launch_bulk_classify(const MediaDev &m, int nx, int ny, int nz, int 
                                  int *n_kslabs, cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_classify<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, bb, kscal,
-                                                           kslab_of_brick, n_kslabs);
+    k_bulk_classify<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_inverse(dx), bb,
+                                                           kscal, kslab_of_brick, n_kslabs);
     return cudaGetLastError();
 }
 
@@ -1829,7 +1846,7 @@ cudaError_t launch_bulk_fill(const MediaDev &m, int nx, int ny, int nz, int mx, 
                              cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_fill<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, bb,
+    k_bulk_fill<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_inverse(dx), bb,
                                                        kslab_of_brick, kslabs);
     return cudaGetLastError();
 }

@@ -93,14 +93,17 @@ def test_heterogeneous_ragged_multisource(shape):
         assert_same(g, o)
 
 
-def test_rules_media_bulking_matches_oracle():
+@pytest.mark.parametrize("dx", [1.0, 0.25, 0.75])
+def test_rules_media_bulking_matches_oracle(dx):
     """Heterogenic Bulking: the GPU's per-brick classification and scalar k
-    equal the oracle's for layers cutting bricks and a sphere."""
+    equal the oracle's for layers cutting bricks and a sphere; node spacings
+    that are powers of two (the quotient c dt / dx taken as an exact product)
+    and one that is not (a division)."""
     shape = (40, 48, 56)
     media = W.Media(kind="rules", c_background=1.0, layers=[(12.0, 1.5), (29.5, 2.0)],
                     spheres=[(27.3, 20.0, 21.0, 9.5, 0.7), (8.0, 8.0, 8.0, 8.0, 2.2)])
-    dt = 0.5 / media.c_max()
-    wl = W.Workload("rules", shape, media, 1.0, dt, [(20, 24, 18, W.ricker(1 / 8, dt))], 80)
+    dt = 0.5 * dx / media.c_max()
+    wl = W.Workload("rules", shape, media, dx, dt, [(20, 24, 18, W.ricker(1 / 8, dt / dx))], 80)
     g, o = pair(wl)
     nb = g.mx * g.my * g.mz
     kinds = set()
@@ -113,6 +116,20 @@ def test_rules_media_bulking_matches_oracle():
     assert kinds == {1, 2}
     g.step(80)
     o.step(80)
+    assert_same(g, o)
+
+
+@pytest.mark.parametrize("dx", [0.5, 0.75])
+def test_dense_media_node_spacing_matches_oracle(dx):
+    """Per-node k from a dense velocity array (every brick bulked) with node
+    spacings of both kinds: 50 steps bit-exact against the oracle."""
+    shape = (24, 20, 28)
+    media = W.random_dense_media(shape, 5, 1.0, 2.0)
+    dt = 0.5 * dx / media.c_max()
+    wl = W.Workload("dx", shape, media, dx, dt, [(9, 10, 12, W.ricker(1 / 8, dt / dx))], 50)
+    g, o = pair(wl)
+    g.step(50)
+    o.step(50)
     assert_same(g, o)
 
 
