@@ -1503,13 +1503,16 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
         bool uniform = M.kind == MEDIA_RULES && rules_uniform(M, x0, x1, y0, y1, z0, z1);
         bool diff = false;
         if (!uniform) {
-            for (int e = lane; e < BVOL; e += 32) {
+            // 32 nodes per round; the first round that finds a k different
+            // from the corner's decides (the warp leaves together)
+            for (int e0 = 0; e0 < BVOL && !diff; e0 += 32) {
+                const int e = e0 + lane;
                 const long long gx = x0 + e % BX, gy = y0 + (e / BX) % BY, gz = z0 + e / (BX * BY);
-                if (gx > x1 || gy > y1 || gz > z1) continue;
-                const float k = k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, idx);
-                if (__float_as_uint(k) != __float_as_uint(k0)) diff = true;
+                bool d = false;
+                if (e < BVOL && gx <= x1 && gy <= y1 && gz <= z1)
+                    d = __float_as_uint(k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, idx)) != __float_as_uint(k0);
+                diff = __any_sync(FULL, d);
             }
-            diff = __any_sync(FULL, diff);
         }
         if (lane == 0) {
             if (diff) {
@@ -1533,11 +1536,22 @@ __global__ void k_bulk_fill(MediaDev M, int nx, int ny, int nz, int mx, int my, 
         const int ks = kslab_of_brick[bb + g];
         if (ks < 0) continue;
         const long long cx = g % mx, cy = (g / mx) % my, cz = g / ((long long)mx * my);
-        for (int e = lane; e < BVOL; e += 32) {
+        // every c of the lane first (independent loads in flight), then k
+        constexpr int PER = (BVOL + 31) / 32;
+        float c[PER];
+        unsigned in = 0u;   // bit j: node lane + 32 j lies in the grid
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int e = lane + 32 * j;
             const long long gx = cx * BX + e % BX, gy = cy * BY + (e / BX) % BY, gz = cz * BZ + e / (BX * BY);
-            float k = 0.f;
-            if (gx < nx && gy < ny && gz < nz) k = k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, idx);
-            kslabs[(size_t)ks * BVOL + e] = k;
+            const bool ok = e < BVOL && gx < nx && gy < ny && gz < nz;
+            c[j] = ok ? media_c(M, nx, ny, gx, gy, gz) : 0.f;
+            in |= (ok ? 1u : 0u) << j;
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int e = lane + 32 * j;
+            if (e < BVOL) kslabs[(size_t)ks * BVOL + e] = (in >> j & 1u) ? k_of_c(c[j], dt, dx, idx) : 0.f;
         }
     }
 }
