@@ -208,7 +208,12 @@ tcm_status tcm_sync(tcm_sim *sim);
 
 /* Copy a window of phi^n (which = 0) or phi^{n-1} (which = 1) into host_out
  * (wx*wy*wz floats, x fastest).  Zeros where a brick is inactive or the window
- * leaves the domain.  The _device variant writes device memory on the stream. */
+ * leaves the domain.  The _device variant writes device memory on the stream.
+ * Page-locked host memory the device can address is written directly by the
+ * device; other host memory goes through a device staging buffer that the
+ * batch keeps (grown to the largest window read so far, freed with the
+ * batch), as do the small buffers of tcm_active_count, tcm_active_bricks and
+ * tcm_energy: these calls allocate device memory only when their need grows. */
 tcm_status tcm_read_field(const tcm_sim *sim, int which, int64_t x0, int64_t y0, int64_t z0,
                           int64_t wx, int64_t wy, int64_t wz, float *host_out);
 tcm_status tcm_read_field_device(const tcm_sim *sim, int which, int64_t x0, int64_t y0,

@@ -102,6 +102,9 @@ struct tcm_batch {
     // scratch of tcm_batch_headroom (allocated by its first call)
     unsigned char *reach_a = nullptr, *reach_b = nullptr;
     unsigned long long *reach_count = nullptr;
+    // device scratch of the read and count calls (grown as needed, kept)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
 };
 
 namespace {
@@ -153,6 +156,31 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// Device scratch of at least `bytes` for a read or count call: one buffer per
+// batch, grown when a call needs more (the old one freed after the batch's
+// stream has drained) and kept until the batch is destroyed, so that the
+// calls neither allocate nor free (and so synchronise the device) each time.
+tcm_status scratch(tcm_batch *b, size_t bytes, void **out)
+{
+    bytes = std::max<size_t>(bytes, 256);
+    if (b->scratch_bytes < bytes) {
+        if (b->scratch) {
+            cudaStreamSynchronize(b->stream);
+            cudaFree(b->scratch);
+            b->scratch = nullptr;
+            b->scratch_bytes = 0;
+        }
+        if (cudaMalloc(&b->scratch, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b->scratch = nullptr;
+            return TCM_ENOMEM;
+        }
+        b->scratch_bytes = bytes;
+    }
+    *out = b->scratch;
+    return TCM_OK;
+}
 
 tcm_status poison(tcm_batch *b, tcm_status s)
 {
@@ -1288,18 +1316,24 @@ tcm_status tcm_read_field(const tcm_sim *cs, int which, int64_t x0, int64_t y0, 
     if (n == 0) return TCM_OK;
     tcm_batch *b = cs->b;
     DeviceGuard g(b->device);
-    float *d = nullptr;
-    if (cudaMalloc(&d, n * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        return TCM_ENOMEM;
+    // page-locked host memory the device can address: the gather kernel
+    // writes it directly
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, host_out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer) {
+        tcm_status st = tcm_read_field_device(cs, which, x0, y0, z0, wx, wy, wz, static_cast<float *>(pa.devicePointer));
+        if (st == TCM_OK) st = dev_err(cudaStreamSynchronize(b->stream));
+        return st;
     }
-    tcm_status st = tcm_read_field_device(cs, which, x0, y0, z0, wx, wy, wz, d);
+    cudaGetLastError();
+    void *d = nullptr;
+    TRYS(scratch(b, (size_t)n * sizeof(float), &d));
+    tcm_status st = tcm_read_field_device(cs, which, x0, y0, z0, wx, wy, wz, static_cast<float *>(d));
     if (st == TCM_OK) {
         cudaError_t e = cudaMemcpyAsync(host_out, d, n * sizeof(float), cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         st = dev_err(e);
     }
-    cudaFree(d);
     return st;
 }
 
@@ -1310,14 +1344,14 @@ tcm_status tcm_active_count(const tcm_sim *cs, int64_t *bricks, int64_t *cells)
     tcm_batch *b = cs->b;
     DeviceGuard g(b->device);
     TRYS(ready_for_read(b, cs->id));
-    unsigned long long *d = nullptr;
-    TRY(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    void *sp = nullptr;
+    TRYS(scratch(b, 2 * sizeof(unsigned long long), &sp));
+    unsigned long long *d = static_cast<unsigned long long *>(sp);
     unsigned long long hc[2] = {0, 0};
     cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), b->stream);
     if (e == cudaSuccess) e = launch_active_bricks(b->E, cs->id, b->list_parity, nullptr, d, d + 1, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hc, d, sizeof(hc), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    cudaFree(d);
     TRY(e);
     if (bricks) *bricks = (int64_t)hc[0];
     if (cells) *cells = (int64_t)hc[1];
@@ -1332,20 +1366,18 @@ tcm_status tcm_active_bricks(const tcm_sim *cs, int64_t *ids, int64_t cap, int64
     DeviceGuard g(b->device);
     TRYS(ready_for_read(b, cs->id));
     const long long upper = h->n_bricks;
-    long long *d = nullptr;
-    unsigned long long *dn = nullptr;
-    TRY(cudaMalloc(&d, std::max<long long>(upper, 1) * sizeof(long long)));
-    cudaError_t e = cudaMalloc(&dn, sizeof(unsigned long long));
+    void *sp = nullptr;
+    TRYS(scratch(b, (size_t)(std::max<long long>(upper, 1) + 1) * sizeof(long long), &sp));
+    unsigned long long *dn = static_cast<unsigned long long *>(sp);   // the count, then the ids
+    long long *d = static_cast<long long *>(sp) + 1;
     unsigned long long hn = 0;
-    if (e == cudaSuccess) e = cudaMemsetAsync(dn, 0, sizeof(unsigned long long), b->stream);
+    cudaError_t e = cudaMemsetAsync(dn, 0, sizeof(unsigned long long), b->stream);
     if (e == cudaSuccess) e = launch_active_bricks(b->E, cs->id, b->list_parity, d, dn, nullptr, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hn, dn, sizeof(hn), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     std::vector<long long> hv((size_t)hn);
     if (e == cudaSuccess && hn > 0)
         e = cudaMemcpy(hv.data(), d, hn * sizeof(long long), cudaMemcpyDeviceToHost);
-    cudaFree(d);
-    if (dn) cudaFree(dn);
     TRY(e);
     std::sort(hv.begin(), hv.end());
     if (n) *n = (int64_t)hn;
@@ -1373,14 +1405,14 @@ tcm_status tcm_energy(const tcm_sim *cs, double *e_out)
     tcm_batch *b = cs->b;
     DeviceGuard g(b->device);
     TRYS(ready_for_read(b, cs->id));
-    double *d = nullptr;
-    TRY(cudaMalloc(&d, sizeof(double)));
+    void *sp = nullptr;
+    TRYS(scratch(b, sizeof(double), &sp));
+    double *d = static_cast<double *>(sp);
     double hv = 0.0;
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double), b->stream);
     if (e == cudaSuccess) e = launch_energy(b->E, cs->id, (int)(h->step & 1), b->list_parity, d, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hv, d, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    cudaFree(d);
     TRY(e);
     *e_out = hv;
     return TCM_OK;
@@ -1662,6 +1694,7 @@ void tcm_batch_destroy(tcm_batch *b)
     if (b->d_wave) cudaFree(b->d_wave);
     if (b->own_pool && b->pool) cudaFree(b->pool);
     if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->scratch) cudaFree(b->scratch);
     delete b;
 }
 
