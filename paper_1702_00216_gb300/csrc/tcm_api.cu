@@ -282,13 +282,36 @@ void range_free(tcm_batch *b, long long base, long long len)
     b->free_ranges.swap(merged);
 }
 
-// Largest value of c[0..n) and whether any is negative, NaN or infinite;
-// branch-free, so the compiler can vectorise it.
+// Largest value of c[0..n) and whether any is negative, NaN or infinite, in
+// four-wide vectors (GCC vector extensions: SIMD on any host) with eight
+// independent running maxima; the comparisons are IEEE ones, so a NaN fails
+// x >= 0 and is flagged, and a maximum does not depend on the order it is
+// taken in.
 void scan_c(const float *c, long long n, float *cmax, bool *bad)
 {
+    typedef float v4f __attribute__((vector_size(16)));
+    typedef int v4i __attribute__((vector_size(16)));
+    const v4f zero = {0.f, 0.f, 0.f, 0.f};
+    const v4f inf = {INFINITY, INFINITY, INFINITY, INFINITY};
+    v4f m0 = zero, m1 = zero;
+    v4i f = {0, 0, 0, 0};
+    long long i = 0;
+    for (; i + 8 <= n; i += 8) {
+        v4f a, b;
+        std::memcpy(&a, c + i, sizeof(a));
+        std::memcpy(&b, c + i + 4, sizeof(b));
+        m0 = a > m0 ? a : m0;
+        m1 = b > m1 ? b : m1;
+        f |= ~(a >= zero) | (a == inf) | ~(b >= zero) | (b == inf);
+    }
     float m = 0.f;
     unsigned flag = 0;
-    for (long long i = 0; i < n; ++i) {
+    for (int k = 0; k < 4; ++k) {
+        m = m0[k] > m ? m0[k] : m;
+        m = m1[k] > m ? m1[k] : m;
+        flag |= f[k] != 0;
+    }
+    for (; i < n; ++i) {
         const float x = c[i];
         m = x > m ? x : m;
         flag |= (unsigned)!(x >= 0.f) | (unsigned)(x == INFINITY);
@@ -512,10 +535,20 @@ tcm_status bulk_sim(tcm_batch *b, HostSim &h, const tcm_velocity_model *velocity
     bool ok = tmp_alloc((void **)&d_cnt, sizeof(int));
     const size_t n_nodes = (size_t)(h.nx * h.ny * h.nz);
     if (ok && md.kind == MEDIA_DENSE) {
-        float *d_c = nullptr;
-        ok = tmp_alloc((void **)&d_c, n_nodes * sizeof(float)) &&
-             cudaMemcpyAsync(d_c, velocity->c, n_nodes * sizeof(float), cudaMemcpyHostToDevice, q) == cudaSuccess;
-        md.c = d_c;
+        // page-locked host memory the device can address is read in place by
+        // the bulking kernels; other memory is copied to the device first
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, velocity->c) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            md.c = static_cast<const float *>(pa.devicePointer);
+        } else {
+            cudaGetLastError();
+            float *d_c = nullptr;
+            ok = tmp_alloc((void **)&d_c, n_nodes * sizeof(float)) &&
+                 cudaMemcpyAsync(d_c, velocity->c, n_nodes * sizeof(float), cudaMemcpyHostToDevice, q) ==
+                     cudaSuccess;
+            md.c = d_c;
+        }
     } else if (ok) {
         double *d_lz = nullptr, *d_sph = nullptr;
         float *d_lc = nullptr, *d_sc = nullptr;

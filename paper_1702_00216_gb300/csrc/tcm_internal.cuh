@@ -194,7 +194,7 @@ struct Engine {
 
 struct MediaDev {
     int kind;
-    const float *c;        // dense, device
+    const float *c;        // dense: device memory, or page-locked host memory the device addresses
     float c_bg;
     int n_layers;
     const double *layer_z;

@@ -101,6 +101,22 @@ def test_dense_model_scan_split_over_threads(lib, where):
         flat[where] = 1.0
 
 
+@pytest.mark.parametrize("where", [0, 3, 7, 1_000_003, 107 * 103 * 101 - 1])
+def test_dense_model_scan_any_lane_and_the_tail(lib, where):
+    """The scan keeps eight running maxima: a bad value or a too-fast node in
+    any of them, or in the last nodes of a count that is not a multiple of
+    eight, is still found."""
+    shape = (101, 103, 107)
+    c = np.full(shape, 1.0, np.float32)
+    flat = c.reshape(-1)
+    for value, expect in ((np.nan, tcm.TCM_EINVAL), (-0.5, tcm.TCM_EINVAL), (1.2, tcm.TCM_ECFL)):
+        flat[where] = value
+        with pytest.raises(tcm.TCMError) as e:
+            tcm.tcm_create(shape, W.dense_media(c), 1.0, 0.5, 0.0, (8, 8, 8), _opts())
+        assert e.value.status == expect, (value, where)
+        flat[where] = 1.0
+
+
 @pytest.mark.parametrize("bad", ["shape", "dx", "dt", "thr", "brick", "decay", "mode", "cneg",
                                  "pool"])
 def test_create_rejects_bad_arguments(lib, bad):
