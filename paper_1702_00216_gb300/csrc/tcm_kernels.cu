@@ -1420,24 +1420,25 @@ __global__ void __launch_bounds__(BLOCK, 1) k_compact(Engine E, int parity)
 // Heterogenic Bulking (create time)
 // ---------------------------------------------------------------------------
 // Eq. 3 coefficient (c dt / dx)^2: the product and the quotient in FP64,
-// squared, rounded to binary32.  idx = 1 / dx when dx is a power of two
-// (0 otherwise): the quotient is then an exact scaling and is taken as a
-// product, unless it would fall below the normal range -- the same bits
-// without the FP64 division, which is slow on this part.
-__device__ __forceinline__ float k_of_c(float c, double dt, double dx, double idx)
+// squared, rounded to binary32.  dts = dt / dx when dx is a power of two and
+// dt / dx is at least 2^-100 (0 otherwise): then (c dt) / dx is an exact
+// scaling of c dt that stays in the normal range for every binary32 c, and it
+// equals c (dt / dx) rounded once -- the same bits with one FP64 product
+// instead of a product and a division (FP64 is slow on this part).
+__device__ __forceinline__ float k_of_c(float c, double dt, double dx, double dts)
 {
-    const double q = (double)c * dt;
-    double r = q * idx;
-    if (idx == 0.0 || (r != 0.0 && fabs(r) < 2.2250738585072014e-308)) r = q / dx;
+    const double r = dts != 0.0 ? (double)c * dts : (double)c * dt / dx;
     return (float)(r * r);
 }
 
-// 1 / dx when dx is a power of two, else 0 (see k_of_c).
-double exact_inverse(double dx)
+// dt / dx for k_of_c when that shortcut is exact, else 0.
+double exact_ratio(double dt, double dx)
 {
     int e = 0;
     const double m = std::frexp(dx, &e);   // dx = m 2^e, m in [0.5, 1)
-    return (m == 0.5 && e > -1000 && e < 1000) ? std::ldexp(1.0, 1 - e) : 0.0;
+    if (m != 0.5 || e <= -1000 || e >= 1000) return 0.0;
+    const double r = dt * std::ldexp(1.0, 1 - e);   // exact: a power-of-two scaling
+    return (std::isfinite(r) && r >= std::ldexp(1.0, -100)) ? r : 0.0;
 }
 
 __device__ float media_c(const MediaDev &M, int nx, int ny, long long i, long long j, long long l)
@@ -1488,7 +1489,7 @@ __device__ bool rules_uniform(const MediaDev &M, long long x0, long long x1, lon
 }
 
 __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
-                                double dx, double idx, long long bb, float *kscal, int *kslab_of_brick,
+                                double dx, double dts, long long bb, float *kscal, int *kslab_of_brick,
                                 int *n_kslabs)
 {
     const long long nb = (long long)mx * my * mz;
@@ -1499,7 +1500,7 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
         const long long x0 = cx * BX, y0 = cy * BY, z0 = cz * BZ;
         const long long x1 = min(x0 + BX, (long long)nx) - 1, y1 = min(y0 + BY, (long long)ny) - 1,
                         z1 = min(z0 + BZ, (long long)nz) - 1;
-        const float k0 = k_of_c(media_c(M, nx, ny, x0, y0, z0), dt, dx, idx);
+        const float k0 = k_of_c(media_c(M, nx, ny, x0, y0, z0), dt, dx, dts);
         bool uniform = M.kind == MEDIA_RULES && rules_uniform(M, x0, x1, y0, y1, z0, z1);
         bool diff = false;
         if (!uniform) {
@@ -1510,7 +1511,7 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
                 const long long gx = x0 + e % BX, gy = y0 + (e / BX) % BY, gz = z0 + e / (BX * BY);
                 bool d = false;
                 if (e < BVOL && gx <= x1 && gy <= y1 && gz <= z1)
-                    d = __float_as_uint(k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, idx)) != __float_as_uint(k0);
+                    d = __float_as_uint(k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, dts)) != __float_as_uint(k0);
                 diff = __any_sync(FULL, d);
             }
         }
@@ -1527,7 +1528,7 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
 }
 
 __global__ void k_bulk_fill(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
-                            double dx, double idx, long long bb, const int *kslab_of_brick, float *kslabs)
+                            double dx, double dts, long long bb, const int *kslab_of_brick, float *kslabs)
 {
     const long long nb = (long long)mx * my * mz;
     const int lane = threadIdx.x & 31;
@@ -1551,7 +1552,7 @@ __global__ void k_bulk_fill(MediaDev M, int nx, int ny, int nz, int mx, int my, 
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const int e = lane + 32 * j;
-            if (e < BVOL) kslabs[(size_t)ks * BVOL + e] = (in >> j & 1u) ? k_of_c(c[j], dt, dx, idx) : 0.f;
+            if (e < BVOL) kslabs[(size_t)ks * BVOL + e] = (in >> j & 1u) ? k_of_c(c[j], dt, dx, dts) : 0.f;
         }
     }
 }
@@ -1850,7 +1851,7 @@ cudaError_t launch_bulk_classify(const MediaDev &m, int nx, int ny, int nz, int 
                                  int *n_kslabs, cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_classify<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_inverse(dx), bb,
+    k_bulk_classify<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_ratio(dt, dx), bb,
                                                            kscal, kslab_of_brick, n_kslabs);
     return cudaGetLastError();
 }
@@ -1860,7 +1861,7 @@ cudaError_t launch_bulk_fill(const MediaDev &m, int nx, int ny, int nz, int mx, 
                              cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_fill<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_inverse(dx), bb,
+    k_bulk_fill<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_ratio(dt, dx), bb,
                                                        kslab_of_brick, kslabs);
     return cudaGetLastError();
 }
