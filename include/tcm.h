@@ -118,8 +118,9 @@ typedef struct {
                            brick pair it asks L2 for the next pair's field arrays and
                            per-node k (bricks with per-node k only).  Same results
                            either way */
-    int cta_warps;      /* warps per CTA of the step kernel: 0 or 8 (every brick shape),
-                           4 or 16 (8x8x8 only); same results, different blocking
+    int cta_warps;      /* warps per CTA of the step kernel: 8 (every brick shape), 4 or
+                           12 (8x8x8 only); 0: 8, except 12 for 8x8x8 bricks with a
+                           16-bit storage.  Same results, different blocking
                            (TCM_EINVAL otherwise) */
 } tcm_options;
 

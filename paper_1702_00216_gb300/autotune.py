@@ -6,9 +6,10 @@ probe window untimed, then the window timed with CUDA events on the
 library's stream.  Candidates:
 
   brick shapes     4x4x4, 8x8x8, 16x8x8 (one build of the library each)
-  CTA blocking     with allow_blocking, the 8x8x8 shape also with 4 and 16
-                   warps per CTA of the step kernel (8 is the default of every
-                   shape; separate builds; same results)
+  CTA blocking     with allow_blocking, the 8x8x8 shape also with 4 and 12
+                   warps per CTA of the step kernel (separate builds; same
+                   results; 8 is the default of every shape, 12 of 8x8x8
+                   bricks with a 16-bit storage)
   schedules        update every step with face neighbours (always); with
                    allow_schedule, also the Eq. 5 interval with the 26
                    neighbour set
@@ -34,7 +35,12 @@ from . import tcm
 
 BRICKS: Tuple[Tuple[int, int, int], ...] = ((4, 4, 4), (8, 8, 8), (16, 8, 8))
 # warps per CTA of the step kernel available per brick shape (8: the default)
-BLOCKINGS = {(8, 8, 8): (4, 16)}
+BLOCKINGS = {(8, 8, 8): (4, 8, 12)}
+
+
+def default_warps(brick, storage="f32") -> int:
+    """Warps per CTA the library takes for cta_warps = 0."""
+    return 12 if tuple(brick) == (8, 8, 8) and storage in ("bf16", "f16") else 8
 _CACHE: Dict[tuple, dict] = {}
 
 
@@ -48,7 +54,7 @@ class Candidate:
 
     def label(self) -> str:
         b = "x".join(map(str, self.brick))
-        if self.cta_warps not in (0, 8):
+        if self.cta_warps:
             b = f"{b}/w{self.cta_warps}"
         b = b if (self.interval, self.neighbours) == (1, 6) else f"{b}/eq5-26"
         return b if self.prefetch else f"{b}/no-prefetch"
@@ -60,10 +66,14 @@ class Candidate:
 
 
 def candidates(allow_schedule: bool = False, bricks: Sequence = BRICKS,
-               allow_blocking: bool = False) -> List[Candidate]:
+               allow_blocking: bool = False, storage: str = "f32") -> List[Candidate]:
+    """The default configuration of every shape; with allow_blocking the
+    shape's other blockings (labelled /w<warps>); with allow_schedule the
+    Eq. 5 / 26-neighbour schedule."""
     out = [Candidate(tuple(b)) for b in bricks]
     if allow_blocking:
-        out += [Candidate(tuple(b), cta_warps=w) for b in bricks for w in BLOCKINGS.get(tuple(b), ())]
+        out += [Candidate(tuple(b), cta_warps=w) for b in bricks for w in BLOCKINGS.get(tuple(b), ())
+                if w != default_warps(b, storage)]
     if allow_schedule:
         out += [Candidate(tuple(b), 0, 26) for b in bricks]
     return out
@@ -98,7 +108,8 @@ def measure(wl, c: Candidate, start: int, count: int, device: int = 0, storage="
         ms = e0.elapsed_time(e1)
         upd = s.updates - u0
         out = {"config": c.label(), "brick": list(c.brick), "schedule": [c.interval, c.neighbours],
-               "prefetch": c.prefetch, "cta_warps": c.cta_warps or 8, "window_ms": ms, "cell_updates": upd,
+               "prefetch": c.prefetch, "cta_warps": c.cta_warps or default_warps(c.brick, storage),
+               "window_ms": ms, "cell_updates": upd,
                "updates_per_s": upd / (ms / 1e3) if ms > 0 else 0.0}
         if ref is not None:
             buf = torch.empty(wl.shape, dtype=torch.float32, device=ref.device)
@@ -158,7 +169,7 @@ def autotune(wl, start: Optional[int] = None, count: Optional[int] = None, allow
                 r["bit_identical_to"] = base.label() if bool((f == fields[base.label()]).all().item()) else None
         table.append(r)
 
-    for c in candidates(allow_schedule, bricks, allow_blocking):
+    for c in candidates(allow_schedule, bricks, allow_blocking, storage):
         run(c)
     if allow_prefetch:
         fastest = min(table, key=lambda r: r["window_ms"])["candidate"]

@@ -43,7 +43,7 @@ DEPS = UNITS + ["tcm_internal.cuh", DISPATCH]
 # every shape; the 8x8x8 shape also has 4- and 16-warp builds for the
 # autotuner.
 SHAPES = [(4, 4, 4, 8, "b444"), (8, 8, 8, 8, "b888"), (16, 8, 8, 8, "b1688"),
-          (8, 8, 8, 4, "b888w4"), (8, 8, 8, 16, "b888w16")]
+          (8, 8, 8, 4, "b888w4"), (8, 8, 8, 12, "b888w12")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-ftz=false", "-prec-div=true",
          "-prec-sqrt=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -29,7 +29,7 @@ struct tcm_batch {
     extern "C" ret tcm_b888_##name params;   \
     extern "C" ret tcm_b1688_##name params;  \
     extern "C" ret tcm_b888w4_##name params; \
-    extern "C" ret tcm_b888w16_##name params;
+    extern "C" ret tcm_b888w12_##name params;
 
 DECL3(tcm_status, slot_bytes, (tcm_brick, int, size_t *))
 DECL3(tcm_status, create, (const tcm_domain *, const tcm_velocity_model *, double, double, double, tcm_brick,
@@ -76,23 +76,27 @@ DECL3(tcm_status, batch_headroom, (void *, int64_t, int64_t *))
 DECL3(tcm_status, lpf_info, (const void *, int64_t *, int64_t *, int64_t *))
 
 // Call the build of `shape` (0 4x4x4, 1 8x8x8, 2 16x8x8, 3 8x8x8 with 4 warps
-// per CTA, 4 8x8x8 with 16 warps per CTA).
+// per CTA, 4 8x8x8 with 12 warps per CTA).
 #define SHAPE_CALL(shape, name, ...)                                                           \
     ((shape) == 0   ? tcm_b444_##name(__VA_ARGS__)                                              \
      : (shape) == 1 ? tcm_b888_##name(__VA_ARGS__)                                              \
      : (shape) == 2 ? tcm_b1688_##name(__VA_ARGS__)                                             \
      : (shape) == 3 ? tcm_b888w4_##name(__VA_ARGS__)                                            \
-                    : tcm_b888w16_##name(__VA_ARGS__))
+                    : tcm_b888w12_##name(__VA_ARGS__))
 
 namespace {
 
 // Build index of a brick shape and CTA blocking (warps per CTA of the step
-// kernel, 0 = the default 8), -1 if unsupported.
-int shape_of(tcm_brick b, int warps = 0)
+// kernel), -1 if unsupported.  warps = 0 takes the default: 8, except 12 for
+// 8x8x8 bricks with a 16-bit storage (measured fastest for those: the 16-bit
+// time stepping is bound by instruction issue, and 12 warps keep more of it
+// in flight).
+int shape_of(tcm_brick b, int warps = 0, int storage = TCM_STORAGE_F32)
 {
-    if (warps == 0) warps = 8;
+    const bool cube8 = b.bx == 8 && b.by == 8 && b.bz == 8;
+    if (warps == 0) warps = cube8 && (storage == TCM_STORAGE_BF16 || storage == TCM_STORAGE_F16) ? 12 : 8;
     if (b.bx == 4 && b.by == 4 && b.bz == 4) return warps == 8 ? 0 : -1;
-    if (b.bx == 8 && b.by == 8 && b.bz == 8) return warps == 8 ? 1 : warps == 4 ? 3 : warps == 16 ? 4 : -1;
+    if (cube8) return warps == 8 ? 1 : warps == 4 ? 3 : warps == 12 ? 4 : -1;
     if (b.bx == 16 && b.by == 8 && b.bz == 8) return warps == 8 ? 2 : -1;
     return -1;
 }
@@ -144,7 +148,7 @@ tcm_status tcm_create(const tcm_domain *domain, const tcm_velocity_model *veloci
     if (!out) return TCM_EINVAL;
     *out = nullptr;
     if (!options) return TCM_EINVAL;
-    const int sh = shape_of(brick, options->cta_warps);
+    const int sh = shape_of(brick, options->cta_warps, options->storage);
     if (sh < 0) return TCM_EINVAL;
     void *impl = nullptr;
     const tcm_status st = SHAPE_CALL(sh, create, domain, velocity, dx, dt, threshold, brick, options, &impl);
@@ -305,7 +309,7 @@ tcm_status tcm_batch_create(const tcm_batch_options *o, tcm_batch **out)
     if (!o) return TCM_EINVAL;
     tcm_brick br = o->brick;
     if (br.bx == 0 && br.by == 0 && br.bz == 0) br = tcm_brick{8, 8, 8};
-    const int sh = shape_of(br, o->cta_warps);
+    const int sh = shape_of(br, o->cta_warps, o->storage);
     if (sh < 0) return TCM_EINVAL;
     void *impl = nullptr;
     const tcm_status st = SHAPE_CALL(sh, batch_create, o, &impl);

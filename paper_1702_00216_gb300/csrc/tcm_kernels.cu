@@ -377,7 +377,13 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
     const float sc = __ldg(&S->scale), isc = __ldg(&S->inv_scale);
     constexpr float U1 = 1.f;
 
+    // binary32 columns in P, M, YH; with more than 8 warps per CTA (at most
+    // 170 registers a thread) 16-bit columns stay as loaded (two registers
+    // per plane instead of four) in PR, MR, YR and are converted where the
+    // plane loop uses them, phi^n once per plane
+    constexpr bool RAW = ST != ST_F32 && P1_WARPS > 8;   // only where registers are tight
     float4 P[BZ], M[BZ], K[BZ], YH[BZ];
+    [[maybe_unused]] uint2 PR[BZ], MR[BZ], YR[BZ];
     float XH[BZ];
     float XH2[XQ == 1 ? BZ : 1];
     float4 Zm = f4zero(), Zp = f4zero();
@@ -395,10 +401,17 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         const typename F::T *now = half_ptr<ST, MIX>(E, w.slot, nh);
         // phi^{n-1} in binary32; v^n in the velocity form (16-bit storages)
         const typename F::T *prv = half_ptr<ST, MIX>(E, w.slot, ST == ST_F32 ? (nh ^ 1) : V_HALF);
+        if constexpr (RAW) {
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), U1);
+            for (int z = 0; z < BZ; ++z) PR[z] = __ldg(reinterpret_cast<const uint2 *>(now + 4 * (z * TPB + t)));
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) M[z] = F::ld_stream(prv + 4 * (z * TPB + t), U1);
+            for (int z = 0; z < BZ; ++z) MR[z] = __ldcs(reinterpret_cast<const uint2 *>(prv + 4 * (z * TPB + t)));
+        } else {
+#pragma unroll
+            for (int z = 0; z < BZ; ++z) P[z] = F::ld(now + 4 * (z * TPB + t), U1);
+#pragma unroll
+            for (int z = 0; z < BZ; ++z) M[z] = F::ld_stream(prv + 4 * (z * TPB + t), U1);
+        }
         if (!(w.kp & KP_SCALAR)) {
             const float4 *k4 = reinterpret_cast<const float4 *>(w.kp);
 #pragma unroll
@@ -417,15 +430,22 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
             P[z] = f4zero();
             M[z] = f4zero();
             K[z] = f4zero();
+            if constexpr (RAW) PR[z] = MR[z] = make_uint2(0u, 0u);
         }
     }
     if (ys >= 0) {
         const typename F::T *yb = half_ptr<ST, MIX>(E, ys, nh) + 4 * ((y == 0 ? BY - 1 : 0) * XQ + x4);
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) YH[z] = F::ld(yb + 4 * z * TPB, U1);
+        for (int z = 0; z < BZ; ++z) {
+            if constexpr (RAW) YR[z] = __ldg(reinterpret_cast<const uint2 *>(yb + 4 * z * TPB));
+            else YH[z] = F::ld(yb + 4 * z * TPB, U1);
+        }
     } else {
 #pragma unroll
-        for (int z = 0; z < BZ; ++z) YH[z] = f4zero();
+        for (int z = 0; z < BZ; ++z) {
+            YH[z] = f4zero();
+            if constexpr (RAW) YR[z] = make_uint2(0u, 0u);
+        }
     }
     if (xs >= 0) {
         const typename F::T *xb = half_ptr<ST, MIX>(E, xs, nh) + y * BX + (x4 == 0 ? BX - 1 : 0);
@@ -458,9 +478,23 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
 
     float mc = 0.f, qm = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 0.f;
     [[maybe_unused]] unsigned qm2 = 0u, f02 = 0u, f12 = 0u, f42 = 0u, f52 = 0u;
+    // 16-bit: phi^n of the plane below, this plane and the plane above
+    [[maybe_unused]] float4 pprev = Zm, pcur = f4zero();
+    if constexpr (RAW) pcur = F::cvt(PR[0], U1);
 #pragma unroll
     for (int z = 0; z < BZ; ++z) {
-        const float4 p = P[z];
+        float4 p, zm, zp;
+        if constexpr (RAW) {
+            p = pcur;
+            zm = pprev;
+            zp = (z < BZ - 1) ? F::cvt(PR[z < BZ - 1 ? z + 1 : 0], U1) : Zp;
+            pprev = pcur;
+            pcur = zp;
+        } else {
+            p = P[z];
+            zm = (z > 0) ? P[z > 0 ? z - 1 : 0] : Zm;
+            zp = (z < BZ - 1) ? P[z < BZ - 1 ? z + 1 : 0] : Zp;
+        }
         // x neighbours inside the brick through shuffles; the edge value from
         // the loaded face column or, within a pair, from lane ^ 17 (the x = 7
         // column of the first brick / the x = 0 column of the second)
@@ -502,15 +536,18 @@ __device__ __forceinline__ void p1_brick(const Engine &E, const WorkItem &w, boo
         yp.y = __shfl_down_sync(FULL, p.y, XQ, TPB);
         yp.z = __shfl_down_sync(FULL, p.z, XQ, TPB);
         yp.w = __shfl_down_sync(FULL, p.w, XQ, TPB);
-        if (y == 0) ym = YH[z];
-        if (y == BY - 1) yp = YH[z];
-        const float4 zm = (z > 0) ? P[z > 0 ? z - 1 : 0] : Zm;
-        const float4 zp = (z < BZ - 1) ? P[z < BZ - 1 ? z + 1 : 0] : Zp;
+        if constexpr (RAW) {
+            if (y == 0) ym = F::cvt(YR[z], U1);
+            if (y == BY - 1) yp = F::cvt(YR[z], U1);
+        } else {
+            if (y == 0) ym = YH[z];
+            if (y == BY - 1) yp = YH[z];
+        }
         // binary32: q = phi^{n+1} by Eq. 3.  Velocity form: vq = v + k lap
         // (+ source), then q = phi^n + vq.
         float4 q, vq;
         if constexpr (ST == ST_F32) q = eq3v(p, M[z], K[z], xm0, xp3, ym, yp, zm, zp);
-        else vq = vel3v(p, M[z], K[z], xm0, xp3, ym, yp, zm, zp);
+        else vq = vel3v(p, RAW ? F::cvt(MR[z], U1) : M[z], K[z], xm0, xp3, ym, yp, zm, zp);
         float4 &acc = (ST == ST_F32) ? q : vq;
         if (src) {
             // Source insertion in box coordinates: every sample of this
@@ -1346,8 +1383,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
     {
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
-        // Eight items per thread at a time, so their loads overlap.
-        constexpr int U = 8;
+        // Eight items per thread at a time, so their loads overlap (four with
+        // more than 8 warps per CTA, whose threads have fewer registers).
+        constexpr int U = P1_WARPS > 8 ? 4 : 8;
         SimCache sc;
         for (int base = gtid; base < nact; base += U * nthr) {
             WorkItem w[U];

@@ -160,7 +160,7 @@ def test_precision_workload_error_against_fp64_dense(capsys):
     # every configuration the autotuner can choose for it (brick shape and
     # CTA blocking; the blocking cannot change a result, the shape can)
     tuned = {}
-    for brick, warps in (((4, 4, 4), 0), ((16, 8, 8), 0), ((8, 8, 8), 4), ((8, 8, 8), 16)):
+    for brick, warps in (((4, 4, 4), 0), ((16, 8, 8), 0), ((8, 8, 8), 4), ((8, 8, 8), 8), ((8, 8, 8), 12)):
         w2 = dataclasses.replace(wl, brick=brick, cta_warps=warps)
         for st in ("f32", "bf16", "f16"):
             s = tcm.Sim.from_workload(w2, storage=st)
@@ -172,7 +172,7 @@ def test_precision_workload_error_against_fp64_dense(capsys):
         print("\nprecision 256^3 x 800 vs FP64 dense (max rel, rms rel):",
               {k_: tuple(float(f"{v:.3e}") for v in e) for k_, e in errs.items()})
         print("other autotuner configurations:",
-              {f"{'x'.join(map(str, b))}/w{w or 8}/{st}": tuple(float(f"{v:.3e}") for v in e)
+              {f"{'x'.join(map(str, b))}/w{w or 'default'}/{st}": tuple(float(f"{v:.3e}") for v in e)
                for (b, w, st), e in tuned.items()})
     for (b, w, st), e in tuned.items():
         if b == (8, 8, 8):

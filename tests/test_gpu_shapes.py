@@ -136,12 +136,13 @@ def test_set_field_16x8x8():
     s.close()
 
 
-@pytest.mark.parametrize("warps", [4, 16])
+@pytest.mark.parametrize("warps", [4, 8, 12])
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_cta_blocking_builds_equal_the_oracle(warps, storage):
-    """The 8x8x8 builds with 4 and 16 warps per CTA of the step kernel (the
-    autotuner's blocking axis) give the oracle's fields, active sets and
-    updates bit for bit, at a level above 0 with shut-down, in a single
+    """The 8x8x8 builds with 4, 8 and 12 warps per CTA of the step kernel
+    (the autotuner's blocking axis; 12 holds the 16-bit columns as loaded and
+    takes 4 update items per thread) give the oracle's fields, active sets
+    and updates bit for bit, at a level above 0 with shut-down, in a single
     simulation and in a batch."""
     wl = het((8, 8, 8), thr_mode=1, tau=1e-4, alpha=0.7, decay=4)
     s = tcm.Sim.from_workload(wl, cta_warps=warps, storage=storage)
@@ -163,4 +164,7 @@ def test_cta_blocking_rejects_unbuilt_combinations():
     wl = het((4, 4, 4))
     with pytest.raises(tcm.TCMError) as e:
         tcm.Sim.from_workload(wl, cta_warps=16)
+    assert e.value.status == tcm.TCM_EINVAL
+    with pytest.raises(tcm.TCMError) as e:
+        tcm.Sim.from_workload(het((8, 8, 8)), cta_warps=16)
     assert e.value.status == tcm.TCM_EINVAL
