@@ -270,7 +270,7 @@ tcm_status tcm_pool_info(const tcm_sim *sim, int64_t *slots, int64_t *free_slots
 
 /* Cumulative device time (ns, from the GPU's global timer) of the three
  * phases of every step so far: time stepping (Eq. 3 on the active bricks),
- * updating active cells (trigger/keep/release/claim), and box recycling plus
+ * the update procedure (trigger/keep/release/claim), and box recycling plus
  * compaction of the active list -- the per-operation split the paper reports
  * for its step (Results, Fig. 11). */
 tcm_status tcm_phase_ns(const tcm_sim *sim, int64_t *stepping, int64_t *update, int64_t *compaction);

@@ -1170,7 +1170,7 @@ __device__ __noinline__ void p2_item_general(const Engine &E, const WorkItem w, 
     if (n > 0) claim_bricks<6>(E, sim, S, nbs, n);
 }
 
-// Updating active cells for one active brick (item w, its own maxima
+// The update procedure (Simulation section, Fig. 3a) for one active brick (item w, its own maxima
 // r0/r1): keep / shut down / release it, and trigger its neighbours across
 // faces above the level (Fig. 3a).  Most bricks are above the level, not
 // shutting down and have no face above it towards an unboxed neighbour:
@@ -1379,7 +1379,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
     if (!grid_barrier(st, &st->bar_count)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t_p1 = globaltimer();
 
-    // ---- P2: updating active cells ---------------------------------------
+    // ---- P2: the update procedure ---------------------------------------
     {
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
