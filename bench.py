@@ -167,9 +167,15 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources' code: comments and blank space are left
+    out, so a change of wording does not mark the recorded counters stale."""
+    import re
     h = hashlib.sha256()
     for f in ("tcm_kernels.cu", "tcm_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1702_00216_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1702_00216_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
