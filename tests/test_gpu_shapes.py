@@ -168,3 +168,27 @@ def test_cta_blocking_rejects_unbuilt_combinations():
     with pytest.raises(tcm.TCMError) as e:
         tcm.Sim.from_workload(het((8, 8, 8)), cta_warps=16)
     assert e.value.status == tcm.TCM_EINVAL
+
+
+@pytest.mark.parametrize("warps", [4, 8, 12])
+def test_mixed_storage_batch_in_every_blocking(warps):
+    """A batch of mixed storage (FP32, BF16 and FP16 simulations stepped by
+    one launch) in each CTA blocking of the 8x8x8 shape -- with 12 warps the
+    16-bit bricks take the path that holds their columns as loaded -- equals
+    the oracle in each simulation's storage form, bit for bit."""
+    wls = [het((8, 8, 8), thr_mode=1, tau=1e-4, alpha=0.7, decay=4),
+           het((8, 8, 8), thr_mode=1, tau=1e-4, alpha=0.7, decay=4, shape=(21, 30, 17)),
+           het((8, 8, 8), shape=(26, 19, 33))]
+    storages = ["bf16", "f32", "f16"]
+    b = tcm.Batch(pool_bytes=6000 * tcm.tcm_slot_bytes(), max_bricks=1 << 15, max_sims=4, cta_warps=warps,
+                  storage="mixed")
+    sims = [b.add(w, storage=st) for w, st in zip(wls, storages)]
+    b.step(45)
+    for sm, w, st in zip(sims, wls, storages):
+        o = oracle_of(w, st)
+        o.step(45)
+        assert np.array_equal(sm.read_field(0), o.read_field(0)), (warps, st)
+        assert np.array_equal(sm.read_field(1), o.read_field(1)), (warps, st)
+        assert np.array_equal(sm.active_bricks(), o.active_bricks())
+        assert sm.updates == o.updates
+    b.close()
