@@ -856,48 +856,61 @@ __device__ __forceinline__ void item_sim(const Engine &E, int si, ItemSim &c)
     c.kslabs = __ldg(reinterpret_cast<const unsigned long long *>(&S->kslabs));
 }
 
-// Work items of up to IB bricks g[0..n) (global ids) at once: every load of
-// all of them is issued before any is used.  An item holds the brick's box,
-// the boxes of its six face neighbours, its coefficient address (or scalar
-// k), its sim and shut-down word, and the half that holds phi^n when the
-// next launch steps it.
+// Brick g's local id b, its box and the boxes of its six face neighbours,
+// addressed with the geometry of sim q.  Every address stays inside q's
+// bricks even when g belongs to another sim (the caller then redoes it).
+__device__ __forceinline__ void item_geom(const Engine &E, long long g, const ItemSim &q, int &b, int &slot,
+                                          int (&nb)[6])
+{
+    b = (int)(g - q.bb);
+    const int cx = b % q.mx, cy = (b / q.mx) % q.my, cz = b / (q.mx * q.my);
+    // a brick outside its sim's grid (never listed) gets no box
+    slot = (b >= 0 && cz < q.mz && TCM_BRICK_OK(E, g)) ? __ldcg(E.slot_of_brick + g) : -1;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+        const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
+        const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
+        nb[f] = (ax >= 0 && ay >= 0 && az >= 0 && ax < q.mx && ay < q.my && az < q.mz)
+                    ? __ldcg(E.slot_of_brick + q.bb + ((long long)az * q.my + ay) * q.mx + ax)
+                    : -3;
+    }
+}
+
+// Work items of up to IB bricks g[0..n) (global ids) at once.  An item
+// holds the brick's box, the boxes of its six face neighbours, its
+// coefficient address (or scalar k), its sim and shut-down word, and the
+// half that holds phi^n when the next launch steps it.  All loads of all
+// the items are issued together: the neighbour boxes are addressed with the
+// geometry of the sim cached in c (a block's sims change rarely), and an
+// item whose sim turns out to be another is redone with its own.
 constexpr int IB = 4;
 
 __device__ __forceinline__ void build_items(const Engine &E, const long long (&g)[IB], int n, WorkItem *const (&out)[IB],
                                             int step_ahead, ItemSim &c)
 {
-    int si[IB];
-#pragma unroll
-    for (int k = 0; k < IB; ++k) si[k] = k < n ? (int)__ldg(E.sim_of_word + (g[k] >> 5)) : 0;
-    int b[IB], slot[IB], kslab[IB], nb[IB][6];
+    int si[IB], b[IB], slot[IB], kslab[IB], nb[IB][6];
     float kscal[IB];
     unsigned sd[IB];
+    const ItemSim c0 = c;
+#pragma unroll
+    for (int k = 0; k < IB; ++k) {
+        if (k >= n) continue;
+        si[k] = (int)__ldg(E.sim_of_word + (g[k] >> 5));
+        kslab[k] = __ldg(E.kslab_of_brick + g[k]);
+        kscal[k] = __ldg(E.kscal + g[k]);
+        sd[k] = __ldcg(E.sd_of_brick + g[k]);
+        item_geom(E, g[k], c0, b[k], slot[k], nb[k]);
+    }
     ItemSim ck[IB];
 #pragma unroll
     for (int k = 0; k < IB; ++k) {
         if (k >= n) continue;
-        item_sim(E, si[k], c);
-        ck[k] = c;
-    }
-#pragma unroll
-    for (int k = 0; k < IB; ++k) {
-        if (k >= n) continue;
-        const ItemSim &q = ck[k];
-        b[k] = (int)(g[k] - q.bb);
-        const int cx = b[k] % q.mx, cy = (b[k] / q.mx) % q.my, cz = b[k] / (q.mx * q.my);
-        // a brick outside its sim's grid (never listed) gets no box
-        slot[k] = (b[k] >= 0 && cz < q.mz && TCM_BRICK_OK(E, g[k])) ? __ldcg(E.slot_of_brick + g[k]) : -1;
-        kslab[k] = __ldg(E.kslab_of_brick + g[k]);
-        kscal[k] = __ldg(E.kscal + g[k]);
-        sd[k] = __ldcg(E.sd_of_brick + g[k]);
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const int ax = cx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
-            const int ay = cy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
-            const int az = cz + (f == 4 ? -1 : (f == 5 ? 1 : 0));
-            nb[k][f] = (ax >= 0 && ay >= 0 && az >= 0 && ax < q.mx && ay < q.my && az < q.mz)
-                           ? __ldcg(E.slot_of_brick + q.bb + ((long long)az * q.my + ay) * q.mx + ax)
-                           : -3;
+        ck[k] = c0;
+        if (si[k] != c0.sim) {
+            item_sim(E, si[k], c);
+            ck[k] = c;
+            item_geom(E, g[k], c, b[k], slot[k], nb[k]);
         }
     }
 #pragma unroll
@@ -921,29 +934,40 @@ __device__ __forceinline__ void build_items(const Engine &E, const long long (&g
 // per-range counts (blocktot, kept by the update procedure) of the blocks
 // before it.  The brick ids of the range (popc + block scan) go to shared
 // memory when they fit, else to the global listids, and the block then
-// builds the items from there, IB per thread at a time.
+// builds the items from there, IB per thread at a time.  The loads that
+// depend on nothing (the range's first words, the counts, the range's first
+// sim) are issued before the caller's own work, mid(), runs.
 constexpr int SMEM_IDS = 4096;
 
-__device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int step_ahead)
+template <class Mid>
+__device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int step_ahead, Mid &&mid)
 {
     __shared__ int s_ids[SMEM_IDS];
-    long long before = 0, all = 0;
-    for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) {
+    const int G = (int)gridDim.x;
+    const long long w0 = (long long)blockIdx.x * E.words_per_block;
+    const long long w1 = min(w0 + E.words_per_block, E.n_words);
+    const long long wf = w0 + threadIdx.x;
+    const unsigned bits0 = wf < w1 ? __ldcg(E.bitmap + wf) : 0u;
+    const int v0 = (int)threadIdx.x < G ? __ldcg(E.blocktot + threadIdx.x) : 0;
+    const int mine = __ldcg(E.blocktot + blockIdx.x);
+    const int s0 = w0 < w1 ? (int)__ldg(E.sim_of_word + w0) : -1;
+    mid();
+    ItemSim c;
+    if (s0 >= 0) item_sim(E, s0, c);
+    long long before = (int)threadIdx.x < (int)blockIdx.x ? v0 : 0, all = v0;
+    for (int j = threadIdx.x + BLOCK; j < G; j += BLOCK) {
         const int v = __ldcg(E.blocktot + j);
         all += v;
         if (j < (int)blockIdx.x) before += v;
     }
-    const int mine = __ldcg(E.blocktot + blockIdx.x);
     block_sum2(before, all);
     const bool local = mine <= SMEM_IDS;
     int *ids = local ? s_ids : E.listids + before;
     const int cap = local ? SMEM_IDS : (int)max(0ll, (long long)E.n_slots - before);
-    const long long w0 = (long long)blockIdx.x * E.words_per_block;
-    const long long w1 = min(w0 + E.words_per_block, E.n_words);
     int off = 0;
     for (long long wb = w0; wb < w1; wb += BLOCK) {
         const long long w = wb + threadIdx.x;
-        unsigned bits = w < w1 ? __ldcg(E.bitmap + w) : 0u;
+        unsigned bits = wb == w0 ? bits0 : (w < w1 ? __ldcg(E.bitmap + w) : 0u);
         int total;
         int pos = off + block_excl_scan(__popc(bits), &total);
         while (bits) {
@@ -957,7 +981,6 @@ __device__ void compact_list(const Engine &E, WorkItem *Lout, int *n_out, int st
     __syncthreads();
     const int n = min(off, cap);
     const int end = (int)min((long long)n, (long long)E.n_slots - before);
-    ItemSim c;
     for (int i = threadIdx.x; i < end; i += IB * BLOCK) {
         long long g[IB];
         WorkItem *o[IB];
@@ -1419,15 +1442,22 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
         const int n_new = min(__ldcg(&st->n_new), E.n_slots);
-        for (int i = gwarp; i < n_new; i += nwarps) {
-            const int ns = __ldcg(E.newslots + i);
-            if (TCM_SLOT_OK(E, ns)) zero_box(E, ns, lane);
-        }
         const int n_ret = __ldcg(&st->n_retired);
         const int base = max(__ldcg(&st->free_top), 0);
-        for (int i = gtid; i < n_ret; i += nthr)
-            if (TCM_SLOT_OK(E, base + i) && TCM_SLOT_OK(E, i)) E.free_stack[base + i] = __ldcg(E.retired + i);
-        compact_list(E, Lnext, &st->n_active[cur ^ 1], 1);
+        compact_list(E, Lnext, &st->n_active[cur ^ 1], 1, [&] {
+            // the boxes claimed by this update zeroed, the released ones
+            // pushed on the free stack (the first loads of both together)
+            const bool r = gtid < n_ret && TCM_SLOT_OK(E, base + gtid) && TCM_SLOT_OK(E, gtid);
+            const int r0 = r ? __ldcg(E.retired + gtid) : 0;
+            int ns = gwarp < n_new ? __ldcg(E.newslots + gwarp) : -1;
+            for (int i = gwarp; i < n_new; i += nwarps) {
+                if (TCM_SLOT_OK(E, ns)) zero_box(E, ns, lane);
+                ns = i + nwarps < n_new ? __ldcg(E.newslots + i + nwarps) : -1;
+            }
+            if (r) E.free_stack[base + gtid] = r0;
+            for (int i = gtid + nthr; i < n_ret; i += nthr)
+                if (TCM_SLOT_OK(E, base + i) && TCM_SLOT_OK(E, i)) E.free_stack[base + i] = __ldcg(E.retired + i);
+        });
         // The last block to finish advances the step: every block has read
         // the step counters by then.
         if (last_block(st)) {
@@ -1451,7 +1481,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
 // Build active list `parity` from the bitmap (start of a simulation).
 __global__ void __launch_bounds__(BLOCK, 1) k_compact(Engine E, int parity)
 {
-    compact_list(E, parity ? E.items1 : E.items0, &E.st->n_active[parity], 0);
+    compact_list(E, parity ? E.items1 : E.items0, &E.st->n_active[parity], 0, [] {});
     if (blockIdx.x == 0 && threadIdx.x == 0) E.st->list_age = 0;
 }
 
