@@ -1406,10 +1406,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_step(Engine E, int cur, int manage
     {
         const int gtid = blockIdx.x * BLOCK + threadIdx.x;
         const int nthr = gridDim.x * BLOCK;
-        // Four items per thread at a time, so their loads overlap (measured:
-        // eight hold more registers and took longer, 16.6 against 14.6 ms
-        // over the 512^3 run).
-        constexpr int U = 4;
+        // Two items per thread at a time, so their loads overlap (measured
+        // over the 512^3 run on one GPU: 1, 2, 3, 4, 5, 6 items took 14.5,
+        // 14.0, 14.2, 14.4-14.6, 15.1, 15.5 ms for FP32; a thread's items
+        // that take the general path run one after another).
+        constexpr int U = 2;
         SimCache sc;
         for (int base = gtid; base < nact; base += U * nthr) {
             WorkItem w[U];
