@@ -1558,6 +1558,13 @@ __device__ bool rules_uniform(const MediaDev &M, long long x0, long long x1, lon
     return true;
 }
 
+// Classification, 32 bricks per warp at a time, one per lane: each lane
+// takes its brick's corner k and, for rule-described media, decides from
+// the rules alone whether no boundary crosses the brick (the common case
+// needs no node: one lane's FP64 work per brick).  The warp then scans the
+// nodes of every brick that is left undecided, one brick at a time, 32 nodes
+// per round; the first round that finds a k different from the corner's
+// decides.  A brick with more than one k gets the next per-node array id.
 __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
                                 double dx, double dts, long long bb, float *kscal, int *kslab_of_brick,
                                 int *n_kslabs)
@@ -1565,28 +1572,45 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
     const long long nb = (long long)mx * my * mz;
     const int lane = threadIdx.x & 31;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nb; g += nw) {
-        const long long cx = g % mx, cy = (g / mx) % my, cz = g / ((long long)mx * my);
-        const long long x0 = cx * BX, y0 = cy * BY, z0 = cz * BZ;
-        const long long x1 = min(x0 + BX, (long long)nx) - 1, y1 = min(y0 + BY, (long long)ny) - 1,
-                        z1 = min(z0 + BZ, (long long)nz) - 1;
-        const float k0 = k_of_c(media_c(M, nx, ny, x0, y0, z0), dt, dx, dts);
-        bool uniform = M.kind == MEDIA_RULES && rules_uniform(M, x0, x1, y0, y1, z0, z1);
-        bool diff = false;
-        if (!uniform) {
-            // 32 nodes per round; the first round that finds a k different
-            // from the corner's decides (the warp leaves together)
+    for (long long g0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; g0 < nb; g0 += nw * 32) {
+        const long long g = g0 + lane;
+        const bool mine = g < nb;
+        int x0 = 0, y0 = 0, z0 = 0, x1 = 0, y1 = 0, z1 = 0;
+        float k0 = 0.f;
+        bool uniform = false;
+        if (mine) {
+            const long long cx = g % mx, cy = (g / mx) % my, cz = g / ((long long)mx * my);
+            x0 = (int)(cx * BX);
+            y0 = (int)(cy * BY);
+            z0 = (int)(cz * BZ);
+            x1 = min(x0 + BX, nx) - 1;
+            y1 = min(y0 + BY, ny) - 1;
+            z1 = min(z0 + BZ, nz) - 1;
+            k0 = k_of_c(media_c(M, nx, ny, x0, y0, z0), dt, dx, dts);
+            uniform = M.kind == MEDIA_RULES && rules_uniform(M, x0, x1, y0, y1, z0, z1);
+        }
+        bool mydiff = false;
+        unsigned todo = __ballot_sync(FULL, mine && !uniform);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int bx0 = __shfl_sync(FULL, x0, src), by0 = __shfl_sync(FULL, y0, src);
+            const int bz0 = __shfl_sync(FULL, z0, src), bx1 = __shfl_sync(FULL, x1, src);
+            const int by1 = __shfl_sync(FULL, y1, src), bz1 = __shfl_sync(FULL, z1, src);
+            const unsigned kb = __float_as_uint(__shfl_sync(FULL, k0, src));
+            bool diff = false;
             for (int e0 = 0; e0 < BVOL && !diff; e0 += 32) {
                 const int e = e0 + lane;
-                const long long gx = x0 + e % BX, gy = y0 + (e / BX) % BY, gz = z0 + e / (BX * BY);
+                const int gx = bx0 + e % BX, gy = by0 + (e / BX) % BY, gz = bz0 + e / (BX * BY);
                 bool d = false;
-                if (e < BVOL && gx <= x1 && gy <= y1 && gz <= z1)
-                    d = __float_as_uint(k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, dts)) != __float_as_uint(k0);
+                if (e < BVOL && gx <= bx1 && gy <= by1 && gz <= bz1)
+                    d = __float_as_uint(k_of_c(media_c(M, nx, ny, gx, gy, gz), dt, dx, dts)) != kb;
                 diff = __any_sync(FULL, d);
             }
+            if (lane == src) mydiff = diff;
         }
-        if (lane == 0) {
-            if (diff) {
+        if (mine) {
+            if (mydiff) {
                 kslab_of_brick[bb + g] = atomicAdd(n_kslabs, 1);
                 kscal[bb + g] = 0.f;
             } else {
@@ -1597,32 +1621,41 @@ __global__ void k_bulk_classify(MediaDev M, int nx, int ny, int nz, int mx, int 
     }
 }
 
+// Per-node k of every brick that has an array: each warp reads the array
+// ids of 32 bricks at once and fills the arrays of those that have one, a
+// brick at a time, every c of a lane loaded before any k is computed.
 __global__ void k_bulk_fill(MediaDev M, int nx, int ny, int nz, int mx, int my, int mz, double dt,
                             double dx, double dts, long long bb, const int *kslab_of_brick, float *kslabs)
 {
     const long long nb = (long long)mx * my * mz;
     const int lane = threadIdx.x & 31;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nb; g += nw) {
-        const int ks = kslab_of_brick[bb + g];
-        if (ks < 0) continue;
-        const long long cx = g % mx, cy = (g / mx) % my, cz = g / ((long long)mx * my);
-        // every c of the lane first (independent loads in flight), then k
-        constexpr int PER = (BVOL + 31) / 32;
-        float c[PER];
-        unsigned in = 0u;   // bit j: node lane + 32 j lies in the grid
+    for (long long g0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; g0 < nb; g0 += nw * 32) {
+        const long long gl = g0 + lane;
+        const int ksl = gl < nb ? kslab_of_brick[bb + gl] : -1;
+        unsigned todo = __ballot_sync(FULL, ksl >= 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int ks = __shfl_sync(FULL, ksl, src);
+            const long long g = g0 + src;
+            const long long cx = g % mx, cy = (g / mx) % my, cz = g / ((long long)mx * my);
+            constexpr int PER = (BVOL + 31) / 32;
+            float c[PER];
+            unsigned in = 0u;   // bit j: node lane + 32 j lies in the grid
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int e = lane + 32 * j;
-            const long long gx = cx * BX + e % BX, gy = cy * BY + (e / BX) % BY, gz = cz * BZ + e / (BX * BY);
-            const bool ok = e < BVOL && gx < nx && gy < ny && gz < nz;
-            c[j] = ok ? media_c(M, nx, ny, gx, gy, gz) : 0.f;
-            in |= (ok ? 1u : 0u) << j;
-        }
+            for (int j = 0; j < PER; ++j) {
+                const int e = lane + 32 * j;
+                const long long gx = cx * BX + e % BX, gy = cy * BY + (e / BX) % BY, gz = cz * BZ + e / (BX * BY);
+                const bool ok = e < BVOL && gx < nx && gy < ny && gz < nz;
+                c[j] = ok ? media_c(M, nx, ny, gx, gy, gz) : 0.f;
+                in |= (ok ? 1u : 0u) << j;
+            }
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int e = lane + 32 * j;
-            if (e < BVOL) kslabs[(size_t)ks * BVOL + e] = (in >> j & 1u) ? k_of_c(c[j], dt, dx, dts) : 0.f;
+            for (int j = 0; j < PER; ++j) {
+                const int e = lane + 32 * j;
+                if (e < BVOL) kslabs[(size_t)ks * BVOL + e] = (in >> j & 1u) ? k_of_c(c[j], dt, dx, dts) : 0.f;
+            }
         }
     }
 }
@@ -1921,8 +1954,8 @@ cudaError_t launch_bulk_classify(const MediaDev &m, int nx, int ny, int nz, int 
                                  int *n_kslabs, cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_classify<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_ratio(dt, dx), bb,
-                                                           kscal, kslab_of_brick, n_kslabs);
+    k_bulk_classify<<<grid_for(nb, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_ratio(dt, dx), bb,
+                                                      kscal, kslab_of_brick, n_kslabs);
     return cudaGetLastError();
 }
 
@@ -1931,8 +1964,8 @@ cudaError_t launch_bulk_fill(const MediaDev &m, int nx, int ny, int nz, int mx, 
                              cudaStream_t s)
 {
     const long long nb = (long long)mx * my * mz;
-    k_bulk_fill<<<grid_for(nb * 32, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_ratio(dt, dx), bb,
-                                                       kslab_of_brick, kslabs);
+    k_bulk_fill<<<grid_for(nb, 256), 256, 0, s>>>(m, nx, ny, nz, mx, my, mz, dt, dx, exact_ratio(dt, dx), bb,
+                                                  kslab_of_brick, kslabs);
     return cudaGetLastError();
 }
 
