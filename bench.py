@@ -576,12 +576,12 @@ def time_to_solution(torch, tcm, W, wl, dev, local_rank):
 
 
 def precision_leg(torch, tcm, W, dev, local_rank):
-    """Field storage FP32 / BF16 / FP16 on the 256^3 layered, perturbed medium
-    (relative threshold 1e-6, 20-step decay), 800 steps each: device time of
-    the steps, node updates/s, HBM GB/s at the storage's algorithmic bytes per
-    update, max and RMS error of phi^800 against the FP32 run (which is within
-    ~1e-6 of the FP64 dense grid), and the drift of the leapfrog energy from
-    step len(wavelet)+50 to step 800 (FP64 reduction on the device)."""
+    """Field storage FP32 / BF16 / FP16 on the 256^3 homogeneous medium with
+    the 64^3 configuration's source (relative threshold 1e-6, 20-step decay),
+    800 steps each: device time of the steps, node updates/s, HBM GB/s at the
+    storage's algorithmic bytes per update, max and RMS error of phi^800
+    against the FP32 run, and the drift of the leapfrog energy from step
+    len(wavelet)+50 to step 800 (FP64 reduction on the device)."""
     from paper_1702_00216_gb300 import autotune
     wl = W.precision(256, 800)
     # brick shape and CTA blocking from the autotuner (steps 300..400, binary32)
@@ -616,7 +616,10 @@ def precision_leg(torch, tcm, W, dev, local_rank):
         buf = torch.empty(wl.shape, dtype=torch.float32, device=dev)
         tcm.tcm_read_field_device(s.handle, 0, (0, 0, 0), wl.shape[::-1], buf.data_ptr())
         torch.cuda.synchronize()
-        bpu = 16 if st == "f32" else 12   # 16-bit: read phi, v (2 B each), k (4 B); write phi, v
+        # every brick has a scalar k (homogeneous medium): binary32 reads phi^n
+        # and phi^{n-1} and writes phi^{n+1}; 16-bit reads phi and v (2 B
+        # each) and writes both
+        bpu = 12 if st == "f32" else 8
         r = {"updates_per_s": upd / (ms / 1e3), "ms": ms, "bytes_per_update": bpu,
              "hbm_gbs": upd * bpu / (ms / 1e3) / 1e9,
              "energy_drift": abs(en_b - en_a) / abs(en_a) if en_a else None}

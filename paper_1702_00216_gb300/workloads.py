@@ -261,11 +261,16 @@ def scatterer(shape=(64, 64, 112), steps: int = 260, beam_sigma: float = 5.0, pu
 
 
 def precision(n: int = 256, steps: int = 800) -> Workload:
-    """The layered, perturbed medium and settings of layered() on a 256^3 grid
-    (the storage-precision comparison)."""
-    w = layered(n, steps)
-    w.name = f"precision-{n}^3-layered-perturbed-ricker"
-    return w
+    """The medium and source of small() -- homogeneous c = 1, dx = 1, dt = 0.5,
+    Ricker f = 1/16 at the grid centre -- on a 256^3 grid, with the relative
+    threshold 1e-6 and 20-step decay of layered() (the storage-precision
+    comparison)."""
+    dt = 0.5
+    f = 1.0 / 16.0
+    c = n // 2
+    return Workload(f"precision-{n}^3-homogeneous-ricker", (n, n, n), homogeneous(1.0), 1.0, dt,
+                    [(c, c, c, ricker(f, dt))], steps,
+                    thr_mode=1, tau=1e-6, decay_alpha=0.8, decay_steps=20)
 
 
 @dataclasses.dataclass

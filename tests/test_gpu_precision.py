@@ -136,13 +136,16 @@ def test_16bit_batch_equals_solo():
 
 
 def test_precision_workload_error_against_fp64_dense(capsys):
-    """256^3 layered, perturbed medium, 800 steps, relative threshold 1e-6 with
-    20-step decay: the TCM solution in each storage against the binary64 dense
-    grid (the oracle's plain definition).  Prints max and RMS errors relative
-    to max|phi| and RMS(phi)."""
+    """The precision workload: the 64^3 configuration's homogeneous medium and
+    centred source on 256^3, 800 steps, relative threshold 1e-6 with 20-step
+    decay: the TCM solution in each storage against the binary64 dense grid
+    (the oracle's plain definition).  Prints max and RMS errors relative to
+    max|phi| and RMS(phi)."""
     wl = W.precision(256, 800)
     (x, y, z, w), = wl.sources
-    k = oracle.k_from_c(wl.media.c, wl.dt, wl.dx, np.float64)
+    c = wl.media.c if wl.media.kind == "dense" else oracle.rules_c(wl.shape, wl.media)
+    k = oracle.k_from_c(c, wl.dt, wl.dx, np.float64)
+    del c
     now = np.zeros(wl.shape)
     prev = np.zeros(wl.shape)
     oracle.set_threads(os.cpu_count() or 1)
@@ -178,10 +181,11 @@ def test_precision_workload_error_against_fp64_dense(capsys):
         if b == (8, 8, 8):
             assert e == errs[st]                     # blocking only: identical results
         assert e[0] < {"f32": 1e-4, "f16": 1.2e-2, "bf16": 8e-2}[st]
-    # measured: f32 6.5e-6, f16 5.7e-3, bf16 4.1e-2 (max rel) with the
-    # velocity form (phi and v = phi^n - phi^{n-1} stored); storing phi^n and
-    # phi^{n-1} in 16 bits gave 1.4e-2 and 0.45, because each rounding of
-    # phi^{n+1} then acts as a velocity kick.  Bounds: 2x the measurements.
+    # measured (max rel): f32 1.3e-5, f16 6.5e-3, bf16 4.2e-2 with the
+    # velocity form (phi and v = phi^n - phi^{n-1} stored); on the layered,
+    # perturbed medium storing phi^n and phi^{n-1} in 16 bits gave 1.4e-2 and
+    # 0.45, because each rounding of phi^{n+1} then acts as a velocity kick.
+    # Bounds: about 2x the measurements.
     assert errs["f32"][0] < 1e-4
     assert errs["f16"][0] < 1.2e-2 and errs["bf16"][0] < 8e-2
     assert errs["f16"][0] < errs["bf16"][0] / 4
